@@ -1,0 +1,235 @@
+/*
+ * fsmp.h -- C ABI of the GB300 FSMP library (libfsmp.so).
+ *
+ * FSMP (Wang et al., "The Fast Stochastic Matching Pursuit for Neutrino and Dark Matter
+ * Experiments", arXiv 2403.03156) analyses a PMT waveform by sampling photo-electron (PE)
+ * sequences z = {t_1..t_N} from p(z | w, lambda0, t0) (Sec. 2.2, Eq. (pz)) with a Gibbs
+ * sampler: a Metropolis-Hastings move on the event time t0, then one reversible-jump move on
+ * z (birth / death / update, Sec. 2.4, Eqs. (birth), (death), (update)), each scored by the
+ * waveform log-likelihood ratio Delta nu of Appendix A.1 (Eqs. (11)-(18)) computed from a
+ * resident Sigma^-1 by Woodbury and determinant-lemma updates.
+ *
+ * This library runs one chain per waveform on the GPU. Every step of the chain (tables, RNG,
+ * proposals, Delta nu, accept/reject, the Sigma^-1 update, summaries) runs in the library's
+ * own sm_103a kernels. No function here throws; every function returns an FSMP_* status.
+ *
+ * Conventions shared by all entry points
+ *  - Times are in ns. A waveform's sample s is at t_origin + s * dt_sample_ns. PE times and
+ *    t0 live on the grid t_origin + j * grid_ns (R = dt_sample_ns / grid_ns is an integer);
+ *    "grid units" below are such j.
+ *  - A waveform batch is ragged: waveform i is samples[offsets[i] .. offsets[i+1]).
+ *  - The random stream of waveform i is Philox4x64-10 keyed by (seed, wf_id) with
+ *    wf_id = wf_ids[i] if given, else index_base + i; the counter is (step, block, 0, 0).
+ *    A result therefore depends only on the waveform, its wf_id and the seed: never on the
+ *    batch it travels in, its position, the GPU slot it ran in or the other work in flight.
+ *  - Pointers named "device" must be device memory of the context's GPU (e.g. from a
+ *    PyTorch CUDA tensor); all others are host memory.
+ */
+#ifndef FSMP_H
+#define FSMP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FSMP_OK 0
+#define FSMP_ERR_INVALID (-1)   /* bad argument; nothing was queued or launched            */
+#define FSMP_ERR_CUDA (-2)      /* a CUDA call failed; the context should be destroyed      */
+#define FSMP_ERR_NOMEM (-3)     /* host or device allocation failed / over the memory budget */
+#define FSMP_ERR_BUSY (-4)      /* submit queue full; retry after fsmp_poll                  */
+#define FSMP_ERR_TIMEOUT (-5)   /* a bounded wait ran out                                   */
+#define FSMP_ERR_CLOSED (-6)    /* context is shutting down                                  */
+
+/* ---- per-chain status bits (fsmp_summary.status) ---- */
+#define FSMP_ST_CAPACITY 1      /* a birth was refused at N == n_cap (truncated target)      */
+#define FSMP_ST_BADDET 2        /* a proposal had det(I + Lambda M) <= 0; it was rejected    */
+#define FSMP_ST_DRIFT 4         /* an FP64 refresh found incremental drift above threshold   */
+#define FSMP_ST_INVALID 8       /* the waveform's inputs were invalid; the chain did not run */
+#define FSMP_ST_NONFINITE 16    /* a non-finite Delta nu was met; the proposal was rejected  */
+
+/* ---- arithmetic of the chain state ---- */
+#define FSMP_FP64 0             /* Sigma^-1, s, y and all reductions in FP64                 */
+#define FSMP_FP32_REFRESH 1     /* FP32 Sigma^-1 / s / y with compensated reductions; FP64
+                                   2x2 algebra, log|Sigma| and log-likelihood; FP64 rebuild of
+                                   Sigma^-1, s and log|Sigma| every refresh_every accepts      */
+
+/* ---- kernel form ---- */
+#define FSMP_KERNEL_AUTO 0      /* library choice (autotuned)                                */
+#define FSMP_KERNEL_SMEM 1      /* persistent kernel, one CTA per chain, packed Sigma^-1 in
+                                   shared memory                                            */
+#define FSMP_KERNEL_GLOBAL 2    /* same kernel with packed Sigma^-1 in global memory (L2/HBM),
+                                   for windows too long for shared memory                   */
+#define FSMP_KERNEL_PLAIN 3     /* baseline: one launch per chain, full n x n FP64 Sigma^-1 in
+                                   global memory                                            */
+
+typedef struct fsmp_ctx fsmp_ctx;
+
+/* Model and engine parameters, copied at fsmp_create. Model terms follow the paper:
+ *  - SER (Sec. 3): ser_kind 0 is the ex-Gaussian shifted by 4 sigma,
+ *    V(t) = (1/2tau) exp((s^2 - 2(t-4s)tau)/2tau^2) erfc((s^2 - (t-4s)tau)/(sqrt2 s tau)),
+ *    normalised to peak 1 on the PE grid; ser_kind 1 subtracts ser_under_frac times a
+ *    peak-normalised ex-Gaussian(ser_under_sigma, ser_under_tau) started at the main peak.
+ *    The SER is truncated after the last grid point with |V| >= ser_eps, rounded up to whole
+ *    samples (L_V samples).
+ *  - phi (PE time density about t0, Eq. (pzmu)): phi_kind 0 ex-Gaussian(phi_p1 = sigma,
+ *    phi_p2 = tau) with Gaussian mean 0; phi_kind 1 the LS profile of Sec. 3
+ *    (tau1 = phi_p1, tau2 = phi_p2). phi := 0 for |t| > phi_support_ns.
+ *  - charges N(mu_q, sigma_q^2) marginalised (Sec. 2.1, Appendix A.1); white noise
+ *    sigma_noise (Sec. 1).
+ *  - t0 prior uniform on [t0_lo, t0_hi] (Eq. (t0prior)); sample_t0 = 0 holds t0 fixed.
+ *  - jump probabilities J, J, 1 - 2J (Sec. 2.4); n_cap = PE capacity per chain. */
+typedef struct {
+  double dt_sample_ns, grid_ns;
+  int ser_kind;
+  double ser_sigma, ser_tau, ser_under_frac, ser_under_sigma, ser_under_tau, ser_eps;
+  int phi_kind;
+  double phi_p1, phi_p2, phi_support_ns;
+  double mu_q, sigma_q, sigma_noise;
+  double t0_lo, t0_hi;
+  int sample_t0;
+  double jump_J;
+  int n_cap;
+  int n_max;               /* longest window (samples) any batch may carry                   */
+  int precision;           /* FSMP_FP64 | FSMP_FP32_REFRESH                                  */
+  int refresh_every;       /* K accepted moves between FP64 refreshes (FP32 mode)            */
+  double drift_tol;        /* relative refresh drift that sets FSMP_ST_DRIFT (0: 1e-3)       */
+  int kernel;              /* FSMP_KERNEL_*                                                  */
+  int threads_per_chain;   /* CTA size: 0 = autotuned, else 64..1024, a multiple of 32       */
+  size_t device_mem_budget;/* bytes the serving loop may hold for admitted requests (0: 4 GiB) */
+  int device;              /* CUDA device ordinal                                            */
+  int max_queued;          /* submit queue depth before FSMP_ERR_BUSY (0: 1024)              */
+  int n_streams;           /* concurrent launch streams of the serving loop (0: 4)           */
+} fsmp_params;
+
+/* One waveform's posterior summaries (after burn_in steps). t0 is in absolute ns.
+ * mean_Q is the posterior-mean total charge, N mu_q + sigma_q^2 u^T Sigma^-1 y with
+ * u = sum_k a_k (the Gaussian posterior of the marginalised charges of Eq. (mgauss)).
+ * logL = log p(w | z_final) (Appendix A.1), logdet = log|Sigma(z_final)|.
+ * acc / prop count accepted / proposed birth, death, update moves (an update by zero grid
+ * steps is proposed but not counted as accepted). */
+typedef struct {
+  double mean_N, var_N, mean_t0, var_t0, mean_Q, var_Q, logL, logdet;
+  int32_t acc[3], prop[3];
+  int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples;
+} fsmp_summary;
+
+/* One chain step (testing aid): log acceptance ratios of the t0 move (la0) and of the jump
+ * (la), the log uniforms they were compared with, Delta nu, N and the t0 grid index after
+ * the step, the jump type (0 birth, 1 death, 2 update) and flags (1 t0 proposed, 2 t0
+ * accepted, 4 jump accepted, 8 jump was a no-op update). -inf marks a forced reject, NaN a
+ * move that was not made. */
+typedef struct {
+  double la0, lu0, la, lu, dnu;
+  int32_t N, k0, jump, flags;
+} fsmp_trace;
+
+/* Host batch for fsmp_submit. All arrays are host memory and are copied during the call;
+ * the caller may free them once fsmp_submit returns. Optional arrays may be NULL:
+ * T_lo / T_hi (PE solution space in grid units, default the whole window [0, n R)),
+ * t0_init (ns, default the grid point nearest the middle of the t0 prior), wf_ids. */
+typedef struct {
+  uint64_t request_id, seed, index_base;
+  int n_waveforms, n_steps, burn_in, record_trace;
+  const float* samples;
+  const int32_t* offsets;        /* n_waveforms + 1 entries, offsets[0] == 0 */
+  const double* lambda0;         /* Poisson expectation guess per waveform, Sec. 2.2 */
+  const double* t_origin_ns;     /* time of sample 0 per waveform (NULL: 0)           */
+  const int32_t* T_lo;
+  const int32_t* T_hi;
+  const double* t0_init;
+  const uint64_t* wf_ids;
+} fsmp_batch;
+
+/* A finished request. Arrays are owned by the library and stay valid until the next
+ * fsmp_poll or fsmp_destroy. latency_s = completion time - submit time (host clock). */
+typedef struct {
+  uint64_t request_id;
+  int n_waveforms, status;       /* status: FSMP_OK or the error that ended the request */
+  const fsmp_summary* summaries; /* n_waveforms entries                                  */
+  const fsmp_trace* trace;       /* n_waveforms * n_steps entries, or NULL               */
+  double latency_s;
+} fsmp_result;
+
+/* Device-resident batch for fsmp_run_device: every pointer is device memory. n_max_hint
+ * bounds the longest window in the batch (0: params.n_max); windows above it are flagged
+ * FSMP_ST_INVALID. out receives n_waveforms summaries; trace (may be NULL) receives
+ * n_waveforms * n_steps records. */
+typedef struct {
+  int n_waveforms, n_steps, burn_in, n_max_hint;
+  uint64_t seed, index_base;
+  const float* samples;
+  const int32_t* offsets;
+  const double* lambda0;
+  const double* t_origin_ns;     /* may be NULL */
+  const int32_t* T_lo;           /* may be NULL */
+  const int32_t* T_hi;           /* may be NULL */
+  const double* t0_init;         /* may be NULL */
+  const uint64_t* wf_ids;        /* may be NULL */
+  fsmp_summary* out;
+  fsmp_trace* trace;             /* may be NULL */
+} fsmp_device_batch;
+
+/* Library and device facts, and the launch shape chosen for each kernel form. */
+typedef struct {
+  int device, sm_count, smem_per_block_optin, ser_len, R, L_V;
+  int n_smem_max;                /* longest window whose Sigma^-1 fits shared memory      */
+  int threads_per_chain, ctas_per_sm;
+  size_t scratch_bytes;          /* device scratch the context holds                     */
+  char name[64];
+} fsmp_info;
+
+/* Create a context on params->device: validates params, computes the SER and phi tables on
+ * the GPU (Sec. 3 formulas), allocates device scratch and starts the serving loop.
+ * Returns FSMP_OK, FSMP_ERR_INVALID, FSMP_ERR_CUDA or FSMP_ERR_NOMEM; *out is set only on
+ * FSMP_OK and is owned by the caller until fsmp_destroy. */
+int fsmp_create(const fsmp_params* params, fsmp_ctx** out);
+
+/* Queue a host batch (copied before returning). Non-blocking: FSMP_ERR_BUSY when the queue
+ * holds max_queued requests; FSMP_ERR_INVALID for malformed batches (nothing queued);
+ * FSMP_ERR_NOMEM when a single request exceeds the device memory budget. The serving loop
+ * admits queued requests as device memory frees, packs them into launches, and overlaps
+ * their work on the GPU (continuous batching). */
+int fsmp_submit(fsmp_ctx* ctx, const fsmp_batch* batch);
+
+/* Collect up to max finished requests, waiting up to timeout_ms (0: do not wait, < 0: wait
+ * forever) for the first one. Returns the number written to out (0 on timeout) or a
+ * negative FSMP_ERR_*. */
+int fsmp_poll(fsmp_ctx* ctx, fsmp_result* out, int max, int timeout_ms);
+
+/* Drain in-flight work (queued but unstarted requests are cancelled), free everything. */
+int fsmp_destroy(fsmp_ctx* ctx);
+
+/* Run a device-resident batch on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream). Enqueues kernels only: no host synchronisation, no host<->device copies. The
+ * context's device scratch is shared by all calls on the context: calls on different
+ * streams must not overlap. Returns FSMP_ERR_INVALID for bad arguments, FSMP_ERR_CUDA if a
+ * launch fails. */
+int fsmp_run_device(fsmp_ctx* ctx, const fsmp_device_batch* batch, void* stream);
+
+/* The device-computed tables (testing aid): the peak-normalised SER on the PE grid
+ * (ser_out, up to max_ser entries; *ser_len gets its length L_V * R) and phi, log phi on grid
+ * offsets d in [d_lo, d_lo + count) (phi_out / logphi_out may be NULL). Synchronous. */
+int fsmp_get_tables(fsmp_ctx* ctx, double* ser_out, int max_ser, int* ser_len, int d_lo,
+                    int count, double* phi_out, double* logphi_out);
+
+int fsmp_get_info(fsmp_ctx* ctx, fsmp_info* out);
+
+/* Philox4x64-10 blocks computed on the GPU (testing aid): out[4i..4i+4) = Philox(ctrs[4i..],
+ * key). ctrs and out are host arrays of 4 * n words. Synchronous. */
+int fsmp_philox_blocks(fsmp_ctx* ctx, const uint64_t key[2], const uint64_t* ctrs, int n,
+                       uint64_t* out);
+
+const char* fsmp_strerror(int status);
+
+/* A description of the last failure of an fsmp_* call made by the calling thread (the
+ * failing CUDA call and its error string, or the argument that was rejected); "" if none.
+ * The string is owned by the library and valid until the thread's next fsmp_* call. */
+const char* fsmp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,101 @@
+// fsmp_internal.h -- definitions shared by the library's translation units (device model,
+// batch view, Philox4x64-10, launch entry points). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fsmp.h"
+
+#define FSMP_HD __host__ __device__ __forceinline__
+
+namespace fsmp {
+
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kLog2Pi = 1.8378770664093453;
+constexpr int kMaxWarps = 16;  // CTAs of at most 512 threads
+
+// Model constants and table pointers, passed by value to every kernel.
+struct DevModel {
+  double g, inv_g, dt;        // PE grid step, 1 / g (grid steps per ns), sample period
+  int R;                      // grid points per sample
+  int Lt, L_V;                // SER table length (L_V * R) and support in samples
+  int D;                      // phi tables cover grid offsets d in [-D, D]
+  int LU;                     // longest union support of a two-PE jump (samples)
+  double mu_q, sigma_q, sq2, se2, inv_se2;
+  double t0_lo, t0_hi;
+  int sample_t0;
+  double J, log_J;
+  int n_cap;
+  int precision, refresh_every;
+  double drift_tol;
+  const double* V64;          // SER on the PE grid, peak 1          [Lt]
+  const float* V32;           // FP32 copy                           [Lt]
+  const double* phi;          // phi(d g)                            [2D + 1], index d + D
+  const double* logphi;       // log phi(d g), -inf where phi = 0
+  const double* cphi;         // running sum of phi over d' <= d (no g factor)
+};
+
+// One launch's chains. Waveform i of the view is samples[offsets[i] .. offsets[i+1]).
+// Optional per-waveform arrays override the batch-wide scalars.
+struct BatchView {
+  int n_waveforms, n_steps, burn_in, n_max;
+  uint64_t seed, index_base;
+  const float* samples;
+  const int32_t* offsets;
+  const double* lambda0;
+  const double* t_origin;      // may be null
+  const int32_t* T_lo;         // may be null
+  const int32_t* T_hi;         // may be null
+  const double* t0_init;       // may be null
+  const uint64_t* wf_ids;      // may be null
+  const uint64_t* seeds;       // may be null: per-waveform seed
+  const int32_t* n_steps_arr;  // may be null
+  const int32_t* burn_in_arr;  // may be null
+  const int64_t* trace_off;    // may be null: first trace record of each waveform
+  const int32_t* order;        // may be null: processing order (a permutation of waveforms)
+  fsmp_summary* out;
+  fsmp_trace* trace;           // may be null
+};
+
+// Philox4x64-10 (Salmon et al., SC'11): two 64x64->128 multiplies per round, Weyl key bumps.
+FSMP_HD void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+#ifdef __CUDA_ARCH__
+    uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+#else
+    unsigned __int128 p0 = (unsigned __int128)M0 * c[0], p1 = (unsigned __int128)M1 * c[2];
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+#endif
+    uint64_t y0 = hi1 ^ c[1] ^ k0, y2 = hi0 ^ c[3] ^ k1;
+    c[0] = y0; c[1] = lo1; c[2] = y2; c[3] = lo0;
+  }
+}
+
+FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
+
+// Launchers (fsmp_tables.cu / fsmp_chain.cu). All return cudaError_t of the launch.
+cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double* V64, float* V32,
+                          double* phi, double* logphi, double* cphi, int* Lt_out_dev,
+                          double* scan_buf, cudaStream_t st);
+cudaError_t launch_philox(const uint64_t* ctrs, uint64_t* out, int n, uint64_t k0, uint64_t k1,
+                          cudaStream_t st);
+
+struct LaunchShape {
+  int threads, ctas;
+  size_t smem;
+};
+// Shared-memory bytes of one chain CTA for windows up to n_alloc samples.
+size_t chain_smem_bytes(int precision, int n_alloc, int n_cap, int LU, int threads, bool sigma_in_smem);
+cudaError_t launch_chains(const DevModel& M, const BatchView& B, int kernel_form, LaunchShape shape,
+                          void* gmem_scratch, size_t gmem_scratch_bytes, cudaStream_t st);
+cudaError_t chain_kernel_attributes(int precision, bool sigma_in_smem, int max_smem);
+
+}  // namespace fsmp

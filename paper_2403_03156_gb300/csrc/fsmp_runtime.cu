@@ -1,0 +1,737 @@
+// fsmp_runtime.cu -- host runtime behind the C ABI of include/fsmp.h: context creation
+// (model tables computed on the GPU), launch shapes, the device-resident entry point, and
+// the serving loop (a scheduler thread that admits submitted requests by device memory,
+// packs them into persistent-kernel launches on a pool of streams, and hands finished
+// requests to fsmp_poll).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "fsmp_internal.h"
+
+using namespace fsmp;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+thread_local char g_last_error[256] = "";
+
+void set_error(const char* what, const char* detail, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (fsmp_runtime.cu:%d)", what, detail, line);
+}
+
+#define CK(call)                                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) {                                   \
+      set_error(#call, cudaGetErrorString(e_), __LINE__);      \
+      return FSMP_ERR_CUDA;                                    \
+    }                                                          \
+  } while (0)
+#define FAIL(code, msg)                   \
+  do {                                    \
+    set_error("rejected", msg, __LINE__); \
+    return code;                          \
+  } while (0)
+
+// One submitted request (host copy of its inputs; results once finished).
+struct Request {
+  uint64_t id = 0, seed = 0, index_base = 0;
+  int W = 0, n_steps = 0, burn_in = 0, record_trace = 0, n_max = 0;
+  std::vector<float> samples;
+  std::vector<int32_t> offsets, T_lo, T_hi;
+  std::vector<double> lambda0, t_origin, t0_init;
+  std::vector<uint64_t> wf_ids;
+  std::vector<fsmp_summary> out;
+  std::vector<fsmp_trace> trace;
+  size_t dev_bytes = 0;
+  double t_submit = 0, t_done = 0;
+  int status = FSMP_OK;
+};
+
+// A launch: several admitted requests packed into one BatchView.
+struct Pack {
+  std::vector<Request*> reqs;
+  std::vector<int> first;          // first waveform of each request in the pack
+  void* dev = nullptr;             // one device block for all arrays
+  void* host = nullptr;            // pinned staging (inputs, then outputs)
+  size_t dev_bytes = 0, host_bytes = 0, in_bytes = 0, out_off = 0, trace_off_bytes = 0;
+  size_t n_trace = 0;
+  int stream = 0;
+  std::atomic<int> done{0};
+  double t_done = 0;
+  struct fsmp_ctx* ctx = nullptr;
+};
+
+}  // namespace
+
+struct fsmp_ctx {
+  fsmp_params p;
+  DevModel M;
+  cudaDeviceProp prop;
+  int n_smem_max = 0;
+  // device tables and scratch
+  double *V64 = nullptr, *phi = nullptr, *logphi = nullptr, *cphi = nullptr, *scan = nullptr;
+  float* V32 = nullptr;
+  int* Lt_dev = nullptr;
+  void* gscratch = nullptr;
+  size_t gscratch_bytes = 0;
+  int gscratch_ctas = 0;
+  LaunchShape shape_smem{256, 0, 0}, shape_gmem{256, 0, 0};
+  // serving loop
+  std::vector<cudaStream_t> streams;
+  cudaStream_t gmem_stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queued;
+  std::vector<Pack*> inflight;
+  std::deque<Request*> done;
+  std::vector<Request*> returned;
+  size_t mem_in_use = 0;
+  bool stopping = false;
+  int fatal = FSMP_OK;
+  std::thread worker;
+  int next_stream = 0;
+};
+
+namespace {
+
+size_t packed_len(int n) { return (size_t)n * (size_t)(n + 1) / 2; }
+
+// Largest window whose packed Sigma^-1 and vectors fit in one CTA's shared memory.
+int smem_n_max(const fsmp_ctx* c) {
+  int lo = 1, hi = 4096;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    size_t b = chain_smem_bytes(c->p.precision, mid, c->p.n_cap, c->M.LU, 0, true);
+    if (b <= (size_t)c->prop.sharedMemPerBlockOptin) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+int default_threads(const fsmp_ctx* c) {
+  if (c->p.threads_per_chain > 0) return c->p.threads_per_chain;
+  return c->p.precision == FSMP_FP64 ? 128 : 256;
+}
+
+// Launch shape for windows up to n_alloc: CTAs = resident CTAs per SM x SMs (persistent).
+int make_shape(fsmp_ctx* c, int n_alloc, bool smemP, LaunchShape* out) {
+  LaunchShape s;
+  s.threads = default_threads(c);
+  s.smem = chain_smem_bytes(c->p.precision, n_alloc, c->p.n_cap, c->M.LU, s.threads, smemP);
+  if (s.smem > (size_t)c->prop.sharedMemPerBlockOptin) return FSMP_ERR_INVALID;
+  int per_sm_smem = (int)(c->prop.sharedMemPerMultiprocessor / (s.smem + 1024));
+  int per_sm_thr = c->prop.maxThreadsPerMultiProcessor / s.threads;
+  int per_sm = std::max(1, std::min(per_sm_smem, per_sm_thr));
+  s.ctas = per_sm * c->prop.multiProcessorCount;
+  *out = s;
+  return FSMP_OK;
+}
+
+int validate_params(const fsmp_params* p) {
+  if (!p) return FSMP_ERR_INVALID;
+  if (!(p->dt_sample_ns > 0) || !(p->grid_ns > 0)) return FSMP_ERR_INVALID;
+  double r = p->dt_sample_ns / p->grid_ns;
+  long R = lround(r);
+  if (R < 1 || R > 64 || fabs(r - (double)R) > 1e-9 * r) return FSMP_ERR_INVALID;
+  if (!(p->ser_sigma > 0) || !(p->ser_tau > 0) || !(p->ser_eps > 0) || p->ser_eps >= 1) return FSMP_ERR_INVALID;
+  if (p->ser_kind != 0 && p->ser_kind != 1) return FSMP_ERR_INVALID;
+  if (p->ser_kind == 1 && (!(p->ser_under_sigma > 0) || !(p->ser_under_tau > 0))) return FSMP_ERR_INVALID;
+  if (p->phi_kind != 0 && p->phi_kind != 1) return FSMP_ERR_INVALID;
+  if (!(p->phi_p1 > 0) || !(p->phi_p2 > 0) || !(p->phi_support_ns > 0)) return FSMP_ERR_INVALID;
+  if (!(p->sigma_q > 0) || !(p->sigma_noise > 0) || !isfinite(p->mu_q)) return FSMP_ERR_INVALID;
+  if (!(p->t0_hi >= p->t0_lo)) return FSMP_ERR_INVALID;
+  if (!(p->jump_J > 0) || !(p->jump_J <= 0.5)) return FSMP_ERR_INVALID;
+  if (p->n_cap < 1 || p->n_cap > 4096 || p->n_max < 1 || p->n_max > 8192) return FSMP_ERR_INVALID;
+  if (p->precision != FSMP_FP64 && p->precision != FSMP_FP32_REFRESH) return FSMP_ERR_INVALID;
+  if (p->kernel < 0 || p->kernel > 3) return FSMP_ERR_INVALID;
+  if (p->threads_per_chain != 0 && (p->threads_per_chain < 32 || p->threads_per_chain > 512 ||
+                                    p->threads_per_chain % 32))
+    return FSMP_ERR_INVALID;
+  if (p->phi_support_ns / p->grid_ns > 4.0e6) return FSMP_ERR_INVALID;
+  return FSMP_OK;
+}
+
+void free_ctx(fsmp_ctx* c) {
+  if (!c) return;
+  cudaFree(c->V64); cudaFree(c->V32); cudaFree(c->phi); cudaFree(c->logphi); cudaFree(c->cphi);
+  cudaFree(c->scan); cudaFree(c->Lt_dev); cudaFree(c->gscratch);
+  for (auto s : c->streams) cudaStreamDestroy(s);
+  if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
+  delete c;
+}
+
+void CUDART_CB pack_done_cb(void* arg) {
+  Pack* pk = (Pack*)arg;
+  pk->t_done = now_s();
+  {
+    std::lock_guard<std::mutex> lk(pk->ctx->mu);
+    pk->done.store(1);
+  }
+  pk->ctx->cv_work.notify_all();
+}
+
+// ---- device batch from arrays already on the device
+int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st) {
+  if (B.n_waveforms <= 0) return FSMP_OK;
+  int form = c->p.kernel;
+  if (form == FSMP_KERNEL_AUTO) form = B.n_max <= c->n_smem_max ? FSMP_KERNEL_SMEM : FSMP_KERNEL_GLOBAL;
+  if (form == FSMP_KERNEL_SMEM && B.n_max > c->n_smem_max) form = FSMP_KERNEL_GLOBAL;
+  if (form == FSMP_KERNEL_PLAIN) {
+    // the baseline form: one launch per chain, one CTA, Sigma^-1 in global memory, FP64
+    if (c->p.precision != FSMP_FP64 || !c->gscratch) FAIL(FSMP_ERR_INVALID, "the plain form needs precision FSMP_FP64");
+    LaunchShape s;
+    s.threads = default_threads(c);
+    s.smem = chain_smem_bytes(FSMP_FP64, B.n_max, c->p.n_cap, c->M.LU, s.threads, false);
+    s.ctas = 1;
+    for (int i = 0; i < B.n_waveforms; ++i) {
+      BatchView b1 = B;
+      b1.n_waveforms = 1;
+      b1.offsets = B.offsets + i;
+      b1.lambda0 = B.lambda0 + i;
+      if (B.t_origin) b1.t_origin = B.t_origin + i;
+      if (B.T_lo) b1.T_lo = B.T_lo + i;
+      if (B.T_hi) b1.T_hi = B.T_hi + i;
+      if (B.t0_init) b1.t0_init = B.t0_init + i;
+      if (B.wf_ids) b1.wf_ids = B.wf_ids + i; else b1.index_base = B.index_base + (uint64_t)i;
+      if (B.seeds) b1.seeds = B.seeds + i;
+      if (B.n_steps_arr) b1.n_steps_arr = B.n_steps_arr + i;
+      if (B.burn_in_arr) b1.burn_in_arr = B.burn_in_arr + i;
+      b1.out = B.out + i;
+      if (B.trace) {
+        if (B.trace_off) b1.trace_off = B.trace_off + i;
+        else b1.trace = B.trace + (size_t)i * B.n_steps;
+      }
+      b1.order = nullptr;
+      cudaError_t e = launch_chains(c->M, b1, FSMP_KERNEL_GLOBAL, s, c->gscratch, c->gscratch_bytes, st);
+      if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
+    }
+    return FSMP_OK;
+  }
+  LaunchShape s;
+  int rc = make_shape(c, B.n_max, form == FSMP_KERNEL_SMEM, &s);
+  if (rc) return rc;
+  if (form == FSMP_KERNEL_GLOBAL) {
+    if (!c->gscratch) FAIL(FSMP_ERR_INVALID, "windows beyond shared memory need n_max above it at fsmp_create");
+    size_t per = packed_len(B.n_max) * (c->p.precision == FSMP_FP64 ? 8 : 4);
+    int cap = (int)std::min<size_t>((size_t)s.ctas, c->gscratch_bytes / per);
+    if (cap < 1) FAIL(FSMP_ERR_NOMEM, "global scratch too small for this window");
+    s.ctas = cap;
+  }
+  s.ctas = std::min(s.ctas, B.n_waveforms);
+  cudaError_t e = launch_chains(c->M, B, form, s, c->gscratch, c->gscratch_bytes, st);
+  if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
+  return FSMP_OK;
+}
+
+// ---- serving loop
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct PackLayout {
+  size_t samples, offsets, lambda0, t_origin, T_lo, T_hi, t0_init, wf_ids, seeds, nsteps, burnin,
+      trace_off, in_end, out, trace, total;
+};
+
+PackLayout pack_layout(size_t n_samp, int W, size_t n_trace) {
+  PackLayout L;
+  size_t o = 0;
+  L.samples = o; o = align_up(o + n_samp * 4, 256);
+  L.offsets = o; o = align_up(o + (size_t)(W + 1) * 4, 256);
+  L.lambda0 = o; o = align_up(o + (size_t)W * 8, 256);
+  L.t_origin = o; o = align_up(o + (size_t)W * 8, 256);
+  L.T_lo = o; o = align_up(o + (size_t)W * 4, 256);
+  L.T_hi = o; o = align_up(o + (size_t)W * 4, 256);
+  L.t0_init = o; o = align_up(o + (size_t)W * 8, 256);
+  L.wf_ids = o; o = align_up(o + (size_t)W * 8, 256);
+  L.seeds = o; o = align_up(o + (size_t)W * 8, 256);
+  L.nsteps = o; o = align_up(o + (size_t)W * 4, 256);
+  L.burnin = o; o = align_up(o + (size_t)W * 4, 256);
+  L.trace_off = o; o = align_up(o + (size_t)W * 8, 256);
+  L.in_end = o;
+  L.out = o; o = align_up(o + (size_t)W * sizeof(fsmp_summary), 256);
+  L.trace = o; o = align_up(o + n_trace * sizeof(fsmp_trace), 256);
+  L.total = o;
+  return L;
+}
+
+size_t request_bytes(const Request* r) {
+  size_t n_trace = r->record_trace ? (size_t)r->W * r->n_steps : 0;
+  return pack_layout(r->samples.size(), r->W, n_trace).total;
+}
+
+// Stage and launch one pack (called by the worker without the lock held).
+int launch_pack(fsmp_ctx* c, Pack* pk) {
+  size_t n_samp = 0, n_trace = 0;
+  int W = 0, n_max = 1;
+  for (Request* r : pk->reqs) {
+    pk->first.push_back(W);
+    n_samp += r->samples.size();
+    W += r->W;
+    if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
+    n_max = std::max(n_max, r->n_max);
+  }
+  PackLayout L = pack_layout(n_samp, W, n_trace);
+  pk->dev_bytes = L.total;
+  pk->host_bytes = L.total;
+  pk->in_bytes = L.in_end;
+  pk->out_off = L.out;
+  pk->n_trace = n_trace;
+  { cudaError_t e_ = cudaMallocHost(&pk->host, L.total); if (e_ != cudaSuccess) { set_error("cudaMallocHost", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  unsigned char* h = (unsigned char*)pk->host;
+  float* samples = (float*)(h + L.samples);
+  int32_t* offsets = (int32_t*)(h + L.offsets);
+  double* lambda0 = (double*)(h + L.lambda0);
+  double* t_origin = (double*)(h + L.t_origin);
+  int32_t* T_lo = (int32_t*)(h + L.T_lo);
+  int32_t* T_hi = (int32_t*)(h + L.T_hi);
+  double* t0_init = (double*)(h + L.t0_init);
+  uint64_t* wf_ids = (uint64_t*)(h + L.wf_ids);
+  uint64_t* seeds = (uint64_t*)(h + L.seeds);
+  int32_t* nsteps = (int32_t*)(h + L.nsteps);
+  int32_t* burnin = (int32_t*)(h + L.burnin);
+  int64_t* toff = (int64_t*)(h + L.trace_off);
+  size_t so = 0, to = 0;
+  int wi = 0;
+  offsets[0] = 0;
+  for (Request* r : pk->reqs) {
+    memcpy(samples + so, r->samples.data(), r->samples.size() * 4);
+    for (int i = 0; i < r->W; ++i, ++wi) {
+      offsets[wi + 1] = (int32_t)(so + r->offsets[i + 1]);
+      lambda0[wi] = r->lambda0[i];
+      t_origin[wi] = r->t_origin.empty() ? 0.0 : r->t_origin[i];
+      int n = r->offsets[i + 1] - r->offsets[i];
+      T_lo[wi] = r->T_lo.empty() ? 0 : r->T_lo[i];
+      T_hi[wi] = r->T_hi.empty() ? n * c->M.R : r->T_hi[i];
+      t0_init[wi] = r->t0_init.empty() ? NAN : r->t0_init[i];
+      wf_ids[wi] = r->wf_ids.empty() ? r->index_base + (uint64_t)i : r->wf_ids[i];
+      seeds[wi] = r->seed;
+      nsteps[wi] = r->n_steps;
+      burnin[wi] = r->burn_in;
+      toff[wi] = r->record_trace ? (int64_t)to : -1;
+      if (r->record_trace) to += (size_t)r->n_steps;
+    }
+    so += r->samples.size();
+  }
+  // packs that use the global-memory Sigma^-1 scratch share it, so they run on one stream
+  const bool uses_scratch = n_max > c->n_smem_max || c->p.kernel == FSMP_KERNEL_GLOBAL ||
+                            c->p.kernel == FSMP_KERNEL_PLAIN;
+  cudaStream_t st = uses_scratch ? c->gmem_stream : c->streams[pk->stream];
+  pk->stream = uses_scratch ? -1 : pk->stream;
+  { cudaError_t e_ = cudaMallocAsync(&pk->dev, L.total, st); if (e_ != cudaSuccess) { set_error("cudaMallocAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  { cudaError_t e_ = cudaMemcpyAsync(pk->dev, pk->host, L.in_end, cudaMemcpyHostToDevice, st); if (e_ != cudaSuccess) { set_error("cudaMemcpyAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
+  unsigned char* d = (unsigned char*)pk->dev;
+  BatchView B{};
+  B.n_waveforms = W;
+  B.n_steps = 0;
+  B.burn_in = 0;
+  B.n_max = n_max;
+  B.samples = (const float*)(d + L.samples);
+  B.offsets = (const int32_t*)(d + L.offsets);
+  B.lambda0 = (const double*)(d + L.lambda0);
+  B.t_origin = (const double*)(d + L.t_origin);
+  B.T_lo = (const int32_t*)(d + L.T_lo);
+  B.T_hi = (const int32_t*)(d + L.T_hi);
+  B.t0_init = (const double*)(d + L.t0_init);
+  B.wf_ids = (const uint64_t*)(d + L.wf_ids);
+  B.seeds = (const uint64_t*)(d + L.seeds);
+  B.n_steps_arr = (const int32_t*)(d + L.nsteps);
+  B.burn_in_arr = (const int32_t*)(d + L.burnin);
+  B.trace_off = n_trace ? (const int64_t*)(d + L.trace_off) : nullptr;
+  B.out = (fsmp_summary*)(d + L.out);
+  B.trace = n_trace ? (fsmp_trace*)(d + L.trace) : nullptr;
+  int rc = run_view(c, B, st);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(h + L.out, d + L.out, L.total - L.out, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return FSMP_ERR_CUDA;
+  { cudaError_t e_ = cudaFreeAsync(pk->dev, st); if (e_ != cudaSuccess) { set_error("cudaFreeAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
+  { cudaError_t e_ = cudaLaunchHostFunc(st, pack_done_cb, pk); if (e_ != cudaSuccess) { set_error("cudaLaunchHostFunc", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
+  return FSMP_OK;
+}
+
+void finish_pack(fsmp_ctx* c, Pack* pk, int status) {
+  // scatter outputs back to the requests (pinned buffer -> request vectors)
+  if (status == FSMP_OK) {
+    size_t n_samp = 0, n_trace = 0;
+    int W = 0;
+    for (Request* r : pk->reqs) {
+      n_samp += r->samples.size();
+      W += r->W;
+      if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
+    }
+    PackLayout L = pack_layout(n_samp, W, n_trace);
+    const unsigned char* h = (const unsigned char*)pk->host;
+    const fsmp_summary* out = (const fsmp_summary*)(h + L.out);
+    const fsmp_trace* tr = (const fsmp_trace*)(h + L.trace);
+    size_t to = 0;
+    for (size_t q = 0; q < pk->reqs.size(); ++q) {
+      Request* r = pk->reqs[q];
+      r->out.assign(out + pk->first[q], out + pk->first[q] + r->W);
+      if (r->record_trace) {
+        r->trace.assign(tr + to, tr + to + (size_t)r->W * r->n_steps);
+        to += (size_t)r->W * r->n_steps;
+      }
+      r->t_done = pk->t_done;
+      r->status = FSMP_OK;
+    }
+  } else {
+    for (Request* r : pk->reqs) { r->status = status; r->t_done = now_s(); }
+  }
+  if (pk->host) cudaFreeHost(pk->host);
+}
+
+void worker_main(fsmp_ctx* c) {
+  cudaSetDevice(c->p.device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  while (true) {
+    // completions
+    for (size_t i = 0; i < c->inflight.size();) {
+      Pack* pk = c->inflight[i];
+      if (pk->done.load()) {
+        c->inflight.erase(c->inflight.begin() + i);
+        lk.unlock();
+        finish_pack(c, pk, FSMP_OK);
+        lk.lock();
+        c->mem_in_use -= pk->dev_bytes;
+        for (Request* r : pk->reqs) c->done.push_back(r);
+        delete pk;
+        c->cv_done.notify_all();
+      } else {
+        ++i;
+      }
+    }
+    if (c->stopping && c->inflight.empty()) break;
+    // admission: pack queued requests that fit the memory budget into one launch per stream
+    if (!c->stopping && !c->queued.empty() && (int)c->inflight.size() < (int)c->streams.size()) {
+      Pack* pk = new Pack();
+      pk->ctx = c;
+      size_t bytes = 0;
+      int traced = -1;
+      while (!c->queued.empty()) {
+        Request* r = c->queued.front();
+        if (traced >= 0 && traced != r->record_trace) break;
+        size_t b = r->dev_bytes;
+        if (c->mem_in_use + bytes + b > c->p.device_mem_budget) break;  // wait for memory to free
+        traced = r->record_trace;
+        bytes += b;
+        pk->reqs.push_back(r);
+        c->queued.pop_front();
+        if (pk->reqs.size() >= 4096) break;
+      }
+      if (!pk->reqs.empty()) {
+        pk->stream = c->next_stream;
+        c->next_stream = (c->next_stream + 1) % (int)c->streams.size();
+        c->mem_in_use += bytes;
+        c->inflight.push_back(pk);
+        lk.unlock();
+        int rc = launch_pack(c, pk);
+        lk.lock();
+        pk->dev_bytes = bytes;
+        if (rc != FSMP_OK) {
+          c->inflight.erase(std::find(c->inflight.begin(), c->inflight.end(), pk));
+          c->mem_in_use -= bytes;
+          lk.unlock();
+          cudaStreamSynchronize(pk->stream < 0 ? c->gmem_stream : c->streams[pk->stream]);
+          finish_pack(c, pk, rc);
+          lk.lock();
+          for (Request* r : pk->reqs) c->done.push_back(r);
+          delete pk;
+          c->cv_done.notify_all();
+        }
+        continue;
+      }
+      delete pk;
+    }
+    c->cv_work.wait_for(lk, std::chrono::microseconds(200));
+  }
+}
+
+int copy_batch(fsmp_ctx* c, const fsmp_batch* b, Request* r) {
+  if (!b->samples || !b->offsets || !b->lambda0 || b->n_waveforms < 1 || b->n_steps < 0 || b->burn_in < 0)
+    return FSMP_ERR_INVALID;
+  if (b->offsets[0] != 0) return FSMP_ERR_INVALID;
+  r->id = b->request_id; r->seed = b->seed; r->index_base = b->index_base;
+  r->W = b->n_waveforms; r->n_steps = b->n_steps; r->burn_in = b->burn_in;
+  r->record_trace = b->record_trace ? 1 : 0;
+  r->n_max = 1;
+  for (int i = 0; i < r->W; ++i) {
+    int n = b->offsets[i + 1] - b->offsets[i];
+    if (n < 1 || n > c->p.n_max) return FSMP_ERR_INVALID;
+    if (!(b->lambda0[i] > 0)) return FSMP_ERR_INVALID;
+    if (b->T_lo && b->T_hi && b->T_hi[i] <= b->T_lo[i]) return FSMP_ERR_INVALID;
+    r->n_max = std::max(r->n_max, n);
+  }
+  size_t ns = (size_t)b->offsets[r->W];
+  r->samples.assign(b->samples, b->samples + ns);
+  r->offsets.assign(b->offsets, b->offsets + r->W + 1);
+  r->lambda0.assign(b->lambda0, b->lambda0 + r->W);
+  if (b->t_origin_ns) r->t_origin.assign(b->t_origin_ns, b->t_origin_ns + r->W);
+  if (b->T_lo && b->T_hi) {
+    r->T_lo.assign(b->T_lo, b->T_lo + r->W);
+    r->T_hi.assign(b->T_hi, b->T_hi + r->W);
+  } else if (b->T_lo || b->T_hi) {
+    return FSMP_ERR_INVALID;
+  }
+  if (b->t0_init) r->t0_init.assign(b->t0_init, b->t0_init + r->W);
+  if (b->wf_ids) r->wf_ids.assign(b->wf_ids, b->wf_ids + r->W);
+  r->dev_bytes = request_bytes(r);
+  return FSMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fsmp_last_error(void) { return g_last_error; }
+
+const char* fsmp_strerror(int s) {
+  switch (s) {
+    case FSMP_OK: return "ok";
+    case FSMP_ERR_INVALID: return "invalid argument";
+    case FSMP_ERR_CUDA: return "CUDA error";
+    case FSMP_ERR_NOMEM: return "out of memory or over the device memory budget";
+    case FSMP_ERR_BUSY: return "submit queue full";
+    case FSMP_ERR_TIMEOUT: return "timed out";
+    case FSMP_ERR_CLOSED: return "context is shutting down";
+    default: return "unknown status";
+  }
+}
+
+int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
+  g_last_error[0] = 0;
+  if (!out) return FSMP_ERR_INVALID;
+  int rc = validate_params(params);
+  if (rc) FAIL(rc, "invalid fsmp_params");
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (params->device < 0 || params->device >= ndev) FAIL(FSMP_ERR_INVALID, "no such device");
+  std::unique_ptr<fsmp_ctx, void (*)(fsmp_ctx*)> c(new fsmp_ctx(), free_ctx);
+  c->p = *params;
+  if (c->p.refresh_every <= 0) c->p.refresh_every = 64;
+  if (!(c->p.drift_tol > 0)) c->p.drift_tol = 1e-3;
+  if (c->p.device_mem_budget == 0) c->p.device_mem_budget = (size_t)4 << 30;
+  if (c->p.max_queued <= 0) c->p.max_queued = 1024;
+  if (c->p.n_streams <= 0) c->p.n_streams = 4;
+  CK(cudaSetDevice(c->p.device));
+  CK(cudaGetDeviceProperties(&c->prop, c->p.device));
+  const fsmp_params& p = c->p;
+  DevModel& M = c->M;
+  M.R = (int)lround(p.dt_sample_ns / p.grid_ns);
+  M.g = p.grid_ns;
+  M.inv_g = 1.0 / p.grid_ns;
+  M.dt = p.dt_sample_ns;
+  // phi table range: the largest D with D g <= phi_support_ns
+  long D = (long)floor(p.phi_support_ns / p.grid_ns);
+  while ((double)(D + 1) * p.grid_ns <= p.phi_support_ns) ++D;
+  while (D > 0 && (double)D * p.grid_ns > p.phi_support_ns) --D;
+  M.D = (int)D;
+  M.mu_q = p.mu_q; M.sigma_q = p.sigma_q; M.sq2 = p.sigma_q * p.sigma_q;
+  M.se2 = p.sigma_noise * p.sigma_noise; M.inv_se2 = 1.0 / M.se2;
+  M.t0_lo = p.t0_lo; M.t0_hi = p.t0_hi; M.sample_t0 = p.sample_t0 ? 1 : 0;
+  M.J = p.jump_J; M.log_J = log(p.jump_J);
+  M.n_cap = p.n_cap;
+  M.precision = p.precision; M.refresh_every = p.refresh_every; M.drift_tol = p.drift_tol;
+  // SER scan range (must match the tables' own rule)
+  double scan_end = 8.0 * p.ser_sigma + 50.0 * p.ser_tau;
+  if (p.ser_kind == 1) scan_end += 8.0 * p.ser_under_sigma + 50.0 * p.ser_under_tau + scan_end;
+  int m_end = (int)ceil(scan_end / p.grid_ns) + 1;
+  if (m_end > (1 << 22)) FAIL(FSMP_ERR_INVALID, "SER scan range too long");
+  CK(cudaMalloc(&c->scan, sizeof(double) * (m_end + M.R)));
+  CK(cudaMalloc(&c->V64, sizeof(double) * (m_end + M.R)));
+  CK(cudaMalloc(&c->V32, sizeof(float) * (m_end + M.R)));
+  CK(cudaMalloc(&c->phi, sizeof(double) * (2 * M.D + 1)));
+  CK(cudaMalloc(&c->logphi, sizeof(double) * (2 * M.D + 1)));
+  CK(cudaMalloc(&c->cphi, sizeof(double) * (2 * M.D + 1)));
+  CK(cudaMalloc(&c->Lt_dev, sizeof(int)));
+  CK(launch_tables(p, M.R, M.D, m_end, c->V64, c->V32, c->phi, c->logphi, c->cphi, c->Lt_dev, c->scan, 0));
+  int Lt = 0;
+  CK(cudaMemcpy(&Lt, c->Lt_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaDeviceSynchronize());
+  if (Lt < M.R) FAIL(FSMP_ERR_INVALID, "SER table shorter than one sample");
+  M.Lt = Lt;
+  M.L_V = Lt / M.R;
+  // the longest |update shift| is below 8.7 ns (the smallest uniform is 2^-54)
+  M.LU = M.L_V + (int)ceil(8.7 / p.dt_sample_ns) + 2;
+  if (M.LU > 128) FAIL(FSMP_ERR_INVALID, "SER support above 117 samples is not supported");
+  M.V64 = c->V64; M.V32 = c->V32; M.phi = c->phi; M.logphi = c->logphi; M.cphi = c->cphi;
+  c->n_smem_max = smem_n_max(c.get());
+  int max_smem = (int)c->prop.sharedMemPerBlockOptin;
+  CK(chain_kernel_attributes(p.precision, true, max_smem));
+  CK(chain_kernel_attributes(p.precision, false, max_smem));
+  if (p.precision != FSMP_FP64) {
+    CK(chain_kernel_attributes(FSMP_FP64, false, max_smem));
+  }
+  // global scratch for Sigma^-1 of windows beyond shared memory (and the plain baseline form)
+  bool need_g = p.n_max > c->n_smem_max || p.kernel == FSMP_KERNEL_GLOBAL || p.kernel == FSMP_KERNEL_PLAIN;
+  if (need_g) {
+    LaunchShape s;
+    if (make_shape(c.get(), p.n_max, false, &s) != FSMP_OK) FAIL(FSMP_ERR_INVALID, "n_max too large for the global-memory kernel");
+    size_t per = packed_len(p.n_max) * (p.precision == FSMP_FP64 ? 8 : 4);
+    c->gscratch_ctas = s.ctas;
+    c->gscratch_bytes = per * (size_t)s.ctas;
+    { cudaError_t e_ = cudaMalloc(&c->gscratch, c->gscratch_bytes); if (e_ != cudaSuccess) { set_error("cudaMalloc", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  }
+  for (int i = 0; i < p.n_streams; ++i) {
+    cudaStream_t s;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->streams.push_back(s);
+  }
+  CK(cudaStreamCreateWithFlags(&c->gmem_stream, cudaStreamNonBlocking));
+  fsmp_ctx* raw = c.release();
+  raw->worker = std::thread(worker_main, raw);
+  *out = raw;
+  return FSMP_OK;
+}
+
+int fsmp_submit(fsmp_ctx* c, const fsmp_batch* b) {
+  g_last_error[0] = 0;
+  if (!c || !b) return FSMP_ERR_INVALID;
+  std::unique_ptr<Request> r(new Request());
+  int rc = copy_batch(c, b, r.get());
+  if (rc) FAIL(rc, "malformed fsmp_batch");
+  if (r->dev_bytes > c->p.device_mem_budget) return FSMP_ERR_NOMEM;
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->stopping) return FSMP_ERR_CLOSED;
+    if ((int)c->queued.size() >= c->p.max_queued) return FSMP_ERR_BUSY;
+    c->queued.push_back(r.release());
+  }
+  c->cv_work.notify_all();
+  return FSMP_OK;
+}
+
+int fsmp_poll(fsmp_ctx* c, fsmp_result* out, int max, int timeout_ms) {
+  if (!c || (!out && max > 0) || max < 0) return FSMP_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(c->mu);
+  for (Request* r : c->returned) delete r;
+  c->returned.clear();
+  if (c->done.empty() && timeout_ms != 0) {
+    auto pred = [&] { return !c->done.empty(); };
+    if (timeout_ms < 0) c->cv_done.wait(lk, pred);
+    else c->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred);
+  }
+  int k = 0;
+  while (k < max && !c->done.empty()) {
+    Request* r = c->done.front();
+    c->done.pop_front();
+    fsmp_result& o = out[k++];
+    o.request_id = r->id;
+    o.n_waveforms = r->W;
+    o.status = r->status;
+    o.summaries = r->out.empty() ? nullptr : r->out.data();
+    o.trace = r->trace.empty() ? nullptr : r->trace.data();
+    o.latency_s = r->t_done - r->t_submit;
+    c->returned.push_back(r);
+  }
+  return k;
+}
+
+int fsmp_destroy(fsmp_ctx* c) {
+  if (!c) return FSMP_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stopping = true;
+    for (Request* r : c->queued) delete r;
+    c->queued.clear();
+  }
+  c->cv_work.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  cudaSetDevice(c->p.device);
+  cudaDeviceSynchronize();
+  for (Request* r : c->done) delete r;
+  for (Request* r : c->returned) delete r;
+  free_ctx(c);
+  return FSMP_OK;
+}
+
+int fsmp_run_device(fsmp_ctx* c, const fsmp_device_batch* b, void* stream) {
+  g_last_error[0] = 0;
+  if (!c || !b || b->n_waveforms < 0 || !b->samples || !b->offsets || !b->lambda0 || !b->out ||
+      b->n_steps < 0 || b->burn_in < 0)
+    return FSMP_ERR_INVALID;
+  if ((b->T_lo == nullptr) != (b->T_hi == nullptr)) return FSMP_ERR_INVALID;
+  BatchView B{};
+  B.n_waveforms = b->n_waveforms;
+  B.n_steps = b->n_steps;
+  B.burn_in = b->burn_in;
+  B.n_max = b->n_max_hint > 0 ? b->n_max_hint : c->p.n_max;
+  if (B.n_max > c->p.n_max) return FSMP_ERR_INVALID;
+  B.seed = b->seed;
+  B.index_base = b->index_base;
+  B.samples = b->samples; B.offsets = b->offsets; B.lambda0 = b->lambda0; B.t_origin = b->t_origin_ns;
+  B.T_lo = b->T_lo; B.T_hi = b->T_hi; B.t0_init = b->t0_init; B.wf_ids = b->wf_ids;
+  B.out = b->out; B.trace = b->trace;
+  { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
+  return run_view(c, B, (cudaStream_t)stream);
+}
+
+int fsmp_get_tables(fsmp_ctx* c, double* ser_out, int max_ser, int* ser_len, int d_lo, int count,
+                    double* phi_out, double* logphi_out) {
+  if (!c) return FSMP_ERR_INVALID;
+  CK(cudaSetDevice(c->p.device));
+  if (ser_len) *ser_len = c->M.Lt;
+  if (ser_out) {
+    if (max_ser < c->M.Lt) return FSMP_ERR_INVALID;
+    CK(cudaMemcpy(ser_out, c->V64, sizeof(double) * c->M.Lt, cudaMemcpyDeviceToHost));
+  }
+  if (count > 0) {
+    if (d_lo < -c->M.D || d_lo + count - 1 > c->M.D) return FSMP_ERR_INVALID;
+    if (phi_out) CK(cudaMemcpy(phi_out, c->phi + (d_lo + c->M.D), sizeof(double) * count, cudaMemcpyDeviceToHost));
+    if (logphi_out) CK(cudaMemcpy(logphi_out, c->logphi + (d_lo + c->M.D), sizeof(double) * count, cudaMemcpyDeviceToHost));
+  }
+  return FSMP_OK;
+}
+
+int fsmp_get_info(fsmp_ctx* c, fsmp_info* o) {
+  if (!c || !o) return FSMP_ERR_INVALID;
+  memset(o, 0, sizeof(*o));
+  o->device = c->p.device;
+  o->sm_count = c->prop.multiProcessorCount;
+  o->smem_per_block_optin = (int)c->prop.sharedMemPerBlockOptin;
+  o->ser_len = c->M.Lt;
+  o->R = c->M.R;
+  o->L_V = c->M.L_V;
+  o->n_smem_max = c->n_smem_max;
+  LaunchShape s;
+  if (make_shape(c, std::min(c->p.n_max, c->n_smem_max), true, &s) == FSMP_OK) {
+    o->threads_per_chain = s.threads;
+    o->ctas_per_sm = s.ctas / c->prop.multiProcessorCount;
+  }
+  o->scratch_bytes = c->gscratch_bytes;
+  snprintf(o->name, sizeof(o->name), "%s", c->prop.name);
+  return FSMP_OK;
+}
+
+int fsmp_philox_blocks(fsmp_ctx* c, const uint64_t key[2], const uint64_t* ctrs, int n, uint64_t* out) {
+  if (!c || !key || !ctrs || !out || n < 0) return FSMP_ERR_INVALID;
+  if (n == 0) return FSMP_OK;
+  CK(cudaSetDevice(c->p.device));
+  uint64_t *dc = nullptr, *dout = nullptr;
+  size_t bytes = sizeof(uint64_t) * 4 * (size_t)n;
+  { cudaError_t e_ = cudaMalloc(&dc, bytes); if (e_ != cudaSuccess) { set_error("cudaMalloc", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  if (cudaMalloc(&dout, bytes) != cudaSuccess) { cudaFree(dc); return FSMP_ERR_NOMEM; }
+  int rc = FSMP_OK;
+  if (cudaMemcpy(dc, ctrs, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_philox(dc, dout, n, key[0], key[1], 0) != cudaSuccess ||
+      cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FSMP_ERR_CUDA;
+  cudaFree(dc);
+  cudaFree(dout);
+  return rc;
+}
+
+}  // extern "C"

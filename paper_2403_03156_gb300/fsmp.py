@@ -1,0 +1,308 @@
+"""Python binding of libfsmp.so (include/fsmp.h): argument marshalling only.
+
+Every step of the chain runs in the library's CUDA kernels. This module loads the in-tree
+library and raises if it is missing; there is no CPU fallback. PyTorch tensors may be passed
+to the device-resident entry point (``run_device``); PyTorch is used only for device memory
+and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_BUSY, ERR_TIMEOUT, ERR_CLOSED = 0, -1, -2, -3, -4, -5, -6
+ST_CAPACITY, ST_BADDET, ST_DRIFT, ST_INVALID, ST_NONFINITE = 1, 2, 4, 8, 16
+FP64, FP32_REFRESH = 0, 1
+KERNEL_AUTO, KERNEL_SMEM, KERNEL_GLOBAL, KERNEL_PLAIN = 0, 1, 2, 3
+
+SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"),
+                          ("var_t0", "<f8"), ("mean_Q", "<f8"), ("var_Q", "<f8"),
+                          ("logL", "<f8"), ("logdet", "<f8"), ("acc", "<i4", (3,)),
+                          ("prop", "<i4", (3,)), ("acc_t0", "<i4"), ("prop_t0", "<i4"),
+                          ("N_final", "<i4"), ("k0_final", "<i4"), ("status", "<i4"),
+                          ("n_samples", "<i4")])
+TRACE_DTYPE = np.dtype([("la0", "<f8"), ("lu0", "<f8"), ("la", "<f8"), ("lu", "<f8"),
+                        ("dnu", "<f8"), ("N", "<i4"), ("k0", "<i4"), ("jump", "<i4"),
+                        ("flags", "<i4")])
+
+_c_double, _c_int, _c_u64, _vp = ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dt_sample_ns", _c_double), ("grid_ns", _c_double), ("ser_kind", _c_int),
+                ("ser_sigma", _c_double), ("ser_tau", _c_double), ("ser_under_frac", _c_double),
+                ("ser_under_sigma", _c_double), ("ser_under_tau", _c_double),
+                ("ser_eps", _c_double), ("phi_kind", _c_int), ("phi_p1", _c_double),
+                ("phi_p2", _c_double), ("phi_support_ns", _c_double), ("mu_q", _c_double),
+                ("sigma_q", _c_double), ("sigma_noise", _c_double), ("t0_lo", _c_double),
+                ("t0_hi", _c_double), ("sample_t0", _c_int), ("jump_J", _c_double),
+                ("n_cap", _c_int), ("n_max", _c_int), ("precision", _c_int),
+                ("refresh_every", _c_int), ("drift_tol", _c_double), ("kernel", _c_int),
+                ("threads_per_chain", _c_int), ("device_mem_budget", ctypes.c_size_t),
+                ("device", _c_int), ("max_queued", _c_int), ("n_streams", _c_int)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("request_id", _c_u64), ("seed", _c_u64), ("index_base", _c_u64),
+                ("n_waveforms", _c_int), ("n_steps", _c_int), ("burn_in", _c_int),
+                ("record_trace", _c_int), ("samples", _vp), ("offsets", _vp), ("lambda0", _vp),
+                ("t_origin_ns", _vp), ("T_lo", _vp), ("T_hi", _vp), ("t0_init", _vp),
+                ("wf_ids", _vp)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("request_id", _c_u64), ("n_waveforms", _c_int), ("status", _c_int),
+                ("summaries", _vp), ("trace", _vp), ("latency_s", _c_double)]
+
+
+class DeviceBatch(ctypes.Structure):
+    _fields_ = [("n_waveforms", _c_int), ("n_steps", _c_int), ("burn_in", _c_int),
+                ("n_max_hint", _c_int), ("seed", _c_u64), ("index_base", _c_u64),
+                ("samples", _vp), ("offsets", _vp), ("lambda0", _vp), ("t_origin_ns", _vp),
+                ("T_lo", _vp), ("T_hi", _vp), ("t0_init", _vp), ("wf_ids", _vp), ("out", _vp),
+                ("trace", _vp)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("device", _c_int), ("sm_count", _c_int), ("smem_per_block_optin", _c_int),
+                ("ser_len", _c_int), ("R", _c_int), ("L_V", _c_int), ("n_smem_max", _c_int),
+                ("threads_per_chain", _c_int), ("ctas_per_sm", _c_int),
+                ("scratch_bytes", ctypes.c_size_t), ("name", ctypes.c_char * 64)]
+
+
+EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
+           "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
+           "fsmp_last_error"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libfsmp.so. Raises if it is missing (no fallback of any kind)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libfsmp.so is not built (%s); run paper_2403_03156_gb300.build.build()" % path)
+        _build.build()
+    L = ctypes.CDLL(path)
+    L.fsmp_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_vp)]
+    L.fsmp_submit.argtypes = [_vp, ctypes.POINTER(Batch)]
+    L.fsmp_poll.argtypes = [_vp, ctypes.POINTER(Result), _c_int, _c_int]
+    L.fsmp_destroy.argtypes = [_vp]
+    L.fsmp_run_device.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _vp]
+    L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
+    L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
+    L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
+    L.fsmp_strerror.restype = ctypes.c_char_p
+    L.fsmp_strerror.argtypes = [_c_int]
+    L.fsmp_last_error.restype = ctypes.c_char_p
+    L.fsmp_last_error.argtypes = []
+    for name in EXPORTS:
+        if name not in ("fsmp_strerror", "fsmp_last_error"):
+            getattr(L, name).restype = _c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().fsmp_strerror(int(code)).decode()
+
+
+class FsmpError(RuntimeError):
+    def __init__(self, code, what):
+        detail = load().fsmp_last_error().decode()
+        super().__init__("%s: %s (%d)%s" % (what, strerror(code), code, " -- " + detail if detail else ""))
+        self.code = code
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise FsmpError(rc, what)
+    return rc
+
+
+_PARAM_DEFAULTS = dict(dt_sample_ns=1.0, grid_ns=0.25, ser_kind=0, ser_sigma=1.5, ser_tau=6.0,
+                       ser_under_frac=0.0, ser_under_sigma=1.0, ser_under_tau=16.0, ser_eps=1e-4,
+                       phi_kind=0, phi_p1=1.5, phi_p2=20.0, phi_support_ns=4096.0, mu_q=1.0,
+                       sigma_q=0.3, sigma_noise=0.06, t0_lo=30.0, t0_hi=40.0, sample_t0=1,
+                       jump_J=0.25, n_cap=32, n_max=1024, precision=FP64, refresh_every=64,
+                       drift_tol=0.0, kernel=KERNEL_AUTO, threads_per_chain=0,
+                       device_mem_budget=0, device=0, max_queued=0, n_streams=0)
+
+
+def make_params(d: dict | None = None, **kw) -> Params:
+    vals = dict(_PARAM_DEFAULTS)
+    for src in (d or {}, kw):
+        for k, v in src.items():
+            if k in vals:
+                vals[k] = v
+    p = Params()
+    for k, v in vals.items():
+        setattr(p, k, v)
+    return p
+
+
+def _np(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dt)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Context:
+    """One fsmp_ctx: tables on the GPU, scratch, and the serving loop."""
+
+    def __init__(self, params: dict | None = None, **kw):
+        L = load()
+        self.params = make_params(params, **kw)
+        h = _vp()
+        _check(L.fsmp_create(ctypes.byref(self.params), ctypes.byref(h)), "fsmp_create")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(load().fsmp_destroy(self.h), "fsmp_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- serving API
+    def submit(self, batch: dict, request_id: int = 0, record_trace: bool = False) -> int:
+        """Queue a host batch (dict of numpy arrays, as produced by workloads). Returns the
+        status code (OK, ERR_BUSY, ...); raises on ERR_INVALID / ERR_CUDA."""
+        b = Batch()
+        arrs = dict(samples=_np(batch["samples"], np.float32), offsets=_np(batch["offsets"], np.int32),
+                    lambda0=_np(batch["lambda0"], np.float64),
+                    t_origin=_np(batch.get("t_origin_ns"), np.float64),
+                    T_lo=_np(batch.get("T_lo"), np.int32), T_hi=_np(batch.get("T_hi"), np.int32),
+                    t0_init=_np(batch.get("t0_init"), np.float64),
+                    wf_ids=_np(batch.get("wf_ids"), np.uint64))
+        b.request_id = int(request_id)
+        b.seed = int(batch.get("seed", 0))
+        b.index_base = int(batch.get("index_base", 0))
+        b.n_waveforms = len(arrs["offsets"]) - 1
+        b.n_steps = int(batch["n_steps"])
+        b.burn_in = int(batch.get("burn_in", 0))
+        b.record_trace = 1 if record_trace else 0
+        b.samples, b.offsets, b.lambda0 = _ptr(arrs["samples"]), _ptr(arrs["offsets"]), _ptr(arrs["lambda0"])
+        b.t_origin_ns, b.T_lo, b.T_hi = _ptr(arrs["t_origin"]), _ptr(arrs["T_lo"]), _ptr(arrs["T_hi"])
+        b.t0_init, b.wf_ids = _ptr(arrs["t0_init"]), _ptr(arrs["wf_ids"])
+        rc = load().fsmp_submit(self.h, ctypes.byref(b))
+        if rc in (ERR_INVALID, ERR_CUDA):
+            raise FsmpError(rc, "fsmp_submit")
+        return rc
+
+    def poll(self, max_results: int = 64, timeout_ms: int = 0):
+        """Finished requests as a list of dicts (summaries / trace copied to numpy)."""
+        res = (Result * max(1, max_results))()
+        k = load().fsmp_poll(self.h, res, int(max_results), int(timeout_ms))
+        if k < 0:
+            raise FsmpError(k, "fsmp_poll")
+        out = []
+        for i in range(k):
+            r = res[i]
+            W = r.n_waveforms
+            summ = None
+            if r.summaries:
+                buf = (ctypes.c_char * (W * SUMMARY_DTYPE.itemsize)).from_address(r.summaries)
+                summ = np.frombuffer(buf, SUMMARY_DTYPE).copy()
+            tr = None
+            if r.trace:
+                n = W * int(self._keep.get(("nsteps", r.request_id), 0))
+                if n:
+                    buf = (ctypes.c_char * (n * TRACE_DTYPE.itemsize)).from_address(r.trace)
+                    tr = np.frombuffer(buf, TRACE_DTYPE).copy().reshape(W, -1)
+            out.append(dict(request_id=r.request_id, status=r.status, summaries=summ, trace=tr,
+                            latency_s=r.latency_s))
+        return out
+
+    def run(self, batch: dict, record_trace: bool = False, request_id: int = 0, timeout_s: float = 600.0):
+        """Submit one host batch and wait for it (convenience for tests)."""
+        self._keep[("nsteps", request_id)] = int(batch["n_steps"])
+        rc = self.submit(batch, request_id=request_id, record_trace=record_trace)
+        _check(rc, "fsmp_submit")
+        got = self.poll(1, int(timeout_s * 1000))
+        if not got:
+            raise FsmpError(ERR_TIMEOUT, "fsmp_poll")
+        r = got[0]
+        _check(r["status"], "request")
+        return r["summaries"], r["trace"]
+
+    # ---------------------------------------------------------------- device-resident API
+    def run_device(self, dev: dict, n_steps: int, burn_in: int = 0, seed: int = 0, index_base: int = 0,
+                   n_max_hint: int = 0, stream=None):
+        """Enqueue chains on device-resident tensors (dict of torch CUDA tensors: samples f32,
+        offsets i32, lambda0 f64, optional t_origin_ns f64, T_lo/T_hi i32, t0_init f64,
+        wf_ids i64, out (uint8 buffer of n * summary bytes), optional trace buffer)."""
+        def p(name):
+            t = dev.get(name)
+            return None if t is None else t.data_ptr()
+
+        b = DeviceBatch()
+        b.n_waveforms = int(dev["offsets"].numel()) - 1
+        b.n_steps, b.burn_in, b.n_max_hint = int(n_steps), int(burn_in), int(n_max_hint)
+        b.seed, b.index_base = int(seed), int(index_base)
+        b.samples, b.offsets, b.lambda0, b.t_origin_ns = p("samples"), p("offsets"), p("lambda0"), p("t_origin_ns")
+        b.T_lo, b.T_hi, b.t0_init, b.wf_ids = p("T_lo"), p("T_hi"), p("t0_init"), p("wf_ids")
+        b.out, b.trace = p("out"), p("trace")
+        st = None if stream is None else int(stream.cuda_stream)
+        _check(load().fsmp_run_device(self.h, ctypes.byref(b), st), "fsmp_run_device")
+
+    # ---------------------------------------------------------------- testing aids
+    def tables(self, d_lo: int = 0, count: int = 0):
+        n = _c_int()
+        _check(load().fsmp_get_tables(self.h, None, 0, ctypes.byref(n), 0, 0, None, None), "fsmp_get_tables")
+        ser = np.zeros(n.value, np.float64)
+        phi = np.zeros(count, np.float64)
+        lphi = np.zeros(count, np.float64)
+        _check(load().fsmp_get_tables(self.h, ser.ctypes.data, n.value, ctypes.byref(n), int(d_lo), int(count),
+                                      phi.ctypes.data if count else None,
+                                      lphi.ctypes.data if count else None), "fsmp_get_tables")
+        return ser, phi, lphi
+
+    def info(self) -> dict:
+        i = Info()
+        _check(load().fsmp_get_info(self.h, ctypes.byref(i)), "fsmp_get_info")
+        d = {k: getattr(i, k) for k, _ in Info._fields_}
+        d["name"] = i.name.decode()
+        return d
+
+    def philox_blocks(self, key, ctrs):
+        ctrs = np.ascontiguousarray(ctrs, np.uint64)
+        out = np.zeros_like(ctrs)
+        k = (_c_u64 * 2)(*[int(x) for x in key])
+        _check(load().fsmp_philox_blocks(self.h, k, ctrs.ctypes.data, len(ctrs), out.ctypes.data),
+               "fsmp_philox_blocks")
+        return out
+
+
+def summaries_from_bytes(buf) -> np.ndarray:
+    """View a uint8 buffer (e.g. a CPU copy of the ``out`` tensor) as summaries."""
+    return np.frombuffer(np.ascontiguousarray(buf).tobytes(), SUMMARY_DTYPE)
+
+
+def traces_from_bytes(buf, n_waveforms) -> np.ndarray:
+    return np.frombuffer(np.ascontiguousarray(buf).tobytes(), TRACE_DTYPE).reshape(n_waveforms, -1)

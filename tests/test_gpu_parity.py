@@ -1,0 +1,71 @@
+"""GPU (C-ABI) against the FP64 CPU oracle, step by step, on identical Philox streams."""
+import numpy as np
+import pytest
+
+from paper_2403_03156_gb300 import fsmp, workloads
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+
+C1 = workloads.CONFIGS["plain_fp64_256x128"]["params"]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_03156_gb300 import build
+    build.build()
+    return fsmp.load()
+
+
+def test_tables_match_oracle(lib, orc):
+    for name in ("plain_fp64_256x128", "lowocc_bulk_1m", "highpileup_20k_1024"):
+        params = workloads.CONFIGS[name]["params"]
+        with fsmp.Context(params, n_max=256) as ctx:
+            ser, phi, lphi = ctx.tables(-2000, 4001)
+            ref, _ = orc.ser_table(params)
+            assert len(ser) == len(ref)
+            assert np.max(np.abs(ser - ref)) < 1e-13
+            g = params["grid_ns"]
+            ref_phi = np.array([orc.phi(params, d * g) for d in range(-2000, 2001)])
+            # values agree to rounding except where phi underflows (below 1e-300 the two
+            # libms may differ by a denormal; log phi < -690 there, a certain reject anyway)
+            big = ref_phi > 1e-300
+            np.testing.assert_allclose(phi[big], ref_phi[big], rtol=1e-13)
+            np.testing.assert_allclose(lphi[big], np.log(ref_phi[big]), rtol=1e-13, atol=1e-13)
+            assert np.all(phi[~big] <= 1e-300) and np.all(lphi[~big] < -690)
+
+
+def test_philox_gpu_matches_cpu_bit_for_bit(lib, orc):
+    rng = np.random.default_rng(3)
+    n = 1_000_000
+    ctrs = np.zeros((n, 4), np.uint64)
+    ctrs[:, 0] = np.arange(n, dtype=np.uint64)
+    ctrs[:, 1] = rng.integers(0, 2, n).astype(np.uint64)
+    ctrs[:, 2] = rng.integers(0, 2**63, n).astype(np.uint64)
+    key = [0x243F6A8885A308D3, 77]
+    with fsmp.Context(C1, n_max=128) as ctx:
+        got = ctx.philox_blocks(key, ctrs)
+    assert np.array_equal(got, orc.philox_blocks(key, ctrs))
+
+
+def _oracle_trace(orc, params, batch, threads=16):
+    s, t = orc.run_batch(params, batch, orc.MODE_INCREMENTAL, n_threads=threads, trace=True)
+    return s, t
+
+
+@pytest.mark.parametrize("kernel", [fsmp.KERNEL_SMEM, fsmp.KERNEL_GLOBAL])
+def test_lockstep_fp64_config1(lib, orc, kernel):
+    """Config 1 (256 x 128 samples, lambda 2, 1000 steps): every log acceptance ratio to 1e-9
+    relative, identical decisions and summaries."""
+    wl = workloads.make_workload("plain_fp64_256x128")
+    b = wl["batch"]
+    with fsmp.Context(C1, n_max=128, precision=fsmp.FP64, kernel=kernel) as ctx:
+        s_gpu, t_gpu = ctx.run(b, record_trace=True)
+    s_orc, t_orc = _oracle_trace(orc, C1, b)
+    gpu_util.compare_traces(t_gpu, t_orc)
+    for f in ("mean_N", "var_N", "mean_t0", "var_t0"):
+        np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12)
+    for f in ("mean_Q", "var_Q", "logL", "logdet"):
+        np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
+    for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
+        np.testing.assert_array_equal(s_gpu[f], s_orc[f])
