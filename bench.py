@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""FSMP MCMC throughput on GB300 (one JSON line on stdout).
+
+Default workload: 100k waveforms of 64-512 samples (lambda log-uniform 0.5-50, windows
+trimmed to the PE span plus the SER support), 2000 MCMC steps per chain, FP32 chain state
+with FP64 refreshes every 64 accepted moves. One bench "step" runs every chain of the batch
+through all its MCMC steps (the whole hot path: tables are built once per context).
+
+  value   MCMC steps/s with inputs resident in HBM (fsmp_run_device, CUDA events on the stream)
+  e2e     the same metric through fsmp_submit / fsmp_poll with host buffers (host<->device
+          copies inside the timed region)
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (a bounded sample of
+the same workload per step). Under torchrun each rank runs its own shard (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FSMP MCMC steps/s at stated error vs plain FP64 form; p50/p99 event latency"
+UNIT = "MCMC steps/s"
+BUCKET_EDGES = [64, 96, 128, 160, 192, 224, 256, 320, 384, 512, 768, 1024, 2048, 8192]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_uneven_100k")
+    ap.add_argument("--n-waveforms", type=int, default=0, help="override the workload size (testing)")
+    ap.add_argument("--mcmc-steps", type=int, default=0, help="override MCMC steps per chain (testing)")
+    ap.add_argument("--precision", default="", help="fp32 | fp64 (default: the workload's)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per chain CTA (0: library default)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "smem", "global", "plain"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--window-range", default="", help="lo,hi: keep only windows of lo..hi samples (profiling)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def shard_workload(args, rank):
+    from paper_2403_03156_gb300 import workloads
+    wl = workloads.make_workload(args.workload, n_waveforms=args.n_waveforms or None,
+                                 seed=args.seed + 1000 * rank, n_steps=args.mcmc_steps or None)
+    b = wl["batch"]
+    W = len(b["offsets"]) - 1
+    # RNG ids unique across ranks: rank r owns waveforms [r W, (r+1) W) of the job
+    b["wf_ids"] = (np.arange(W, dtype=np.uint64) + np.uint64(rank * W))
+    if args.window_range:
+        lo, hi = (int(x) for x in args.window_range.split(","))
+        n = np.diff(b["offsets"])
+        keep = np.nonzero((n >= lo) & (n <= hi))[0]
+        wl["batch"] = workloads.subset(b, keep)
+    return wl
+
+
+# ------------------------------------------------------------------------ CPU oracle arm
+def oracle_rate(wl, target_s, rng_seed=0, max_wf=None):
+    """Time the FP64 CPU oracle (incremental mode, one thread per host core) on a random
+    sample of the workload's waveforms, sized to about target_s seconds of wall time."""
+    from oracle import oracle
+    from paper_2403_03156_gb300 import workloads
+    b = wl["batch"]
+    W = len(b["offsets"]) - 1
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(rng_seed)
+    n_probe = min(W, max(cores, 16))
+    idx = rng.choice(W, n_probe, replace=False)
+    sub = workloads.subset(b, idx)
+    t = time.perf_counter()
+    oracle.run_batch(wl["params"], sub, oracle.MODE_INCREMENTAL, n_threads=cores)
+    dt = max(time.perf_counter() - t, 1e-3)
+    n_full = int(min(W if max_wf is None else max_wf, max(n_probe, n_probe * target_s / dt)))
+    idx = rng.choice(W, n_full, replace=False)
+    sub = workloads.subset(b, idx)
+    t = time.perf_counter()
+    oracle.run_batch(wl["params"], sub, oracle.MODE_INCREMENTAL, n_threads=cores)
+    dt = time.perf_counter() - t
+    steps = n_full * int(b["n_steps"])
+    return dict(value=steps / dt, unit=UNIT, cores=cores, kind="oracle",
+                sample="%d random waveforms of %s x %d MCMC steps (FP64 incremental oracle, %d threads, %.1f s)"
+                       % (n_full, wl["name"], int(b["n_steps"]), cores, dt)), dt, n_full
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = shard_workload(args, 0)
+    b = wl["batch"]
+    cores = os.cpu_count() or 1
+    # each step: a bounded random sample, sized so warmup + steps end within a few minutes
+    per_step_target = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    base, _, n_wf = oracle_rate(wl, per_step_target)
+    from oracle import oracle
+    from paper_2403_03156_gb300 import workloads
+    rng = np.random.default_rng(7)
+    W = len(b["offsets"]) - 1
+    times = []
+    for it in range(args.warmup + args.steps):
+        sub = workloads.subset(b, rng.choice(W, n_wf, replace=False))
+        t = time.perf_counter()
+        oracle.run_batch(wl["params"], sub, oracle.MODE_INCREMENTAL, n_threads=cores)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t)
+    steps = n_wf * int(b["n_steps"])
+    value = steps / (sum(times) / len(times))
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic",
+          "config": {"workload": wl["name"], "n_waveforms": W, "mcmc_steps_per_chain": int(b["n_steps"]),
+                     "sample_per_step": n_wf},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": "%d random waveforms x %d MCMC steps per step" % (n_wf, int(b["n_steps"]))},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# ------------------------------------------------------------------------ GPU arm
+class Clocks:
+    """nvidia-smi samples of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def buckets_of(lengths):
+    """Length buckets (indices into a decreasing-length order) for one launch each."""
+    order = np.argsort(-lengths, kind="stable")
+    n_sorted = lengths[order]
+    out, i, W = [], 0, len(order)
+    while i < W:
+        nmax = int(n_sorted[i])
+        lo = max([e for e in BUCKET_EDGES if e < nmax], default=0)
+        j = i
+        while j < W and n_sorted[j] > lo:
+            j += 1
+        out.append((order[i:j], nmax))
+        i = j
+    return out
+
+
+def device_batches(torch, wl, dev, n_smem_max):
+    """Split the workload into length buckets, each a device-resident sub-batch."""
+    from paper_2403_03156_gb300 import fsmp, workloads
+    b = wl["batch"]
+    lengths = np.diff(b["offsets"]).astype(np.int64)
+    subs = []
+    for idx, nmax in buckets_of(lengths):
+        if nmax > n_smem_max and int(lengths[idx].min()) <= n_smem_max:
+            # never mix windows on both sides of the shared-memory limit
+            big = idx[lengths[idx] > n_smem_max]
+            small = idx[lengths[idx] <= n_smem_max]
+            parts = [(big, nmax), (small, int(lengths[small].max()))]
+        else:
+            parts = [(idx, nmax)]
+        for ii, nm in parts:
+            sb = workloads.subset(b, ii)
+            W = len(ii)
+            t = {
+                "samples": torch.from_numpy(sb["samples"]).to(dev),
+                "offsets": torch.from_numpy(sb["offsets"].astype(np.int32)).to(dev),
+                "lambda0": torch.from_numpy(sb["lambda0"].astype(np.float64)).to(dev),
+                "t_origin_ns": torch.from_numpy(sb["t_origin_ns"].astype(np.float64)).to(dev),
+                "wf_ids": torch.from_numpy(sb["wf_ids"].astype(np.int64)).to(dev),
+                "out": torch.zeros(W * fsmp.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dev),
+            }
+            if sb.get("T_lo") is not None:
+                t["T_lo"] = torch.from_numpy(sb["T_lo"].astype(np.int32)).to(dev)
+                t["T_hi"] = torch.from_numpy(sb["T_hi"].astype(np.int32)).to(dev)
+            subs.append((t, nm, W))
+    return subs
+
+
+def load_traffic(kernel_src):
+    """DRAM traffic per launch of the chain kernel from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "chain_kernel_dram_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    return d if d.get("kernel_sha") == sha else None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2403_03156_gb300 import build, fsmp, workloads
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    wl = shard_workload(args, rank)
+    cfg = workloads.CONFIGS[args.workload]
+    prec = {"fp32": fsmp.FP32_REFRESH, "fp64": fsmp.FP64}[args.precision or cfg["precision"]]
+    b = wl["batch"]
+    W = len(b["offsets"]) - 1
+    lengths = np.diff(b["offsets"])
+    params = dict(wl["params"], precision=prec, refresh_every=wl["meta"].get("refresh_every") or 64,
+                  n_max=int(max(lengths.max(), 64)), device=local, threads_per_chain=args.threads,
+                  kernel={"auto": fsmp.KERNEL_AUTO, "smem": fsmp.KERNEL_SMEM, "global": fsmp.KERNEL_GLOBAL,
+                          "plain": fsmp.KERNEL_PLAIN}[args.kernel])
+    ctx = fsmp.Context(params)
+    info = ctx.info()
+    peaks = ctx.measure_peaks()
+    subs = device_batches(torch, wl, dev, info["n_smem_max"])
+    n_steps = int(b["n_steps"])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step(ev=None):
+        for k, (t, nm, _) in enumerate(subs):
+            if ev is not None:
+                ev[k][0].record(stream)
+            ctx.run_device(t, n_steps=n_steps, burn_in=int(b.get("burn_in", 0)), seed=int(b["seed"]),
+                           n_max_hint=nm, stream=stream)
+            if ev is not None:
+                ev[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in subs]
+           for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (256 MiB write)
+        one_step(evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+        tw = torch.tensor([W], dtype=torch.float64, device=dev)
+        dist.all_reduce(tw, op=dist.ReduceOp.SUM)
+        W_total = int(tw.item())
+    else:
+        W_total = W
+    ms_per_step = elapsed_ms / args.steps
+    value = W_total * n_steps / (ms_per_step / 1000.0)
+
+    # per-launch roofline of the dominant kernel (the longest bucket launch)
+    summ = [fsmp.summaries_from_bytes(t["out"].cpu().numpy()) for (t, _, _) in subs]
+    durs = np.array([[evs[i][k][0].elapsed_time(evs[i][k][1]) for k in range(len(subs))]
+                     for i in range(args.steps)])
+    mean_dur = durs.mean(0)
+    kdom = int(np.argmax(mean_dur))
+    alg_bytes = float(summ[kdom]["alg_bytes"].sum())
+    achieved = alg_bytes / (mean_dur[kdom] * 1e-3) / 1e9
+    kernel_src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_chain.cu")
+    tr = load_traffic(kernel_src)
+    allsum = np.concatenate(summ)
+    acc = allsum["acc"].sum(0)
+    prop = allsum["prop"].sum(0)
+    roofline = {"bound": "smem", "achieved": achieved, "peak": peaks["smem_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["smem_gbs"],
+                "traffic": None if tr is None else tr["traffic_bytes_per_launch"] * (
+                    (summ[kdom]["prop"].sum() / max(1.0, tr["units_per_launch"])) if tr.get("scale_by_units") else 1.0),
+                "peak_source": "measured live: fsmp_measure_peaks (16-byte shared loads, 4 CTAs/SM)",
+                "kernel": "chain_kernel<%s, smem>, bucket n<=%d (%d chains)" % (
+                    "float" if prec == fsmp.FP32_REFRESH else "double", subs[kdom][1], subs[kdom][2]),
+                "alg_bytes_per_launch": alg_bytes, "launch_ms": float(mean_dur[kdom]),
+                "all_launch_ms": [float(x) for x in mean_dur]}
+    if prec == fsmp.FP64:
+        fp64 = peaks["fp64_tflops"]
+        roofline["note"] = "FP64 mode is FP64-FMA bound on this part (measured %.2f TFLOP/s FP64)" % fp64
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == fsmp.FP32_REFRESH else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "kernel": args.kernel, "n_waveforms": W_total,
+                       "mcmc_steps_per_chain": n_steps,
+                       "precision": "fp32 state + fp64 refresh" if prec == fsmp.FP32_REFRESH else "fp64",
+                       "refresh_every": params["refresh_every"],
+                       "window_samples": [int(lengths.min()), int(np.median(lengths)), int(lengths.max())],
+                       "launches_per_step": len(subs), "threads_per_chain": info["threads_per_chain"],
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "accept_rate": float(acc.sum() / max(1, prop.sum())),
+                       "accepts_per_type": [int(x) for x in acc], "proposals_per_type": [int(x) for x in prop]},
+            "roofline": roofline,
+            "gpu_launches": (W if args.kernel == "plain" else len(subs)) * args.steps, "clocks": clk,
+            "peaks_measured": peaks}
+
+    # e2e: the public host-buffer API (submit / poll), copies inside the timed region
+    if not args.no_e2e:
+        host = dict(b)
+        e2e_times = []
+        lat = []
+        for i in range(1 + min(args.steps, 3)):
+            t0 = time.perf_counter()
+            ctx.run(host, request_id=100 + i)
+            dt = time.perf_counter() - t0
+            if i > 0:
+                e2e_times.append(dt)
+        # what the serving loop stages per request: samples, offsets and 11 per-waveform
+        # arrays (lambda0, t_origin, T_lo, T_hi, t0_init, wf_id, seed, n_steps, burn_in,
+        # trace offset, processing order)
+        h2d = b["samples"].nbytes + 4 * (W + 1) + W * (8 + 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4 + 8 + 4)
+        d2h = W * fsmp.SUMMARY_DTYPE.itemsize
+        e2e_val = W * n_steps / statistics.mean(e2e_times)
+        if world > 1:
+            te = torch.tensor([statistics.mean(e2e_times)], dtype=torch.float64, device=dev)
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e_val = W_total * n_steps / float(te.item())
+        line["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, _, _ = oracle_rate(wl, args.cpu_seconds)
+        line["cpu_baseline"] = base
+    ctx.close()
+    if rank == 0:
+        emit(line)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

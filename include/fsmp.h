@@ -95,7 +95,7 @@ typedef struct {
   int n_max;               /* longest window (samples) any batch may carry                   */
   int precision;           /* FSMP_FP64 | FSMP_FP32_REFRESH                                  */
   int refresh_every;       /* K accepted moves between FP64 refreshes (FP32 mode)            */
-  double drift_tol;        /* relative refresh drift that sets FSMP_ST_DRIFT (0: 1e-3)       */
+  double drift_tol;        /* relative refresh drift that sets FSMP_ST_DRIFT (0: 5e-2)       */
   int kernel;              /* FSMP_KERNEL_*                                                  */
   int threads_per_chain;   /* CTA size: 0 = autotuned, else 64..1024, a multiple of 32       */
   size_t device_mem_budget;/* bytes the serving loop may hold for admitted requests (0: 4 GiB) */
@@ -108,12 +108,18 @@ typedef struct {
  * mean_Q is the posterior-mean total charge, N mu_q + sigma_q^2 u^T Sigma^-1 y with
  * u = sum_k a_k (the Gaussian posterior of the marginalised charges of Eq. (mgauss)).
  * logL = log p(w | z_final) (Appendix A.1), logdet = log|Sigma(z_final)|.
+ * drift_max: FP32 mode, the largest relative difference between the incrementally updated
+ * state and its FP64 rebuild seen at a refresh (n_refresh of them).
+ * alg_bytes: bytes of chain state the method had to move (per proposal the U x U lower
+ * triangle of Sigma^-1 and s on U; per accepted jump Sigma^-1 a, the packed rank-2 update
+ * read and write, and s), for roofline accounting.
  * acc / prop count accepted / proposed birth, death, update moves (an update by zero grid
  * steps is proposed but not counted as accepted). */
 typedef struct {
   double mean_N, var_N, mean_t0, var_t0, mean_Q, var_Q, logL, logdet;
+  double drift_max, alg_bytes;
   int32_t acc[3], prop[3];
-  int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples;
+  int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples, n_refresh, reserved;
 } fsmp_summary;
 
 /* One chain step (testing aid): log acceptance ratios of the t0 move (la0) and of the jump
@@ -221,6 +227,11 @@ int fsmp_get_info(fsmp_ctx* ctx, fsmp_info* out);
  * key). ctrs and out are host arrays of 4 * n words. Synchronous. */
 int fsmp_philox_blocks(fsmp_ctx* ctx, const uint64_t key[2], const uint64_t* ctrs, int n,
                        uint64_t* out);
+
+/* Roofline denominators measured on the context's GPU (the paper has no counterpart; it is
+ * a measurement aid): shared-memory load bandwidth in GB/s (16-byte loads, 4 CTAs per SM),
+ * and FP64 / FP32 FMA throughput in TFLOP/s (2 flops per FMA). Synchronous, ~0.1 s. */
+int fsmp_measure_peaks(fsmp_ctx* ctx, double* smem_gbs, double* fp64_tflops, double* fp32_tflops);
 
 const char* fsmp_strerror(int status);
 

@@ -21,6 +21,7 @@ struct DevModel {
   int Lt, L_V;                // SER table length (L_V * R) and support in samples
   int D;                      // phi tables cover grid offsets d in [-D, D]
   int LU;                     // longest union support of a two-PE jump (samples)
+  int win_extra;              // phi window per chain: n R + win_extra grid offsets (t0 range + 2)
   double mu_q, sigma_q, sq2, se2, inv_se2;
   double t0_lo, t0_hi;
   int sample_t0;
@@ -33,6 +34,9 @@ struct DevModel {
   const double* phi;          // phi(d g)                            [2D + 1], index d + D
   const double* logphi;       // log phi(d g), -inf where phi = 0
   const double* cphi;         // running sum of phi over d' <= d (no g factor)
+  const float* phi32;         // FP32 copies of the three phi tables (FP32 mode)
+  const float* logphi32;
+  const float* cphi32;
 };
 
 // One launch's chains. Waveform i of the view is samples[offsets[i] .. offsets[i+1]).
@@ -83,8 +87,8 @@ FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x
 
 // Launchers (fsmp_tables.cu / fsmp_chain.cu). All return cudaError_t of the launch.
 cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double* V64, float* V32,
-                          double* phi, double* logphi, double* cphi, int* Lt_out_dev,
-                          double* scan_buf, cudaStream_t st);
+                          double* phi, double* logphi, double* cphi, float* phi32, float* logphi32,
+                          float* cphi32, int* Lt_out_dev, double* scan_buf, cudaStream_t st);
 cudaError_t launch_philox(const uint64_t* ctrs, uint64_t* out, int n, uint64_t k0, uint64_t k1,
                           cudaStream_t st);
 
@@ -93,9 +97,17 @@ struct LaunchShape {
   size_t smem;
 };
 // Shared-memory bytes of one chain CTA for windows up to n_alloc samples.
-size_t chain_smem_bytes(int precision, int n_alloc, int n_cap, int LU, int threads, bool sigma_in_smem);
+size_t chain_smem_bytes(const DevModel& M, int n_alloc, bool sigma_in_smem);
+// Launch the chain kernel. gmem_scratch: packed Sigma^-1 slots for the global-memory form;
+// refresh_ws: FP32-mode refresh workspace, refresh_slots slots of refresh_stride bytes.
 cudaError_t launch_chains(const DevModel& M, const BatchView& B, int kernel_form, LaunchShape shape,
-                          void* gmem_scratch, size_t gmem_scratch_bytes, cudaStream_t st);
+                          void* gmem_scratch, size_t gmem_scratch_bytes, void* refresh_ws,
+                          size_t refresh_stride, int refresh_slots, cudaStream_t st);
+// Bytes of one CTA's refresh workspace for windows up to n_alloc samples.
+size_t chain_refresh_bytes(int n_cap, int n_alloc);
 cudaError_t chain_kernel_attributes(int precision, bool sigma_in_smem, int max_smem);
+// Resident CTAs per SM of the chain kernel for this block size and dynamic shared memory.
+int chain_kernel_occupancy(int precision, bool sigma_in_smem, int threads, size_t smem);
+cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, double* fp32_tflops);
 
 }  // namespace fsmp

@@ -86,7 +86,10 @@ struct fsmp_ctx {
   int n_smem_max = 0;
   // device tables and scratch
   double *V64 = nullptr, *phi = nullptr, *logphi = nullptr, *cphi = nullptr, *scan = nullptr;
-  float* V32 = nullptr;
+  float *V32 = nullptr, *phi32 = nullptr, *logphi32 = nullptr, *cphi32 = nullptr;
+  void* rscratch = nullptr;        // FP64 refresh workspace (FP32 mode)
+  size_t rscratch_stride = 0;      // doubles per CTA slot
+  int rscratch_slots = 0;
   int* Lt_dev = nullptr;
   void* gscratch = nullptr;
   size_t gscratch_bytes = 0;
@@ -117,26 +120,29 @@ int smem_n_max(const fsmp_ctx* c) {
   int lo = 1, hi = 4096;
   while (lo < hi) {
     int mid = (lo + hi + 1) / 2;
-    size_t b = chain_smem_bytes(c->p.precision, mid, c->p.n_cap, c->M.LU, 0, true);
+    size_t b = chain_smem_bytes(c->M, mid, true);
     if (b <= (size_t)c->prop.sharedMemPerBlockOptin) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
 
-int default_threads(const fsmp_ctx* c) {
+// CTA size for windows up to n_alloc samples: enough threads for the per-row phases, few
+// enough that several chains share an SM (the per-step critical path runs on one warp).
+int default_threads(const fsmp_ctx* c, int n_alloc) {
   if (c->p.threads_per_chain > 0) return c->p.threads_per_chain;
-  return c->p.precision == FSMP_FP64 ? 128 : 256;
+  if (c->p.precision == FSMP_FP64) return 128;
+  return n_alloc <= 128 ? 128 : 256;
 }
 
 // Launch shape for windows up to n_alloc: CTAs = resident CTAs per SM x SMs (persistent).
 int make_shape(fsmp_ctx* c, int n_alloc, bool smemP, LaunchShape* out) {
   LaunchShape s;
-  s.threads = default_threads(c);
-  s.smem = chain_smem_bytes(c->p.precision, n_alloc, c->p.n_cap, c->M.LU, s.threads, smemP);
+  s.threads = default_threads(c, n_alloc);
+  s.smem = chain_smem_bytes(c->M, n_alloc, smemP);
   if (s.smem > (size_t)c->prop.sharedMemPerBlockOptin) return FSMP_ERR_INVALID;
-  int per_sm_smem = (int)(c->prop.sharedMemPerMultiprocessor / (s.smem + 1024));
-  int per_sm_thr = c->prop.maxThreadsPerMultiProcessor / s.threads;
-  int per_sm = std::max(1, std::min(per_sm_smem, per_sm_thr));
+  // resident CTAs per SM as the hardware computes it (registers, shared memory, threads)
+  int per_sm = chain_kernel_occupancy(c->p.precision, smemP, s.threads, s.smem);
+  if (per_sm < 1) return FSMP_ERR_INVALID;
   s.ctas = per_sm * c->prop.multiProcessorCount;
   *out = s;
   return FSMP_OK;
@@ -170,6 +176,7 @@ void free_ctx(fsmp_ctx* c) {
   if (!c) return;
   cudaFree(c->V64); cudaFree(c->V32); cudaFree(c->phi); cudaFree(c->logphi); cudaFree(c->cphi);
   cudaFree(c->scan); cudaFree(c->Lt_dev); cudaFree(c->gscratch);
+  cudaFree(c->phi32); cudaFree(c->logphi32); cudaFree(c->cphi32); cudaFree(c->rscratch);
   for (auto s : c->streams) cudaStreamDestroy(s);
   if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
   delete c;
@@ -195,8 +202,8 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st) {
     // the baseline form: one launch per chain, one CTA, Sigma^-1 in global memory, FP64
     if (c->p.precision != FSMP_FP64 || !c->gscratch) FAIL(FSMP_ERR_INVALID, "the plain form needs precision FSMP_FP64");
     LaunchShape s;
-    s.threads = default_threads(c);
-    s.smem = chain_smem_bytes(FSMP_FP64, B.n_max, c->p.n_cap, c->M.LU, s.threads, false);
+    s.threads = default_threads(c, B.n_max);
+    s.smem = chain_smem_bytes(c->M, B.n_max, false);
     s.ctas = 1;
     for (int i = 0; i < B.n_waveforms; ++i) {
       BatchView b1 = B;
@@ -217,7 +224,7 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st) {
         else b1.trace = B.trace + (size_t)i * B.n_steps;
       }
       b1.order = nullptr;
-      cudaError_t e = launch_chains(c->M, b1, FSMP_KERNEL_GLOBAL, s, c->gscratch, c->gscratch_bytes, st);
+      cudaError_t e = launch_chains(c->M, b1, FSMP_KERNEL_GLOBAL, s, c->gscratch, c->gscratch_bytes, nullptr, 0, 0, st);
       if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
     }
     return FSMP_OK;
@@ -232,9 +239,43 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st) {
     if (cap < 1) FAIL(FSMP_ERR_NOMEM, "global scratch too small for this window");
     s.ctas = cap;
   }
+  if (c->p.precision != FSMP_FP64) {
+    if (!c->rscratch || chain_refresh_bytes(c->p.n_cap, B.n_max) > c->rscratch_stride)
+      FAIL(FSMP_ERR_INVALID, "refresh workspace missing or too small");
+    s.ctas = std::min(s.ctas, c->rscratch_slots);
+  }
   s.ctas = std::min(s.ctas, B.n_waveforms);
-  cudaError_t e = launch_chains(c->M, B, form, s, c->gscratch, c->gscratch_bytes, st);
+  cudaError_t e = launch_chains(c->M, B, form, s, c->gscratch, c->gscratch_bytes, c->rscratch,
+                                c->rscratch_stride, c->rscratch_slots, st);
   if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
+  return FSMP_OK;
+}
+
+// Launch the chains of B in length buckets. order_dev lists B's waveforms by decreasing
+// window length (n_sorted[i] = length of waveform order[i], host copy). Each bucket gets its
+// own persistent launch sized for its longest window, so short windows run with a small
+// shared-memory footprint and more CTAs per SM.
+int run_bucketed(fsmp_ctx* c, BatchView B, const int32_t* order_dev, const std::vector<int>& n_sorted,
+                 cudaStream_t st) {
+  static const int kEdges[] = {64, 96, 128, 160, 192, 224, 256, 320, 384, 512, 768, 1024, 2048, 8192};
+  const int W = (int)n_sorted.size();
+  int i = 0;
+  while (i < W) {
+    const int nmax = n_sorted[i];
+    int lo_edge = 0;
+    for (int e : kEdges) if (e < nmax) lo_edge = e;
+    // a bucket never straddles the shared-memory limit
+    if (nmax > c->n_smem_max && lo_edge < c->n_smem_max) lo_edge = c->n_smem_max;
+    int j = i;
+    while (j < W && n_sorted[j] > lo_edge) ++j;
+    BatchView b = B;
+    b.order = order_dev + i;
+    b.n_waveforms = j - i;
+    b.n_max = nmax;
+    int rc = run_view(c, b, st);
+    if (rc) return rc;
+    i = j;
+  }
   return FSMP_OK;
 }
 
@@ -243,7 +284,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct PackLayout {
   size_t samples, offsets, lambda0, t_origin, T_lo, T_hi, t0_init, wf_ids, seeds, nsteps, burnin,
-      trace_off, in_end, out, trace, total;
+      trace_off, order, in_end, out, trace, total;
 };
 
 PackLayout pack_layout(size_t n_samp, int W, size_t n_trace) {
@@ -261,6 +302,7 @@ PackLayout pack_layout(size_t n_samp, int W, size_t n_trace) {
   L.nsteps = o; o = align_up(o + (size_t)W * 4, 256);
   L.burnin = o; o = align_up(o + (size_t)W * 4, 256);
   L.trace_off = o; o = align_up(o + (size_t)W * 8, 256);
+  L.order = o; o = align_up(o + (size_t)W * 4, 256);
   L.in_end = o;
   L.out = o; o = align_up(o + (size_t)W * sizeof(fsmp_summary), 256);
   L.trace = o; o = align_up(o + n_trace * sizeof(fsmp_trace), 256);
@@ -304,6 +346,7 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   int32_t* nsteps = (int32_t*)(h + L.nsteps);
   int32_t* burnin = (int32_t*)(h + L.burnin);
   int64_t* toff = (int64_t*)(h + L.trace_off);
+  int32_t* order = (int32_t*)(h + L.order);
   size_t so = 0, to = 0;
   int wi = 0;
   offsets[0] = 0;
@@ -326,6 +369,13 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
     }
     so += r->samples.size();
   }
+  // processing order: decreasing window length (longest chains first, and length buckets)
+  std::vector<int> n_sorted(W);
+  for (int i = 0; i < W; ++i) order[i] = i;
+  std::stable_sort(order, order + W, [&](int a, int b) {
+    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+  });
+  for (int i = 0; i < W; ++i) n_sorted[i] = offsets[order[i] + 1] - offsets[order[i]];
   // packs that use the global-memory Sigma^-1 scratch share it, so they run on one stream
   const bool uses_scratch = n_max > c->n_smem_max || c->p.kernel == FSMP_KERNEL_GLOBAL ||
                             c->p.kernel == FSMP_KERNEL_PLAIN;
@@ -353,7 +403,7 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   B.trace_off = n_trace ? (const int64_t*)(d + L.trace_off) : nullptr;
   B.out = (fsmp_summary*)(d + L.out);
   B.trace = n_trace ? (fsmp_trace*)(d + L.trace) : nullptr;
-  int rc = run_view(c, B, st);
+  int rc = run_bucketed(c, B, (const int32_t*)(d + L.order), n_sorted, st);
   if (rc) return rc;
   if (cudaMemcpyAsync(h + L.out, d + L.out, L.total - L.out, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return FSMP_ERR_CUDA;
@@ -521,7 +571,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   std::unique_ptr<fsmp_ctx, void (*)(fsmp_ctx*)> c(new fsmp_ctx(), free_ctx);
   c->p = *params;
   if (c->p.refresh_every <= 0) c->p.refresh_every = 64;
-  if (!(c->p.drift_tol > 0)) c->p.drift_tol = 1e-3;
+  if (!(c->p.drift_tol > 0)) c->p.drift_tol = 5e-2;
   if (c->p.device_mem_budget == 0) c->p.device_mem_budget = (size_t)4 << 30;
   if (c->p.max_queued <= 0) c->p.max_queued = 1024;
   if (c->p.n_streams <= 0) c->p.n_streams = 4;
@@ -555,8 +605,12 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   CK(cudaMalloc(&c->phi, sizeof(double) * (2 * M.D + 1)));
   CK(cudaMalloc(&c->logphi, sizeof(double) * (2 * M.D + 1)));
   CK(cudaMalloc(&c->cphi, sizeof(double) * (2 * M.D + 1)));
+  CK(cudaMalloc(&c->phi32, sizeof(float) * (2 * M.D + 1)));
+  CK(cudaMalloc(&c->logphi32, sizeof(float) * (2 * M.D + 1)));
+  CK(cudaMalloc(&c->cphi32, sizeof(float) * (2 * M.D + 1)));
   CK(cudaMalloc(&c->Lt_dev, sizeof(int)));
-  CK(launch_tables(p, M.R, M.D, m_end, c->V64, c->V32, c->phi, c->logphi, c->cphi, c->Lt_dev, c->scan, 0));
+  CK(launch_tables(p, M.R, M.D, m_end, c->V64, c->V32, c->phi, c->logphi, c->cphi, c->phi32,
+                   c->logphi32, c->cphi32, c->Lt_dev, c->scan, 0));
   int Lt = 0;
   CK(cudaMemcpy(&Lt, c->Lt_dev, sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaDeviceSynchronize());
@@ -565,8 +619,10 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   M.L_V = Lt / M.R;
   // the longest |update shift| is below 8.7 ns (the smallest uniform is 2^-54)
   M.LU = M.L_V + (int)ceil(8.7 / p.dt_sample_ns) + 2;
+  M.win_extra = (int)ceil((p.t0_hi - p.t0_lo) / p.grid_ns) + 4;
   if (M.LU > 128) FAIL(FSMP_ERR_INVALID, "SER support above 117 samples is not supported");
   M.V64 = c->V64; M.V32 = c->V32; M.phi = c->phi; M.logphi = c->logphi; M.cphi = c->cphi;
+  M.phi32 = c->phi32; M.logphi32 = c->logphi32; M.cphi32 = c->cphi32;
   c->n_smem_max = smem_n_max(c.get());
   int max_smem = (int)c->prop.sharedMemPerBlockOptin;
   CK(chain_kernel_attributes(p.precision, true, max_smem));
@@ -583,6 +639,18 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     c->gscratch_ctas = s.ctas;
     c->gscratch_bytes = per * (size_t)s.ctas;
     { cudaError_t e_ = cudaMalloc(&c->gscratch, c->gscratch_bytes); if (e_ != cudaSuccess) { set_error("cudaMalloc", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  }
+  // FP32 mode: per-CTA FP64 refresh workspace, one slot per resident CTA of the widest launch
+  if (p.precision != FSMP_FP64) {
+    int slots = 0;
+    for (int nn : {64, std::min(p.n_max, c->n_smem_max), p.n_max}) {
+      LaunchShape s;
+      if (make_shape(c.get(), std::max(1, nn), nn <= c->n_smem_max, &s) == FSMP_OK) slots = std::max(slots, s.ctas);
+    }
+    c->rscratch_slots = slots;
+    c->rscratch_stride = (chain_refresh_bytes(p.n_cap, p.n_max) + 255) / 256 * 256;
+    if (cudaMalloc(&c->rscratch, c->rscratch_stride * (size_t)slots) != cudaSuccess)
+      FAIL(FSMP_ERR_NOMEM, "refresh workspace allocation failed");
   }
   for (int i = 0; i < p.n_streams; ++i) {
     cudaStream_t s;
@@ -711,8 +779,8 @@ int fsmp_get_info(fsmp_ctx* c, fsmp_info* o) {
     o->threads_per_chain = s.threads;
     o->ctas_per_sm = s.ctas / c->prop.multiProcessorCount;
   }
-  o->scratch_bytes = c->gscratch_bytes;
-  snprintf(o->name, sizeof(o->name), "%s", c->prop.name);
+  o->scratch_bytes = c->gscratch_bytes + c->rscratch_stride * (size_t)c->rscratch_slots;
+  snprintf(o->name, sizeof(o->name), "%.63s", c->prop.name);
   return FSMP_OK;
 }
 
@@ -732,6 +800,14 @@ int fsmp_philox_blocks(fsmp_ctx* c, const uint64_t key[2], const uint64_t* ctrs,
   cudaFree(dc);
   cudaFree(dout);
   return rc;
+}
+
+int fsmp_measure_peaks(fsmp_ctx* c, double* smem_gbs, double* fp64_tflops, double* fp32_tflops) {
+  g_last_error[0] = 0;
+  if (!c || !smem_gbs || !fp64_tflops || !fp32_tflops) FAIL(FSMP_ERR_INVALID, "null argument");
+  CK(cudaSetDevice(c->p.device));
+  CK(measure_peaks(c->prop.multiProcessorCount, smem_gbs, fp64_tflops, fp32_tflops));
+  return FSMP_OK;
 }
 
 }  // extern "C"

@@ -137,6 +137,11 @@ __global__ void phi_table_kernel(int kind, double p1, double p2, double support,
 }
 
 // Running sum of phi over the table (one CTA: per-thread chunks, then a scan of chunk sums).
+__global__ void to_float_kernel(const double* a, float* b, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
 __global__ void __launch_bounds__(1024) phi_cumsum_kernel(const double* phi, double* cphi, int n) {
   __shared__ double part[1024];
   int T = blockDim.x, t = threadIdx.x;
@@ -166,8 +171,8 @@ __global__ void philox_kernel(const uint64_t* ctrs, uint64_t* out, int n, uint64
 }  // namespace
 
 cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double* V64, float* V32,
-                          double* phi, double* logphi, double* cphi, int* Lt_out_dev,
-                          double* scan_buf, cudaStream_t st) {
+                          double* phi, double* logphi, double* cphi, float* phi32, float* logphi32,
+                          float* cphi32, int* Lt_out_dev, double* scan_buf, cudaStream_t st) {
   SerArgs a{p.ser_kind, p.ser_sigma, p.ser_tau, p.ser_under_frac, p.ser_under_sigma, p.ser_under_tau,
             p.ser_eps, p.grid_ns, m_end, R};
   ser_table_kernel<<<1, 1024, 0, st>>>(a, scan_buf, V64, V32, Lt_out_dev);
@@ -179,6 +184,11 @@ cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double*
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   phi_cumsum_kernel<<<1, 1024, 0, st>>>(phi, cphi, n);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  to_float_kernel<<<(n + 255) / 256, 256, 0, st>>>(phi, phi32, n);
+  to_float_kernel<<<(n + 255) / 256, 256, 0, st>>>(logphi, logphi32, n);
+  to_float_kernel<<<(n + 255) / 256, 256, 0, st>>>(cphi, cphi32, n);
   return cudaGetLastError();
 }
 

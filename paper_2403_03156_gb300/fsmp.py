@@ -21,10 +21,11 @@ KERNEL_AUTO, KERNEL_SMEM, KERNEL_GLOBAL, KERNEL_PLAIN = 0, 1, 2, 3
 
 SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"),
                           ("var_t0", "<f8"), ("mean_Q", "<f8"), ("var_Q", "<f8"),
-                          ("logL", "<f8"), ("logdet", "<f8"), ("acc", "<i4", (3,)),
-                          ("prop", "<i4", (3,)), ("acc_t0", "<i4"), ("prop_t0", "<i4"),
-                          ("N_final", "<i4"), ("k0_final", "<i4"), ("status", "<i4"),
-                          ("n_samples", "<i4")])
+                          ("logL", "<f8"), ("logdet", "<f8"), ("drift_max", "<f8"),
+                          ("alg_bytes", "<f8"), ("acc", "<i4", (3,)), ("prop", "<i4", (3,)),
+                          ("acc_t0", "<i4"), ("prop_t0", "<i4"), ("N_final", "<i4"),
+                          ("k0_final", "<i4"), ("status", "<i4"), ("n_samples", "<i4"),
+                          ("n_refresh", "<i4"), ("reserved", "<i4")])
 TRACE_DTYPE = np.dtype([("la0", "<f8"), ("lu0", "<f8"), ("la", "<f8"), ("lu", "<f8"),
                         ("dnu", "<f8"), ("N", "<i4"), ("k0", "<i4"), ("jump", "<i4"),
                         ("flags", "<i4")])
@@ -76,7 +77,7 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
-           "fsmp_last_error"]
+           "fsmp_last_error", "fsmp_measure_peaks"]
 
 _lib = None
 
@@ -104,6 +105,8 @@ def load(build_if_missing: bool = False):
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
     L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
     L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
+    L.fsmp_measure_peaks.argtypes = [_vp, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double),
+                                     ctypes.POINTER(_c_double)]
     L.fsmp_strerror.restype = ctypes.c_char_p
     L.fsmp_strerror.argtypes = [_c_int]
     L.fsmp_last_error.restype = ctypes.c_char_p
@@ -289,6 +292,12 @@ class Context:
         d = {k: getattr(i, k) for k, _ in Info._fields_}
         d["name"] = i.name.decode()
         return d
+
+    def measure_peaks(self) -> dict:
+        a, b, c = _c_double(), _c_double(), _c_double()
+        _check(load().fsmp_measure_peaks(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "fsmp_measure_peaks")
+        return dict(smem_gbs=a.value, fp64_tflops=b.value, fp32_tflops=c.value)
 
     def philox_blocks(self, key, ctrs):
         ctrs = np.ascontiguousarray(ctrs, np.uint64)

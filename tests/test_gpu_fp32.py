@@ -1,0 +1,95 @@
+"""FP32 mode (FP32 Sigma^-1 / s / y, FP64 refresh every K accepted moves) against the FP64 CPU
+oracle: step-level agreement while the chains stay in lockstep, and posterior summaries within
+Monte Carlo error over independent waveforms."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_03156_gb300 import fsmp, workloads
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_03156_gb300 import build
+    build.build()
+    return fsmp.load()
+
+
+def _lockstep_prefix(tg, to):
+    """Per chain, the number of leading steps with identical decisions, N and t0 index."""
+    same = (tg["flags"] == to["flags"]) & (tg["N"] == to["N"]) & (tg["k0"] == to["k0"])
+    bad = ~same
+    return np.where(bad.any(1), bad.argmax(1), same.shape[1])
+
+
+def _la_err(tg, to, pref):
+    """(absolute error, oracle value) of the log acceptance ratios over the lockstep prefixes."""
+    errs, ref = [], []
+    for i, p in enumerate(pref):
+        a = np.maximum(np.nan_to_num(tg["la"][i, :p], nan=0.0), gpu_util.LA_FLOOR)
+        b = np.maximum(np.nan_to_num(to["la"][i, :p], nan=0.0), gpu_util.LA_FLOOR)
+        errs.append(np.abs(a - b))
+        ref.append(b)
+    return np.concatenate(errs), np.concatenate(ref)
+
+
+def _params(wl, **kw):
+    b = wl["batch"]
+    n_max = int(np.diff(b["offsets"]).max())
+    return dict(wl["params"], n_max=max(64, n_max), precision=fsmp.FP32_REFRESH, **kw)
+
+
+@pytest.mark.parametrize("refresh_every", [1, 64])
+def test_fp32_tracks_oracle_step_by_step(lib, orc, refresh_every):
+    """With a refresh after every accepted move the FP32 state is rebuilt in FP64 each time,
+    so the log acceptance ratios must match the FP64 oracle to FP32 rounding; with K = 64 the
+    incremental FP32 drift between refreshes stays small."""
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=96, n_steps=600, seed=3)
+    b = wl["batch"]
+    with fsmp.Context(_params(wl, refresh_every=refresh_every)) as ctx:
+        s_gpu, t_gpu = ctx.run(b, record_trace=True)
+    s_orc, t_orc = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16, trace=True)
+    pref = _lockstep_prefix(t_gpu, t_orc)
+    assert np.median(pref) >= 300, np.sort(pref)[:20]
+    err, ref = _la_err(t_gpu, t_orc, pref)
+    # where the decision is in play (|log alpha| < 20) the error must be small in absolute
+    # terms; the paper's own FP32 check found |error of Delta nu| mainly within 1.0
+    near = np.abs(ref) < 20
+    tol = 5e-3 if refresh_every == 1 else 2e-2
+    assert np.percentile(err[near], 99) < tol, np.percentile(err[near], [50, 99, 100])
+    assert err[near].max() < 1.0
+    rel = err / np.maximum(1.0, np.abs(ref))
+    assert np.percentile(rel, 99) < (1e-3 if refresh_every == 1 else 1e-2), np.percentile(rel, [50, 99, 100])
+    print("refresh_every=%d: |dla| p50 %.2e p99 %.2e max %.2e (|la|<20); rel p99 %.2e" % (
+        refresh_every, *np.percentile(err[near], [50, 99, 100]), np.percentile(rel, 99)))
+    assert s_gpu["n_refresh"].sum() > 0
+    assert np.all((s_gpu["status"] & (fsmp.ST_DRIFT | fsmp.ST_BADDET | fsmp.ST_NONFINITE | fsmp.ST_INVALID)) == 0)
+    print("drift_max: p50 %.2e max %.2e" % (np.median(s_gpu["drift_max"]), s_gpu["drift_max"].max()))
+    assert s_gpu["drift_max"].max() < 5e-2
+    # chains that never left lockstep end in the same state with the same log-likelihood
+    full = pref == b["n_steps"]
+    assert full.sum() > (10 if refresh_every == 1 else 0)
+    np.testing.assert_array_equal(s_gpu["N_final"][full], s_orc["N_final"][full])
+    # the running FP64 log-likelihood adds FP32 Delta nu values since the last FP64 refresh
+    np.testing.assert_allclose(s_gpu["logL"][full], s_orc["logL"][full], rtol=1e-6,
+                               atol=1e-4 if refresh_every == 1 else 1e-2)
+
+
+def test_fp32_summaries_match_oracle_statistically(lib, orc):
+    """Posterior N, charge and t0 summaries over 384 waveforms of the uneven-window workload
+    (2000 steps, burn-in 400): the mean paired difference GPU - oracle is within 3 standard
+    errors (and each summary's differences are centred)."""
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=384, n_steps=2000, seed=11, burn_in=400)
+    b = wl["batch"]
+    with fsmp.Context(_params(wl, refresh_every=64)) as ctx:
+        s_gpu, _ = ctx.run(b)
+    s_orc, _ = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16)
+    for f in ("mean_N", "mean_Q", "mean_t0"):
+        d = s_gpu[f] - s_orc[f]
+        se = d.std(ddof=1) / math.sqrt(len(d))
+        assert abs(d.mean()) <= 3 * se + 1e-9, (f, d.mean(), se)
+    assert np.all((s_gpu["status"] & (fsmp.ST_DRIFT | fsmp.ST_BADDET | fsmp.ST_NONFINITE | fsmp.ST_INVALID)) == 0)
