@@ -1092,6 +1092,11 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       if (lane == 0 && S.bk_pending) bookkeep(S);
     }
     __syncthreads();
+    if constexpr (fp32) {
+      // the reported log-likelihood and log|Sigma| of the final state come from an FP64
+      // rebuild, not from the FP32 increments accumulated since the last refresh
+      if (M.refresh_every > 0 && S.n_acc_refresh > 0) refresh_state<T>(M, L, P, ws, n, n_alloc);
+    }
     if (tid == 0) {
       close_charge_hold(S, n_steps);
       fsmp_summary o;
