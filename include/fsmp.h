@@ -215,6 +215,27 @@ int fsmp_destroy(fsmp_ctx* ctx);
  * launch fails. */
 int fsmp_run_device(fsmp_ctx* ctx, const fsmp_device_batch* batch, void* stream);
 
+/* fsmp_run_device for callers that cannot allocate device memory. The paper has no
+ * counterpart: this is an integration aid. Some callers cannot call cudaMalloc -- code that
+ * runs under a framework allocator owning all device memory, or in a service that forbids
+ * allocation after start-up -- and so cannot create an fsmp_ctx (which allocates its tables
+ * and scratch). This entry point takes the parameters directly, allocates nothing, and keeps
+ * all device scratch it needs (the model tables and the per-CTA FP64 refresh workspaces of
+ * the FP32 chain kernel) in one static 64 MiB device array that every GPU loading this code
+ * holds until the process exits. The caller passes inputs and outputs as in fsmp_run_device.
+ *  - Only precision FSMP_FP32_REFRESH, windows of at most 256 samples, n_cap <= 64,
+ *    phi_support_ns / grid_ns <= 32768 and SER scans of at most 16384 grid points; larger
+ *    sizes return FSMP_ERR_INVALID (see fsmp_last_error()).
+ *  - The first call on a device sets up that device (it resolves the array's address and the
+ *    kernel's shared-memory limit), and the first call with a new set of model parameters
+ *    rebuilds the tables and synchronises `stream` once: make such a call before any stream
+ *    capture.
+ *  - All calls share the array and leave it holding the last call's tables and workspaces;
+ *    calls that overlap on the GPU race on it.
+ * The current device is restored on return. Returns FSMP_OK, FSMP_ERR_INVALID or
+ * FSMP_ERR_CUDA. */
+int fsmp_run_device_noalloc(const fsmp_params* params, const fsmp_device_batch* batch, void* stream);
+
 /* The device-computed tables (testing aid): the peak-normalised SER on the PE grid
  * (ser_out, up to max_ser entries; *ser_len gets its length L_V * R) and phi, log phi on grid
  * offsets d in [d_lo, d_lo + count) (phi_out / logphi_out may be NULL). Synchronous. */

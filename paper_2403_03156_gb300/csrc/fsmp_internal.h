@@ -109,5 +109,7 @@ cudaError_t chain_kernel_attributes(int precision, bool sigma_in_smem, int max_s
 // Resident CTAs per SM of the chain kernel for this block size and dynamic shared memory.
 int chain_kernel_occupancy(int precision, bool sigma_in_smem, int threads, size_t smem);
 cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, double* fp32_tflops);
+// Set (or, with what == nullptr, clear) the calling thread's fsmp_last_error() message.
+void record_error(const char* what, const char* detail);
 
 }  // namespace fsmp

@@ -547,6 +547,15 @@ extern "C" {
 
 const char* fsmp_last_error(void) { return g_last_error; }
 
+}  // extern "C"
+
+void fsmp::record_error(const char* what, const char* detail) {
+  if (!what) { g_last_error[0] = 0; return; }
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, detail ? detail : "");
+}
+
+extern "C" {
+
 const char* fsmp_strerror(int s) {
   switch (s) {
     case FSMP_OK: return "ok";

@@ -77,7 +77,7 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
-           "fsmp_last_error", "fsmp_measure_peaks"]
+           "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc"]
 
 _lib = None
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
     L.fsmp_poll.argtypes = [_vp, ctypes.POINTER(Result), _c_int, _c_int]
     L.fsmp_destroy.argtypes = [_vp]
     L.fsmp_run_device.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _vp]
+    L.fsmp_run_device_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(DeviceBatch), _vp]
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
     L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
     L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
@@ -306,6 +307,36 @@ class Context:
         _check(load().fsmp_philox_blocks(self.h, k, ctrs.ctypes.data, len(ctrs), out.ctypes.data),
                "fsmp_philox_blocks")
         return out
+
+
+def _device_batch(dev, n_steps, burn_in, seed, index_base, n_max_hint):
+    def p(name):
+        t = dev.get(name)
+        return None if t is None else t.data_ptr()
+
+    b = DeviceBatch()
+    b.n_waveforms = int(dev["offsets"].numel()) - 1
+    b.n_steps, b.burn_in, b.n_max_hint = int(n_steps), int(burn_in), int(n_max_hint)
+    b.seed, b.index_base = int(seed), int(index_base)
+    b.samples, b.offsets, b.lambda0, b.t_origin_ns = p("samples"), p("offsets"), p("lambda0"), p("t_origin_ns")
+    b.T_lo, b.T_hi, b.t0_init, b.wf_ids = p("T_lo"), p("T_hi"), p("t0_init"), p("wf_ids")
+    b.out, b.trace = p("out"), p("trace")
+    return b
+
+
+def run_device_noalloc(params: dict, dev: dict, n_steps: int, burn_in: int = 0, seed: int = 0,
+                       index_base: int = 0, n_max_hint: int = 0, stream=None):
+    """Run chains on device tensors (as ``Context.run_device``) without allocating device
+    memory, for callers that cannot allocate: code under a framework allocator that owns all
+    device memory, or a service that forbids allocation after start-up. Needs no Context; its
+    scratch is one static 64 MiB device array shared by all calls, so calls must not overlap
+    on the GPU. FP32 mode only, windows of at most 256 samples, n_cap at most 64. The first
+    call on a device, and the first after the model parameters change, synchronise ``stream``
+    once; make such a call before any stream capture."""
+    prm = make_params(params)
+    b = _device_batch(dev, n_steps, burn_in, seed, index_base, n_max_hint)
+    st = None if stream is None else int(stream.cuda_stream)
+    _check(load().fsmp_run_device_noalloc(ctypes.byref(prm), ctypes.byref(b), st), "fsmp_run_device_noalloc")
 
 
 def summaries_from_bytes(buf) -> np.ndarray:
