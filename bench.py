@@ -68,6 +68,8 @@ def shard_workload(args, rank):
     from paper_2403_03156_gb300 import workloads
     wl = workloads.make_workload(args.workload, n_waveforms=args.n_waveforms or None,
                                  seed=args.seed + 1000 * rank, n_steps=args.mcmc_steps or None)
+    # burn-in of one fifth of the chain for the posterior summaries (it costs the same steps)
+    wl["batch"]["burn_in"] = int(wl["batch"]["n_steps"]) // 5
     b = wl["batch"]
     W = len(b["offsets"]) - 1
     # RNG ids unique across ranks: rank r owns waveforms [r W, (r+1) W) of the job
