@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--mcmc-steps", type=int, default=0, help="override MCMC steps per chain (testing)")
     ap.add_argument("--precision", default="", help="fp32 | fp64 (default: the workload's)")
     ap.add_argument("--threads", type=int, default=0, help="threads per chain CTA (0: library default)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "smem", "global", "plain"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "smem", "global", "plain", "pe"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
@@ -206,14 +206,20 @@ def buckets_of(lengths):
     return out
 
 
-def device_batches(torch, wl, dev, n_smem_max):
-    """Split the workload into length buckets, each a device-resident sub-batch."""
+def device_batches(torch, wl, dev, n_smem_max, one_launch=False):
+    """Split the workload into length buckets, each a device-resident sub-batch (or, for the
+    PE-space kernel, one batch in decreasing window length)."""
     from paper_2403_03156_gb300 import fsmp, workloads
     b = wl["batch"]
     lengths = np.diff(b["offsets"]).astype(np.int64)
     subs = []
-    for idx, nmax in buckets_of(lengths):
-        if nmax > n_smem_max and int(lengths[idx].min()) <= n_smem_max:
+    if one_launch:
+        order = np.argsort(-lengths, kind="stable")
+        groups = [(order, int(lengths.max()))]
+    else:
+        groups = buckets_of(lengths)
+    for idx, nmax in groups:
+        if not one_launch and nmax > n_smem_max and int(lengths[idx].min()) <= n_smem_max:
             # never mix windows on both sides of the shared-memory limit
             big = idx[lengths[idx] > n_smem_max]
             small = idx[lengths[idx] <= n_smem_max]
@@ -270,11 +276,11 @@ def run_ours(args):
     params = dict(wl["params"], precision=prec, refresh_every=wl["meta"].get("refresh_every") or 64,
                   n_max=int(max(lengths.max(), 64)), device=local, threads_per_chain=args.threads,
                   kernel={"auto": fsmp.KERNEL_AUTO, "smem": fsmp.KERNEL_SMEM, "global": fsmp.KERNEL_GLOBAL,
-                          "plain": fsmp.KERNEL_PLAIN}[args.kernel])
+                          "plain": fsmp.KERNEL_PLAIN, "pe": fsmp.KERNEL_PE}[args.kernel])
     ctx = fsmp.Context(params)
     info = ctx.info()
     peaks = ctx.measure_peaks()
-    subs = device_batches(torch, wl, dev, info["n_smem_max"])
+    subs = device_batches(torch, wl, dev, info["n_smem_max"], one_launch=args.kernel == "pe")
     n_steps = int(b["n_steps"])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -343,7 +349,8 @@ def run_ours(args):
                 "traffic": None if tr is None else tr["traffic_bytes_per_launch"] * (
                     (summ[kdom]["prop"].sum() / max(1.0, tr["units_per_launch"])) if tr.get("scale_by_units") else 1.0),
                 "peak_source": "measured live: fsmp_measure_peaks (16-byte shared loads, 4 CTAs/SM)",
-                "kernel": "chain_kernel<%s, smem>, bucket n<=%d (%d chains)" % (
+                "kernel": ("pe_kernel<%s>, one launch, n<=%d (%d chains)" if args.kernel == "pe" else
+                           "chain_kernel<%s, smem>, bucket n<=%d (%d chains)") % (
                     "float" if prec == fsmp.FP32_REFRESH else "double", subs[kdom][1], subs[kdom][2]),
                 "alg_bytes_per_launch": alg_bytes, "launch_ms": float(mean_dur[kdom]),
                 "all_launch_ms": [float(x) for x in mean_dur]}

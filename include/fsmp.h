@@ -64,6 +64,9 @@ extern "C" {
                                    for windows too long for shared memory                   */
 #define FSMP_KERNEL_PLAIN 3     /* baseline: one launch per chain, full n x n FP64 Sigma^-1 in
                                    global memory                                            */
+#define FSMP_KERNEL_PE 4        /* persistent kernel, one warp per chain, state in PE space:
+                                   the N x N inverse of C = (sigma_eps^2/sigma_q^2) I + A^T A
+                                   (Woodbury on all of A), O(N^2) per accepted move          */
 
 typedef struct fsmp_ctx fsmp_ctx;
 
@@ -97,11 +100,14 @@ typedef struct {
   int refresh_every;       /* K accepted moves between FP64 refreshes (FP32 mode)            */
   double drift_tol;        /* relative refresh drift that sets FSMP_ST_DRIFT (0: 5e-2)       */
   int kernel;              /* FSMP_KERNEL_*                                                  */
-  int threads_per_chain;   /* CTA size: 0 = autotuned, else 64..1024, a multiple of 32       */
+  int threads_per_chain;   /* CTA size: 0 = autotuned, else 32..512, a multiple of 32; with
+                              FSMP_KERNEL_PE each warp of the CTA runs its own chain        */
   size_t device_mem_budget;/* bytes the serving loop may hold for admitted requests (0: 4 GiB) */
   int device;              /* CUDA device ordinal                                            */
   int max_queued;          /* submit queue depth before FSMP_ERR_BUSY (0: 1024)              */
   int n_streams;           /* concurrent launch streams of the serving loop (0: 4)           */
+  int pe_tile;             /* FSMP_KERNEL_PE: PEs per chain whose C^-1 stays in shared memory
+                              (0: autotuned); a chain moves C^-1 to global memory beyond it */
 } fsmp_params;
 
 /* One waveform's posterior summaries (after burn_in steps). t0 is in absolute ns.

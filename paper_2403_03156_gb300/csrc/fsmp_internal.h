@@ -37,7 +37,14 @@ struct DevModel {
   const float* phi32;         // FP32 copies of the three phi tables (FP32 mode)
   const float* logphi32;
   const float* cphi32;
+  // SER cross-correlation prefix sums [R][tcM][2 Lt - 1] (the PE-space kernel; may be null)
+  const double* tc64;
+  const float* tc32;
+  int tcM;                    // rows per phase: ceil(Lt / R) + 1
 };
+
+// Rows per phase of the cross-correlation table: prefix lengths 0 .. ceil(Lt / R).
+FSMP_HD int xcorr_rows(int Lt, int R) { return (Lt + R - 1) / R + 1; }
 
 // One launch's chains. Waveform i of the view is samples[offsets[i] .. offsets[i+1]).
 // Optional per-waveform arrays override the batch-wide scalars.
@@ -89,6 +96,7 @@ FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x
 cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double* V64, float* V32,
                           double* phi, double* logphi, double* cphi, float* phi32, float* logphi32,
                           float* cphi32, int* Lt_out_dev, double* scan_buf, cudaStream_t st);
+cudaError_t launch_xcorr_table(const double* V64, int Lt, int R, double* tc64, float* tc32, cudaStream_t st);
 cudaError_t launch_philox(const uint64_t* ctrs, uint64_t* out, int n, uint64_t k0, uint64_t k1,
                           cudaStream_t st);
 
@@ -109,6 +117,17 @@ cudaError_t chain_kernel_attributes(int precision, bool sigma_in_smem, int max_s
 // Resident CTAs per SM of the chain kernel for this block size and dynamic shared memory.
 int chain_kernel_occupancy(int precision, bool sigma_in_smem, int threads, size_t smem);
 cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, double* fp32_tflops);
+// PE-space kernel (fsmp_pe.cu): one warp per chain. Shared memory per CTA of `warps` chains with
+// windows up to n_alloc and a Ns x Ns shared tile of C^-1; FP64 workspace doubles per warp slot
+// (FP32 mode); row stride of a global C^-1 slot.
+size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns);
+size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
+int pe_ldc(int n_cap);
+cudaError_t pe_kernel_attributes(int precision, int max_smem);
+int pe_kernel_occupancy(int precision, int threads, size_t smem);
+// counter: one int of device memory, zeroed on `st` before the launch.
+cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas, int Ns, size_t smem, void* cinv,
+                      size_t c_stride, double* ws, size_t ws_stride, int* counter, cudaStream_t st);
 // Set (or, with what == nullptr, clear) the calling thread's fsmp_last_error() message.
 void record_error(const char* what, const char* detail);
 

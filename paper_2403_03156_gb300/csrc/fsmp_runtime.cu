@@ -95,6 +95,18 @@ struct fsmp_ctx {
   size_t gscratch_bytes = 0;
   int gscratch_ctas = 0;
   LaunchShape shape_smem{256, 0, 0}, shape_gmem{256, 0, 0};
+  // PE-space kernel: SER cross-correlation tables and one scratch set per launch stream (the
+  // serving streams, then one for fsmp_run_device), each with slots for every resident warp
+  double* tc64 = nullptr;
+  float* tc32 = nullptr;
+  struct PeSet {
+    void* cinv = nullptr;    // C^-1 slots
+    double* ws = nullptr;    // FP64 refresh workspace slots
+    int* counter = nullptr;  // chain counter of the launch
+  };
+  std::vector<PeSet> pe_sets;
+  int pe_slots = 0, pe_warps = 4, pe_tile = 0;
+  size_t pe_c_stride = 0, pe_ws_stride = 0, pe_bytes = 0;
   // serving loop
   std::vector<cudaStream_t> streams;
   cudaStream_t gmem_stream = nullptr;
@@ -164,7 +176,8 @@ int validate_params(const fsmp_params* p) {
   if (!(p->jump_J > 0) || !(p->jump_J <= 0.5)) return FSMP_ERR_INVALID;
   if (p->n_cap < 1 || p->n_cap > 4096 || p->n_max < 1 || p->n_max > 8192) return FSMP_ERR_INVALID;
   if (p->precision != FSMP_FP64 && p->precision != FSMP_FP32_REFRESH) return FSMP_ERR_INVALID;
-  if (p->kernel < 0 || p->kernel > 3) return FSMP_ERR_INVALID;
+  if (p->kernel < 0 || p->kernel > 4) return FSMP_ERR_INVALID;
+  if (p->pe_tile < 0 || p->pe_tile > 128) return FSMP_ERR_INVALID;
   if (p->threads_per_chain != 0 && (p->threads_per_chain < 32 || p->threads_per_chain > 512 ||
                                     p->threads_per_chain % 32))
     return FSMP_ERR_INVALID;
@@ -177,6 +190,8 @@ void free_ctx(fsmp_ctx* c) {
   cudaFree(c->V64); cudaFree(c->V32); cudaFree(c->phi); cudaFree(c->logphi); cudaFree(c->cphi);
   cudaFree(c->scan); cudaFree(c->Lt_dev); cudaFree(c->gscratch);
   cudaFree(c->phi32); cudaFree(c->logphi32); cudaFree(c->cphi32); cudaFree(c->rscratch);
+  cudaFree(c->tc64); cudaFree(c->tc32);
+  for (auto& ps : c->pe_sets) { cudaFree(ps.cinv); cudaFree(ps.ws); cudaFree(ps.counter); }
   for (auto s : c->streams) cudaStreamDestroy(s);
   if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
   delete c;
@@ -193,9 +208,36 @@ void CUDART_CB pack_done_cb(void* arg) {
 }
 
 // ---- device batch from arrays already on the device
-int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st) {
+// Launch shape of the PE-space kernel for windows up to n_alloc: warps (chains) per CTA, the
+// shared tile of C^-1, and resident CTAs per SM from the hardware's occupancy rule.
+int pe_shape(fsmp_ctx* c, int n_alloc, int* ctas, size_t* smem) {
+  *smem = pe_smem_bytes(c->M, n_alloc, c->pe_warps, c->pe_tile);
+  if (*smem > (size_t)c->prop.sharedMemPerBlockOptin) return FSMP_ERR_INVALID;
+  const int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem);
+  if (per_sm < 1) return FSMP_ERR_INVALID;
+  *ctas = per_sm * c->prop.multiProcessorCount;
+  return FSMP_OK;
+}
+
+int run_pe(fsmp_ctx* c, BatchView B, int set, cudaStream_t st) {
+  if (c->pe_sets.empty()) FAIL(FSMP_ERR_INVALID, "the PE-space kernel was not set up at fsmp_create");
+  if (B.n_max > c->p.n_max) FAIL(FSMP_ERR_INVALID, "window longer than n_max");
+  int ctas = 0;
+  size_t smem = 0;
+  if (pe_shape(c, B.n_max, &ctas, &smem) != FSMP_OK) FAIL(FSMP_ERR_INVALID, "window too long for the PE-space kernel");
+  ctas = std::min(ctas, c->pe_slots / c->pe_warps);
+  ctas = std::min(ctas, (B.n_waveforms + c->pe_warps - 1) / c->pe_warps);
+  const fsmp_ctx::PeSet& ps = c->pe_sets[set];
+  cudaError_t e = launch_pe(c->M, B, c->pe_warps, ctas, c->pe_tile, smem, ps.cinv, c->pe_c_stride, ps.ws,
+                            c->pe_ws_stride, ps.counter, st);
+  if (e != cudaSuccess) { set_error("launch_pe", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
+  return FSMP_OK;
+}
+
+int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st, int set) {
   if (B.n_waveforms <= 0) return FSMP_OK;
   int form = c->p.kernel;
+  if (form == FSMP_KERNEL_PE) return run_pe(c, B, set, st);
   if (form == FSMP_KERNEL_AUTO) form = B.n_max <= c->n_smem_max ? FSMP_KERNEL_SMEM : FSMP_KERNEL_GLOBAL;
   if (form == FSMP_KERNEL_SMEM && B.n_max > c->n_smem_max) form = FSMP_KERNEL_GLOBAL;
   if (form == FSMP_KERNEL_PLAIN) {
@@ -256,9 +298,15 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st) {
 // own persistent launch sized for its longest window, so short windows run with a small
 // shared-memory footprint and more CTAs per SM.
 int run_bucketed(fsmp_ctx* c, BatchView B, const int32_t* order_dev, const std::vector<int>& n_sorted,
-                 cudaStream_t st) {
+                 cudaStream_t st, int set) {
   static const int kEdges[] = {64, 96, 128, 160, 192, 224, 256, 320, 384, 512, 768, 1024, 2048, 8192};
   const int W = (int)n_sorted.size();
+  if (c->p.kernel == FSMP_KERNEL_PE) {  // one launch: warps take chains longest first
+    BatchView b = B;
+    b.order = order_dev;
+    b.n_max = W > 0 ? n_sorted[0] : 1;
+    return run_view(c, b, st, set);
+  }
   int i = 0;
   while (i < W) {
     const int nmax = n_sorted[i];
@@ -272,7 +320,7 @@ int run_bucketed(fsmp_ctx* c, BatchView B, const int32_t* order_dev, const std::
     b.order = order_dev + i;
     b.n_waveforms = j - i;
     b.n_max = nmax;
-    int rc = run_view(c, b, st);
+    int rc = run_view(c, b, st, set);
     if (rc) return rc;
     i = j;
   }
@@ -376,9 +424,12 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
     return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
   });
   for (int i = 0; i < W; ++i) n_sorted[i] = offsets[order[i] + 1] - offsets[order[i]];
-  // packs that use the global-memory Sigma^-1 scratch share it, so they run on one stream
-  const bool uses_scratch = n_max > c->n_smem_max || c->p.kernel == FSMP_KERNEL_GLOBAL ||
-                            c->p.kernel == FSMP_KERNEL_PLAIN;
+  // packs of the Sigma^-1 kernels that use context scratch (global Sigma^-1, or the FP32-mode
+  // refresh workspace) share it, so they run on one stream; the PE-space kernel has a scratch
+  // set per stream
+  const bool uses_scratch = c->p.kernel != FSMP_KERNEL_PE &&
+                            (n_max > c->n_smem_max || c->p.kernel == FSMP_KERNEL_GLOBAL ||
+                             c->p.kernel == FSMP_KERNEL_PLAIN || c->p.precision != FSMP_FP64);
   cudaStream_t st = uses_scratch ? c->gmem_stream : c->streams[pk->stream];
   pk->stream = uses_scratch ? -1 : pk->stream;
   { cudaError_t e_ = cudaMallocAsync(&pk->dev, L.total, st); if (e_ != cudaSuccess) { set_error("cudaMallocAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
@@ -403,7 +454,8 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   B.trace_off = n_trace ? (const int64_t*)(d + L.trace_off) : nullptr;
   B.out = (fsmp_summary*)(d + L.out);
   B.trace = n_trace ? (fsmp_trace*)(d + L.trace) : nullptr;
-  int rc = run_bucketed(c, B, (const int32_t*)(d + L.order), n_sorted, st);
+  int rc = run_bucketed(c, B, (const int32_t*)(d + L.order), n_sorted, st,
+                        pk->stream < 0 ? (int)c->streams.size() : pk->stream);
   if (rc) return rc;
   if (cudaMemcpyAsync(h + L.out, d + L.out, L.total - L.out, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return FSMP_ERR_CUDA;
@@ -632,6 +684,15 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   if (M.LU > 128) FAIL(FSMP_ERR_INVALID, "SER support above 117 samples is not supported");
   M.V64 = c->V64; M.V32 = c->V32; M.phi = c->phi; M.logphi = c->logphi; M.cphi = c->cphi;
   M.phi32 = c->phi32; M.logphi32 = c->logphi32; M.cphi32 = c->cphi32;
+  // SER cross-correlation prefix sums for the PE-space kernel
+  {
+    const size_t ntc = (size_t)M.R * xcorr_rows(M.Lt, M.R) * (2 * M.Lt - 1);
+    CK(cudaMalloc(&c->tc64, sizeof(double) * ntc));
+    CK(cudaMalloc(&c->tc32, sizeof(float) * ntc));
+    CK(launch_xcorr_table(c->V64, M.Lt, M.R, c->tc64, c->tc32, 0));
+    CK(cudaDeviceSynchronize());
+    M.tc64 = c->tc64; M.tc32 = c->tc32; M.tcM = xcorr_rows(M.Lt, M.R);
+  }
   c->n_smem_max = smem_n_max(c.get());
   int max_smem = (int)c->prop.sharedMemPerBlockOptin;
   CK(chain_kernel_attributes(p.precision, true, max_smem));
@@ -660,6 +721,34 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     c->rscratch_stride = (chain_refresh_bytes(p.n_cap, p.n_max) + 255) / 256 * 256;
     if (cudaMalloc(&c->rscratch, c->rscratch_stride * (size_t)slots) != cudaSuccess)
       FAIL(FSMP_ERR_NOMEM, "refresh workspace allocation failed");
+  }
+  // PE-space kernel: per-warp slots of C^-1 (when the shared tile can overflow) and of the FP64
+  // refresh workspace (FP32 mode), one set per launch stream
+  if (p.kernel == FSMP_KERNEL_PE) {
+    c->pe_warps = p.threads_per_chain > 0 ? p.threads_per_chain / 32 : 4;
+    const size_t esz = 8;  // C^-1 is FP64 in both modes
+    c->pe_tile = p.pe_tile > 0 ? std::min(p.pe_tile, p.n_cap) : std::min(p.n_cap, 24);
+    CK(pe_kernel_attributes(p.precision, max_smem));
+    int slots = 0;
+    for (int nn : {std::min(64, p.n_max), p.n_max}) {
+      int ctas = 0;
+      size_t sm = 0;
+      if (pe_shape(c.get(), nn, &ctas, &sm) == FSMP_OK) slots = std::max(slots, ctas * c->pe_warps);
+    }
+    if (slots < 1) FAIL(FSMP_ERR_INVALID, "n_max too large for the PE-space kernel");
+    c->pe_slots = slots;
+    const int ldc = pe_ldc(p.n_cap);
+    c->pe_c_stride = c->pe_tile < p.n_cap ? (size_t)p.n_cap * ldc : 0;
+    c->pe_ws_stride = p.precision == FSMP_FP64 ? 0 : pe_ws_slot_doubles(p.n_cap, p.n_max);
+    for (int i = 0; i <= p.n_streams; ++i) {
+      fsmp_ctx::PeSet ps;
+      const size_t cb = c->pe_c_stride * esz * (size_t)slots, wb = c->pe_ws_stride * 8 * (size_t)slots;
+      if (cb && cudaMalloc(&ps.cinv, cb) != cudaSuccess) FAIL(FSMP_ERR_NOMEM, "PE-space C^-1 slots");
+      if (wb && cudaMalloc((void**)&ps.ws, wb) != cudaSuccess) FAIL(FSMP_ERR_NOMEM, "PE-space refresh workspace");
+      CK(cudaMalloc((void**)&ps.counter, sizeof(int)));
+      c->pe_bytes += cb + wb + sizeof(int);
+      c->pe_sets.push_back(ps);
+    }
   }
   for (int i = 0; i < p.n_streams; ++i) {
     cudaStream_t s;
@@ -753,7 +842,7 @@ int fsmp_run_device(fsmp_ctx* c, const fsmp_device_batch* b, void* stream) {
   B.T_lo = b->T_lo; B.T_hi = b->T_hi; B.t0_init = b->t0_init; B.wf_ids = b->wf_ids;
   B.out = b->out; B.trace = b->trace;
   { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
-  return run_view(c, B, (cudaStream_t)stream);
+  return run_view(c, B, (cudaStream_t)stream, (int)c->streams.size());
 }
 
 int fsmp_get_tables(fsmp_ctx* c, double* ser_out, int max_ser, int* ser_len, int d_lo, int count,
@@ -788,7 +877,7 @@ int fsmp_get_info(fsmp_ctx* c, fsmp_info* o) {
     o->threads_per_chain = s.threads;
     o->ctas_per_sm = s.ctas / c->prop.multiProcessorCount;
   }
-  o->scratch_bytes = c->gscratch_bytes + c->rscratch_stride * (size_t)c->rscratch_slots;
+  o->scratch_bytes = c->gscratch_bytes + c->rscratch_stride * (size_t)c->rscratch_slots + c->pe_bytes;
   snprintf(o->name, sizeof(o->name), "%.63s", c->prop.name);
   return FSMP_OK;
 }

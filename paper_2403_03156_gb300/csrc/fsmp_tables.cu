@@ -168,7 +168,38 @@ __global__ void philox_kernel(const uint64_t* ctrs, uint64_t* out, int n, uint64
   for (int k = 0; k < 4; ++k) out[4 * i + k] = c[k];
 }
 
+// Prefix sums of SER cross-correlations on the PE grid. For a PE whose first sample sits at
+// phase ph (the grid distance from the PE to that sample, 0 <= ph < R) and a second PE o grid
+// points earlier:
+//   tc[ph][m][o + Lt - 1] = sum_{i < m} V[ph + i R] V[ph + i R + o],  V = 0 outside [0, Lt).
+// The inner product of the two PEs' columns over the samples i in [ilo, ihi) of the first one's
+// support is then tc[.][ihi][.] - tc[.][ilo][.]; with o = 0 it is the squared norm. One thread per
+// (ph, o), FP64 running sums.
+__global__ void xcorr_table_kernel(const double* V, int Lt, int R, int M1, double* tc) {
+  const int O = 2 * Lt - 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= R * O) return;
+  const int ph = t / O, oi = t - ph * O, o = oi - (Lt - 1);
+  double acc = 0.0;
+  for (int m = 0; m < M1; ++m) {
+    tc[((size_t)ph * M1 + m) * O + oi] = acc;
+    const int a = ph + m * R, b = a + o;
+    if (a < Lt && b >= 0 && b < Lt) acc += V[a] * V[b];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_xcorr_table(const double* V64, int Lt, int R, double* tc64, float* tc32, cudaStream_t st) {
+  const int M1 = xcorr_rows(Lt, R);
+  const int n = R * (2 * Lt - 1);
+  xcorr_table_kernel<<<(n + 127) / 128, 128, 0, st>>>(V64, Lt, R, M1, tc64);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int tot = n * M1;
+  to_float_kernel<<<(tot + 255) / 256, 256, 0, st>>>(tc64, tc32, tot);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double* V64, float* V32,
                           double* phi, double* logphi, double* cphi, float* phi32, float* logphi32,

@@ -17,7 +17,7 @@ from . import build as _build
 OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_BUSY, ERR_TIMEOUT, ERR_CLOSED = 0, -1, -2, -3, -4, -5, -6
 ST_CAPACITY, ST_BADDET, ST_DRIFT, ST_INVALID, ST_NONFINITE = 1, 2, 4, 8, 16
 FP64, FP32_REFRESH = 0, 1
-KERNEL_AUTO, KERNEL_SMEM, KERNEL_GLOBAL, KERNEL_PLAIN = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SMEM, KERNEL_GLOBAL, KERNEL_PLAIN, KERNEL_PE = 0, 1, 2, 3, 4
 
 SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"),
                           ("var_t0", "<f8"), ("mean_Q", "<f8"), ("var_Q", "<f8"),
@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
                 ("n_cap", _c_int), ("n_max", _c_int), ("precision", _c_int),
                 ("refresh_every", _c_int), ("drift_tol", _c_double), ("kernel", _c_int),
                 ("threads_per_chain", _c_int), ("device_mem_budget", ctypes.c_size_t),
-                ("device", _c_int), ("max_queued", _c_int), ("n_streams", _c_int)]
+                ("device", _c_int), ("max_queued", _c_int), ("n_streams", _c_int),
+                ("pe_tile", _c_int)]
 
 
 class Batch(ctypes.Structure):
@@ -142,7 +143,7 @@ _PARAM_DEFAULTS = dict(dt_sample_ns=1.0, grid_ns=0.25, ser_kind=0, ser_sigma=1.5
                        sigma_q=0.3, sigma_noise=0.06, t0_lo=30.0, t0_hi=40.0, sample_t0=1,
                        jump_J=0.25, n_cap=32, n_max=1024, precision=FP64, refresh_every=64,
                        drift_tol=0.0, kernel=KERNEL_AUTO, threads_per_chain=0,
-                       device_mem_budget=0, device=0, max_queued=0, n_streams=0)
+                       device_mem_budget=0, device=0, max_queued=0, n_streams=0, pe_tile=0)
 
 
 def make_params(d: dict | None = None, **kw) -> Params:

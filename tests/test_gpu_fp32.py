@@ -43,14 +43,18 @@ def _params(wl, **kw):
     return dict(wl["params"], n_max=max(64, n_max), precision=fsmp.FP32_REFRESH, **kw)
 
 
+KERNELS = [pytest.param(fsmp.KERNEL_AUTO, id="sigma"), pytest.param(fsmp.KERNEL_PE, id="pe")]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("refresh_every", [1, 64])
-def test_fp32_tracks_oracle_step_by_step(lib, orc, refresh_every):
+def test_fp32_tracks_oracle_step_by_step(lib, orc, refresh_every, kernel):
     """With a refresh after every accepted move the FP32 state is rebuilt in FP64 each time,
     so the log acceptance ratios must match the FP64 oracle to FP32 rounding; with K = 64 the
     incremental FP32 drift between refreshes stays small."""
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=96, n_steps=600, seed=3)
     b = wl["batch"]
-    with fsmp.Context(_params(wl, refresh_every=refresh_every)) as ctx:
+    with fsmp.Context(_params(wl, refresh_every=refresh_every, kernel=kernel)) as ctx:
         s_gpu, t_gpu = ctx.run(b, record_trace=True)
     s_orc, t_orc = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16, trace=True)
     pref = _lockstep_prefix(t_gpu, t_orc)
@@ -79,13 +83,14 @@ def test_fp32_tracks_oracle_step_by_step(lib, orc, refresh_every):
     np.testing.assert_allclose(s_gpu["logdet"][full], s_orc["logdet"][full], rtol=1e-9, atol=1e-8)
 
 
-def test_fp32_summaries_match_oracle_statistically(lib, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_summaries_match_oracle_statistically(lib, orc, kernel):
     """Posterior N, charge and t0 summaries over 384 waveforms of the uneven-window workload
     (2000 steps, burn-in 400): the mean paired difference GPU - oracle is within 3 standard
     errors (and each summary's differences are centred)."""
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=384, n_steps=2000, seed=11, burn_in=400)
     b = wl["batch"]
-    with fsmp.Context(_params(wl, refresh_every=64)) as ctx:
+    with fsmp.Context(_params(wl, refresh_every=64, kernel=kernel)) as ctx:
         s_gpu, _ = ctx.run(b)
     s_orc, _ = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16)
     for f in ("mean_N", "mean_Q", "mean_t0"):

@@ -53,7 +53,7 @@ def _oracle_trace(orc, params, batch, threads=16):
     return s, t
 
 
-@pytest.mark.parametrize("kernel", [fsmp.KERNEL_SMEM, fsmp.KERNEL_GLOBAL])
+@pytest.mark.parametrize("kernel", [fsmp.KERNEL_SMEM, fsmp.KERNEL_GLOBAL, fsmp.KERNEL_PE])
 def test_lockstep_fp64_config1(lib, orc, kernel):
     """Config 1 (256 x 128 samples, lambda 2, 1000 steps): every log acceptance ratio to 1e-9
     relative, identical decisions and summaries."""
