@@ -23,6 +23,7 @@ struct DevModel {
   int LU;                     // longest union support of a two-PE jump (samples)
   int win_extra;              // phi window per chain: n R + win_extra grid offsets (t0 range + 2)
   double mu_q, sigma_q, sq2, se2, inv_se2;
+  double log_se2, log_r;       // log sigma_eps^2 and log(sigma_eps^2 / sigma_q^2)
   double t0_lo, t0_hi;
   int sample_t0;
   double J, log_J;
@@ -40,6 +41,7 @@ struct DevModel {
   // SER cross-correlation prefix sums [R][tcM][2 Lt - 1] (the PE-space kernel; may be null)
   const double* tc64;
   const float* tc32;
+  const float* tcff;          // float-float pairs (hi, lo) of tc64
   int tcM;                    // rows per phase: ceil(Lt / R) + 1
 };
 
@@ -124,6 +126,7 @@ size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns);
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
 int pe_ldc(int n_cap);
 cudaError_t pe_kernel_attributes(int precision, int max_smem);
+cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st);
 int pe_kernel_occupancy(int precision, int threads, size_t smem);
 // counter: one int of device memory, zeroed on `st` before the launch.
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas, int Ns, size_t smem, void* cinv,

@@ -20,13 +20,15 @@
 // launch-wide counter. C^-1 sits in a per-warp shared-memory tile of Ns x Ns while N <= Ns and
 // moves to the warp's global slot (n_cap x ldc) when a birth would exceed the tile.
 //
-// Precision: C^-1, v and b are FP64 in both modes. For PEs close in time C is nearly singular
-// (eigenvalues down to r) and C^-1 holds entries near 1/r that cancel in b^T C^-1 b; stored in
-// FP32 they cost about 1e-2 in log alpha per step. In FP32 mode the residual y, the SER and phi
-// tables, the random draws and the 2x2 algebra are FP32, and C^-1, v, y, log|Sigma| and the
-// log-likelihood are rebuilt from z in FP64 (Gauss-Jordan inversion of C, which is symmetric
-// positive definite) every refresh_every accepted moves and at the end. Per step the random
-// draws, proposal rules and acceptance tests are those of the Sigma^-1 kernel.
+// Precision. For PEs close in time C is nearly singular (eigenvalues down to r) and C^-1 holds
+// entries near 1/r that cancel in b^T C^-1 b; stored in FP32 they cost about 1e-2 in log alpha per
+// step. C^-1, v and b therefore carry about 48 significant bits: FP64 in FP64 mode, and in FP32
+// mode float-float pairs (hi + lo, Dekker's exact product and Knuth's TwoSum) that run on the FP32
+// pipe -- an FP64 instruction costs this part as much as 64 FP32 ones. In FP32 mode the residual y,
+// the SER and phi tables, the random draws and the 2x2 algebra are FP32, and C^-1, v, y, log|Sigma|
+// and the log-likelihood are rebuilt from z in FP64 (Gauss-Jordan inversion of C, which is
+// symmetric positive definite) every refresh_every accepted moves and at the end. Per step the
+// random draws, proposal rules and acceptance tests are those of the Sigma^-1 kernel.
 #include <math.h>
 
 #include "fsmp_internal.h"
@@ -35,20 +37,120 @@ namespace fsmp {
 namespace {
 
 constexpr int kPeRB = 32;  // steps per batch of random draws
+constexpr int kPeMaxThreads = 128;  // chains (warps) per CTA: at most 4
 constexpr unsigned kFull = 0xffffffffu;
 
+// ---------------------------------------------------------------- float-float arithmetic
+// A value hi + lo with |lo| <= ulp(hi) / 2. TwoSum (Knuth) and the FMA-based exact product
+// (Dekker) give the rounding error of one FP32 operation exactly; the pair operations below are
+// the usual "sloppy" double-float forms (relative error about 2^-44).
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_quick(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+  return ff_quick(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return ff_quick(p, e);
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+
+// The state arithmetic for both modes: C = double (FP64 mode) or ff (FP32 mode).
+__device__ __forceinline__ double cadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double csub(double a, double b) { return a - b; }
+__device__ __forceinline__ double cmul(double a, double b) { return a * b; }
+__device__ __forceinline__ double cfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double cneg(double a) { return -a; }
+__device__ __forceinline__ double crcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ double cnum(double a) { return a; }   // to the scoring precision
+__device__ __forceinline__ double c64(double a) { return a; }    // to FP64
+__device__ __forceinline__ bool cnz(double a) { return a != 0.0; }
+__device__ __forceinline__ double cshfl_xor(double a, int o) { return __shfl_xor_sync(kFull, a, o); }
+__device__ __forceinline__ double cshfl(double a, int src) { return __shfl_sync(kFull, a, src); }
+__device__ __forceinline__ double cfromf(double a) { return a; }
+template <typename C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ double czero<double>() { return 0.0; }
+
+__device__ __forceinline__ ff cadd(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ ff csub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff cmul(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ ff cfma(ff a, ff b, ff c) { return ff_add(ff_mul(a, b), c); }
+__device__ __forceinline__ ff cneg(ff a) { return ff_neg(a); }
+__device__ __forceinline__ ff crcp(ff a) {  // one Newton step on the FP32 reciprocal
+  const float r = __frcp_rn(a.hi);
+  const ff e = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul(a, ff{r, 0.0f})));
+  return ff_add(ff{r, 0.0f}, ff_mul(e, ff{r, 0.0f}));
+}
+__device__ __forceinline__ float cnum(ff a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ double c64(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ bool cnz(ff a) { return a.hi != 0.0f; }
+__device__ __forceinline__ ff cshfl_xor(ff a, int o) {
+  return ff{__shfl_xor_sync(kFull, a.hi, o), __shfl_xor_sync(kFull, a.lo, o)};
+}
+__device__ __forceinline__ ff cshfl(ff a, int src) {
+  return ff{__shfl_sync(kFull, a.hi, src), __shfl_sync(kFull, a.lo, src)};
+}
+__device__ __forceinline__ ff cfromf(float a) { return ff{a, 0.0f}; }
+template <> __device__ __forceinline__ ff czero<ff>() { return ff{0.0f, 0.0f}; }
+// FP64 -> state value (refresh only)
+template <typename C> __device__ __forceinline__ C cfrom64(double a);
+template <> __device__ __forceinline__ double cfrom64<double>(double a) { return a; }
+template <> __device__ __forceinline__ ff cfrom64<ff>(double a) {
+  const float h = (float)a;
+  return ff{h, (float)(a - (double)h)};
+}
+// a model constant as a state value
+template <typename C> __device__ __forceinline__ C cconst(double a) { return cfrom64<C>(a); }
+
+// warp sums of state values: over all lanes, or over lanes [0, m) (zero beyond m)
+template <typename C> __device__ __forceinline__ C csum(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = cadd(v, cshfl_xor(v, o));
+  return v;
+}
+template <typename C> __device__ __forceinline__ C csum_first(C v, int m) {
+  for (int o = 16; o > 0; o >>= 1)
+    if (o < m) v = cadd(v, cshfl_xor(v, o));
+  return cshfl(v, 0);
+}
+
+template <typename T> __device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T wmax(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------- model tables
 template <typename T> struct PeTab;
 template <> struct PeTab<double> {
+  using C = double;
   __device__ static const double* V(const DevModel& M) { return M.V64; }
   __device__ static const double* logphi(const DevModel& M) { return M.logphi; }
   __device__ static const double* cphi(const DevModel& M) { return M.cphi; }
   __device__ static const double* tc(const DevModel& M) { return M.tc64; }
 };
 template <> struct PeTab<float> {
+  using C = ff;
   __device__ static const float* V(const DevModel& M) { return M.V32; }
   __device__ static const float* logphi(const DevModel& M) { return M.logphi32; }
   __device__ static const float* cphi(const DevModel& M) { return M.cphi32; }
-  __device__ static const float* tc(const DevModel& M) { return M.tc32; }
+  __device__ static const ff* tc(const DevModel& M) { return reinterpret_cast<const ff*>(M.tcff); }
 };
 
 template <typename T> __device__ __forceinline__ T pe_logphi(const DevModel& M, int d) {
@@ -58,24 +160,6 @@ template <typename T> __device__ __forceinline__ T pe_cphi(const DevModel& M, in
   if (d < -M.D) return (T)0;
   if (d > M.D) return __ldg(PeTab<T>::cphi(M) + 2 * M.D);
   return __ldg(PeTab<T>::cphi(M) + (d + M.D));
-}
-
-template <typename T> __device__ __forceinline__ T wsum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-// Sum over lanes [0, m) of values that are zero on lanes >= m (1 <= m <= 32); every lane of
-// [0, next power of two >= m) gets the sum.
-__device__ __forceinline__ double wsum_first(double v, int m) {
-  for (int o = 16; o > 0; o >>= 1)
-    if (o < m) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-template <typename T> __device__ __forceinline__ T wmax(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-  return v;
 }
 
 // Support of the PE at grid index j in a window of n samples: its first sample w0 = ceil(j / R),
@@ -96,11 +180,11 @@ __device__ __forceinline__ Sup pe_sup(const DevModel& M, int n, int j) {
 }
 
 // a_x^T a_q over the window, for x with support s and q = x - o (|o| < Lt), from the prefix table.
-template <typename T> __device__ __forceinline__ T xcorr(const DevModel& M, const T* __restrict__ tc, const Sup& s, int o) {
+template <typename C> __device__ __forceinline__ C xcorr(const DevModel& M, const C* __restrict__ tc, const Sup& s, int o) {
   const int O = 2 * M.Lt - 1;
-  const T* base = tc + (size_t)s.ph * M.tcM * O + (o + M.Lt - 1);
-  T v = __ldg(base + (size_t)s.ihi * O);
-  if (s.ilo > 0) v -= __ldg(base + (size_t)s.ilo * O);
+  const C* base = tc + (size_t)s.ph * M.tcM * O + (o + M.Lt - 1);
+  C v = base[(size_t)s.ihi * O];
+  if (s.ilo > 0) v = csub(v, base[(size_t)s.ilo * O]);
   return v;
 }
 
@@ -137,6 +221,12 @@ template <typename T> struct PeRand {
   T z1, lu0, u3, u4, z2, lu;  // t0 shift normal, log u2, jump type, PE choice, shift normal, log u7
 };
 
+// FP32 value of the uniform ((x >> 11) + 0.5) 2^-53: the odd 54-bit integer 2 (x >> 11) + 1
+// rounded to FP32, times 2^-54 (exact), i.e. the FP64 uniform rounded to FP32 without FP64 work.
+__device__ __forceinline__ float u01_float(uint64_t x) {
+  return __ull2float_rn(((x >> 11) << 1) | 1ull) * 0x1.0p-54f;
+}
+
 // Per-chain statistics (shared memory, written by lane 0).
 struct PeStats {
   long long sN, sN2, sK, sK2;
@@ -147,52 +237,51 @@ struct PeStats {
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Per-warp shared memory.
+// Per-warp shared memory. C is the state type (8 bytes in both modes).
 template <typename T> struct PeWarp {
+  using C = typename PeTab<T>::C;
   PeStats* st;
   PeRand<T>* rnd;
   int* list;   // PE grid indices [n_cap]
   int* ovi;    // PEs overlapping the proposed one [n_cap]
-  double* ovb; // their inner products with it [n_cap]
-  double* v;   // C^-1 A^T y [n_cap]
-  T* vT;       // v at the scoring precision [n_cap]
-  double* cv;  // row k of C^-1 / C^-1 b [n_cap]
-  double* uv;  // second work vector [n_cap]
+  C* ovb;      // their inner products with it [n_cap]
+  C* v;        // C^-1 A^T y [n_cap]
+  C* cv;       // row k of C^-1 / C^-1 b [n_cap]
+  C* uv;       // second work vector [n_cap]
   T* y;        // residual [n_alloc]
   T* lPhi;     // log(Phi_T(t0) g) on the chain's t0 grid [win_extra]
-  double* Cs;  // C^-1 tile [Ns * Ns]
+  C* Cs;       // C^-1 tile [Ns * Ns]
 };
 template <typename T> __host__ __device__ inline size_t pe_warp_bytes(int n_cap, int n_alloc, int win_extra, int Ns) {
   return a16(sizeof(PeStats)) + a16(sizeof(PeRand<T>) * kPeRB) + 2 * a16(sizeof(int) * n_cap) +
-         4 * a16(sizeof(double) * n_cap) + a16(sizeof(T) * n_cap) + a16(sizeof(T) * n_alloc) +
-         a16(sizeof(T) * win_extra) +
-         a16(sizeof(double) * (size_t)Ns * Ns);
+         4 * a16(8 * (size_t)n_cap) + a16(sizeof(T) * n_alloc) + a16(sizeof(T) * win_extra) +
+         a16(8 * (size_t)Ns * Ns);
 }
 template <typename T> __host__ __device__ inline size_t pe_block_bytes(int Lt, int n_cap) {
   return a16(sizeof(T) * Lt) + a16(sizeof(T) * (n_cap + 2));
 }
 template <typename T> __device__ PeWarp<T> pe_carve(unsigned char* p, int n_cap, int n_alloc, int win_extra, int Ns) {
+  using C = typename PeTab<T>::C;
   PeWarp<T> W;
   size_t o = 0;
   W.st = reinterpret_cast<PeStats*>(p + o); o += a16(sizeof(PeStats));
   W.rnd = reinterpret_cast<PeRand<T>*>(p + o); o += a16(sizeof(PeRand<T>) * kPeRB);
   W.list = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
   W.ovi = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
-  W.ovb = reinterpret_cast<double*>(p + o); o += a16(sizeof(double) * n_cap);
-  W.v = reinterpret_cast<double*>(p + o); o += a16(sizeof(double) * n_cap);
-  W.vT = reinterpret_cast<T*>(p + o); o += a16(sizeof(T) * n_cap);
-  W.cv = reinterpret_cast<double*>(p + o); o += a16(sizeof(double) * n_cap);
-  W.uv = reinterpret_cast<double*>(p + o); o += a16(sizeof(double) * n_cap);
+  W.ovb = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
+  W.v = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
+  W.cv = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
+  W.uv = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
   W.y = reinterpret_cast<T*>(p + o); o += a16(sizeof(T) * n_alloc);
   W.lPhi = reinterpret_cast<T*>(p + o); o += a16(sizeof(T) * win_extra);
-  W.Cs = reinterpret_cast<double*>(p + o);
+  W.Cs = reinterpret_cast<C*>(p + o);
   return W;
 }
 
 // Global per-warp slots.
 struct PeSlots {
-  double* C;           // C^-1 slots: n_cap rows of ldc entries each
-  size_t c_stride;     // elements per slot
+  void* C;             // C^-1 slots (8-byte entries): n_cap rows of ldc entries each
+  size_t c_stride;     // entries per slot
   int ldc;
   double* ws;          // FP64 refresh workspace slots (FP32 mode)
   size_t ws_stride;    // doubles per slot
@@ -216,12 +305,20 @@ __device__ __forceinline__ void close_hold(PeStats& S, int s, int burn_in) {
   }
 }
 
+struct RefreshOut {
+  int ok;
+  double logdet, logL, drift;
+};
+
 // FP64 rebuild of C^-1, v, y, log|Sigma| and the log-likelihood from the PE list (FP32 mode).
-// Returns false (state untouched) if C is not numerically positive definite.
+// ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
+// value (no address of the caller's locals escapes, so they stay in registers).
 template <typename T>
-__device__ __noinline__ bool pe_refresh(const DevModel& M, PeWarp<T>& W, double* Cp, int ld, double* ws, int n_cap, int lvec,
-                           const float* w, int n, int N, int lane, double& logdet_out, double& logL_out,
-                           double& drift_out) {
+__device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T> W, typename PeTab<T>::C* Cp, int ld,
+                                              double* ws, int n_cap, int lvec, const float* w, int n, int N,
+                                              int lane) {
+  using C = typename PeTab<T>::C;
+  RefreshOut out{0, 0.0, 0.0, 0.0};
   const int ws_ld = n_cap;
   double* A = ws;                               // C, then C^-1 (row-major, stride n_cap)
   double* yres = A + (size_t)n_cap * n_cap;     // residual y (FP64)
@@ -231,17 +328,22 @@ __device__ __noinline__ bool pe_refresh(const DevModel& M, PeWarp<T>& W, double*
   const double* V = M.V64;
   const double mu = M.mu_q, r = M.se2 / M.sq2;
   // residual y = w - mu sum_k a_k
+#pragma unroll 1
   for (int x = lane; x < n; x += 32) yres[x] = (double)w[x];
   __syncwarp();
+#pragma unroll 1
   for (int k = 0; k < N; ++k) {
     const Sup s = pe_sup(M, n, W.list[k]);
+#pragma unroll 1
     for (int i = s.ilo + lane; i < s.ihi; i += 32) yres[s.w0 + i] -= mu * V[s.ph + i * M.R];
     __syncwarp();
   }
   // C = r I + A^T A (full, row-major)
+#pragma unroll 1
   for (int i = 0; i < N; ++i) {
     const int ji = W.list[i];
     const Sup si = pe_sup(M, n, ji);
+#pragma unroll 1
     for (int j = lane; j < N; j += 32) {
       const int o = ji - W.list[j];
       double c = (o > -M.Lt && o < M.Lt) ? xcorr<double>(M, M.tc64, si, o) : 0.0;
@@ -250,15 +352,17 @@ __device__ __noinline__ bool pe_refresh(const DevModel& M, PeWarp<T>& W, double*
     }
   }
   // h = A^T y
+#pragma unroll 1
   for (int k = lane; k < N; k += 32) {
     const Sup s = pe_sup(M, n, W.list[k]);
     double a0 = 0.0, a1 = 0.0;
     int i = s.ilo;
+#pragma unroll 1
     for (; i + 1 < s.ihi; i += 2) {
-      a0 += V[s.ph + i * M.R] * yres[s.w0 + i];
-      a1 += V[s.ph + (i + 1) * M.R] * yres[s.w0 + i + 1];
+      a0 = fma(V[s.ph + i * M.R], yres[s.w0 + i], a0);
+      a1 = fma(V[s.ph + (i + 1) * M.R], yres[s.w0 + i + 1], a1);
     }
-    if (i < s.ihi) a0 += V[s.ph + i * M.R] * yres[s.w0 + i];
+    if (i < s.ihi) a0 = fma(V[s.ph + i * M.R], yres[s.w0 + i], a0);
     h[k] = a0 + a1;
   }
   __syncwarp();
@@ -266,26 +370,34 @@ __device__ __noinline__ bool pe_refresh(const DevModel& M, PeWarp<T>& W, double*
   // LDL^T pivots, all positive); log|C| = sum log pivot, kept as mantissa x 2^exponent
   double pm = 1.0;
   int pe = 0;
+#pragma unroll 1
   for (int k = 0; k < N; ++k) {
+#pragma unroll 1
     for (int j = lane; j < N; j += 32) {
       rowk[j] = A[(size_t)k * ws_ld + j];
       colk[j] = A[(size_t)j * ws_ld + k];
     }
     __syncwarp();
     const double piv = rowk[k];
-    if (!(piv > 0.0) || !isfinite(piv)) return false;
+    if (!(piv > 0.0) || !isfinite(piv)) return out;
     const double ip = 1.0 / piv;
     int ex;
     pm *= frexp(piv, &ex);
     pe += ex;
     pm = frexp(pm, &ex);
     pe += ex;
+#pragma unroll 1
+    for (int j = lane; j < N; j += 32) colk[j] *= ip;  // the row multipliers
+    __syncwarp();
+#pragma unroll 1
     for (int i = 0; i < N; ++i) {
       double* Ai = A + (size_t)i * ws_ld;
       if (i == k) {
+#pragma unroll 1
         for (int j = lane; j < N; j += 32) Ai[j] = (j == k) ? ip : rowk[j] * ip;
       } else {
-        const double f = colk[i] * ip;
+        const double f = colk[i];
+#pragma unroll 1
         for (int j = lane; j < N; j += 32) Ai[j] = (j == k) ? -f : fma(-f, rowk[j], Ai[j]);
       }
     }
@@ -293,190 +405,202 @@ __device__ __noinline__ bool pe_refresh(const DevModel& M, PeWarp<T>& W, double*
   }
   const double logdetC = log(pm) + (double)pe * 0.6931471805599453;
   // v = C^-1 h (C^-1 symmetric: lanes over columns)
-  double dmax = 0.0, amax = 0.0;
+#pragma unroll 1
   for (int i = lane; i < N; i += 32) {
     double s = 0.0;
+#pragma unroll 1
     for (int j = 0; j < N; ++j) s = fma(A[(size_t)j * ws_ld + i], h[j], s);
     rowk[i] = s;
   }
   __syncwarp();
   double hv = 0.0;
+#pragma unroll 1
   for (int i = lane; i < N; i += 32) hv += h[i] * rowk[i];
   hv = wsum(hv);
   double yy = 0.0;
+#pragma unroll 1
   for (int x = lane; x < n; x += 32) yy += yres[x] * yres[x];
   yy = wsum(yy);
   // drift of the incremental state, then the refreshed state
+  double dmax = 0.0, amax = 0.0;
+#pragma unroll 1
   for (int i = 0; i < N; ++i) {
+#pragma unroll 1
     for (int j = lane; j < N; j += 32) {
       const double nv = A[(size_t)i * ws_ld + j];
-      dmax = fmax(dmax, fabs(nv - Cp[(size_t)i * ld + j]));
+      dmax = fmax(dmax, fabs(nv - c64(Cp[(size_t)i * ld + j])));
       amax = fmax(amax, fabs(nv));
-      Cp[(size_t)i * ld + j] = nv;
+      Cp[(size_t)i * ld + j] = cfrom64<C>(nv);
     }
   }
   double vd = 0.0, va = 0.0;
+#pragma unroll 1
   for (int i = lane; i < N; i += 32) {
-    vd = fmax(vd, fabs(rowk[i] - W.v[i]));
+    vd = fmax(vd, fabs(rowk[i] - c64(W.v[i])));
     va = fmax(va, fabs(rowk[i]));
-    W.v[i] = rowk[i];
-    W.vT[i] = (T)rowk[i];
+    W.v[i] = cfrom64<C>(rowk[i]);
   }
+#pragma unroll 1
   for (int x = lane; x < n; x += 32) W.y[x] = (T)yres[x];
   dmax = wmax(dmax); amax = wmax(amax); vd = wmax(vd); va = wmax(va);
   __syncwarp();
-  drift_out = fmax(amax > 0.0 ? dmax / amax : 0.0, va > 0.0 ? vd / fmax(va, 1.0) : 0.0);
-  logdet_out = n * log(M.se2) + logdetC - N * log(r);
-  logL_out = -0.5 * (n * kLog2Pi + logdet_out + (yy - hv) / M.se2);
-  return true;
+  out.ok = 1;
+  out.drift = fmax(amax > 0.0 ? dmax / amax : 0.0, va > 0.0 ? vd / fmax(va, 1.0) : 0.0);
+  out.logdet = n * M.log_se2 + logdetC - N * M.log_r;
+  out.logL = -0.5 * (n * kLog2Pi + out.logdet + (yy - hv) / M.se2);
+  return out;
 }
 
 // Scalars of an accepted move, from the proposal and its scoring.
-struct PeMove {
+template <typename C> struct PeMove {
   int jump, kk, jp, jm, np;
-  double aa, quad, bv, vk, ay;
+  C aa, quad, bv, vk, ay;
   Sup sp;
 };
 
+template <typename C> struct AcceptOut {
+  C* Cp;
+  int ld, N;
+  unsigned long long words;
+};
+
 // Apply an accepted move to C^-1, v, y and the PE list (out of line: it runs on a minority of
-// steps and keeps the per-step code compact). Returns the new N; *Cp / *ld change when C^-1
-// moves from the shared tile to the global slot.
+// steps and keeps the per-step code compact). Returns the new N, and the new C^-1 storage when
+// it moves from the shared tile to the global slot.
 template <typename T>
-__device__ __noinline__ int pe_accept(const DevModel& M, const PeWarp<T>& W, const T* Vs, double** Cpp, int* ldp,
-                                      double* Cg, int ldc, const PeMove mv, int n, int N, int lane,
-                                      unsigned long long* words) {
-  double* Cp = *Cpp;
-  int ld = *ldp;
-  const double mu = M.mu_q, rr = M.se2 / M.sq2;
+__device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel& M, const PeWarp<T> W, const T* Vs,
+                                                                  typename PeTab<T>::C* Cp, int ld,
+                                                                  typename PeTab<T>::C* Cg, int ldc,
+                                                                  const PeMove<typename PeTab<T>::C> mv, int n, int N,
+                                                                  int lane) {
+  // One form for the three moves. With c = row k of C^-1 (death, update), gamma = c_k, and
+  // u' = C_-^-1 b~ (birth, update: C_- is C without PE k for an update, C itself for a birth;
+  // b~ is b without its k entry), delta = r + |a_+|^2 - b~^T u':
+  //   C'_ij = C_{m(i) m(j)} - c_m(i) c_m(j) / gamma + u'_i u'_j / delta   (i, j != s),
+  //   C'_is = -u'_i / delta,  C'_ss = 1 / delta,
+  // where s is the slot of the new PE (N for a birth, k for an update; none for a death) and
+  // m moves the last PE into slot k for a death (identity otherwise). v changes the same way.
+  using C = typename PeTab<T>::C;
+  const C mu = cconst<C>(M.mu_q), rr = cconst<C>(M.se2 / M.sq2);
   const T muT = (T)M.mu_q;
-  const int R = M.R, np = mv.np, kk = mv.kk;
-  const Sup sp = mv.sp;
-  if (mv.jump == 0) {
-    // bordering: u = C^-1 b, delta = r + |a|^2 - b^T u
-    for (int i = lane; i < N; i += 32) {
-      double s = 0.0;
-      for (int a = 0; a < np; ++a) s = fma(Cp[(size_t)W.ovi[a] * ld + i], W.ovb[a], s);
-      W.cv[i] = s;
-    }
-    __syncwarp();
-    const double idl = 1.0 / (rr + mv.aa - mv.quad);
-    if (N + 1 > ld && Cp != Cg) {  // the tile is full: move C^-1 to the global slot
-      for (int i = 0; i < N; ++i)
-        for (int j = lane; j < N; j += 32) Cg[(size_t)i * ldc + j] = Cp[(size_t)i * ld + j];
-      Cp = Cg;
-      ld = ldc;
+  const int R = M.R, np = mv.np, kk = mv.kk, jump = mv.jump;
+  const bool has_m = jump != 0, has_p = jump != 1;
+  const int skip = jump == 2 ? kk : -1;
+  const int Nout = N + (jump == 0 ? 1 : (jump == 1 ? -1 : 0));
+  const int s = jump == 0 ? N : (jump == 2 ? kk : -1);
+  const int last = N - 1;
+  // vectors: c (cv; zero for a birth) and C^-1 b~ (uv; zero for a death). The passes below
+  // always apply both terms, so that they have no branches on the move type.
+  const int krow = has_m ? kk : 0;
+  const int npu = has_p ? np : 0;
+#pragma unroll 1
+  for (int i = lane; i < N; i += 32) {
+    const C ci = Cp[(size_t)krow * ld + i];
+    W.cv[i] = has_m ? ci : czero<C>();
+    C acc = czero<C>();
+#pragma unroll 1
+    for (int a = 0; a < npu; ++a)
+      if (W.ovi[a] != skip) acc = cfma(Cp[(size_t)W.ovi[a] * ld + i], W.ovb[a], acc);
+    W.uv[i] = acc;
+  }
+  if (lane == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth
+  __syncwarp();
+  C ig = czero<C>(), idl = czero<C>(), t = czero<C>(), fv = czero<C>();
+  if (has_m) {
+    ig = crcp(W.cv[kk]);
+    fv = cmul(cadd(mv.vk, mu), ig);
+  }
+  if (has_p) {
+    C bk = czero<C>(), wk = czero<C>();
+    if (jump == 2) {
+      // u' = w - c w_k / gamma on the system without PE k
+      wk = W.uv[kk];
+      const C wkg = cneg(cmul(wk, ig));
+#pragma unroll 1
+      for (int i = lane; i < N; i += 32) W.uv[i] = (i == kk) ? czero<C>() : cfma(W.cv[i], wkg, W.uv[i]);
+#pragma unroll 1
+      for (int a = lane; a < np; a += 32)
+        if (W.ovi[a] == kk) bk = W.ovb[a];
+      bk = csum(bk);
       __syncwarp();
     }
-    for (int j0 = 0; j0 <= N; j0 += 32) {
-      const int j = j0 + lane;
-      const double uj = j < N ? W.cv[j] * idl : 0.0;
-      for (int i = 0; i < N; ++i) {
-        const double ui = W.cv[i];
-        double* Ci = Cp + (size_t)i * ld;
-        if (j < N) Ci[j] = fma(ui, uj, Ci[j]);
-        else if (j == N) Ci[N] = -ui * idl;
-      }
-      if (j < N) Cp[(size_t)N * ld + j] = -uj;
-      else if (j == N) Cp[(size_t)N * ld + N] = idl;
-    }
-    // v' = [v + (t - mu) u; -t], t = (b^T v - mu b^T u - h_new) / delta, h_new = a^T y'
-    const double hnew = mv.ay - mu * mv.aa;
-    const double t = (mv.bv - mu * mv.quad - hnew) * idl;
-    for (int i = lane; i < N; i += 32) W.v[i] = fma(t - mu, W.cv[i], W.v[i]);
-    if (lane == 0) { W.v[N] = -t; W.list[N] = mv.jp; }
-    for (int i = sp.ilo + lane; i < sp.ihi; i += 32) W.y[sp.w0 + i] -= muT * Vs[sp.ph + i * R];
-    *words += (unsigned long long)N * np + 2ull * (N + 1) * (N + 1) + 2 * N + 2 * (sp.ihi - sp.ilo);
-    N += 1;
-  } else if (mv.jump == 1) {
-    // Schur downdate by row k, then the last PE moves into slot k
-    for (int i = lane; i < N; i += 32) W.cv[i] = Cp[(size_t)kk * ld + i];
-    __syncwarp();
-    const double ig = 1.0 / W.cv[kk];
-    const int last = N - 1;
-    for (int j0 = 0; j0 < last; j0 += 32) {
-      const int j = j0 + lane;
-      if (j < last) {
-        const int mj = (j == kk) ? last : j;
-        const double cj = W.cv[mj] * ig;
-        for (int i = 0; i < last; ++i) {
-          const int mi = (i == kk) ? last : i;
-          Cp[(size_t)i * ld + j] = fma(-W.cv[mi], cj, Cp[(size_t)mi * ld + mj]);
-        }
-      }
-    }
-    const double fv = (mv.vk + mu) * ig;
-    for (int i = lane; i < last; i += 32) {
-      const int mi = (i == kk) ? last : i;
-      W.v[i] = fma(-W.cv[mi], fv, W.v[mi]);
-    }
-    const Sup sm = pe_sup(M, n, mv.jm);
-    for (int i = sm.ilo + lane; i < sm.ihi; i += 32) W.y[sm.w0 + i] += muT * Vs[sm.ph + i * R];
-    __syncwarp();
-    if (lane == 0) W.list[kk] = W.list[last];
-    *words += (unsigned long long)N + 2ull * last * last + 2 * N + 2 * (sm.ihi - sm.ilo);
-    N -= 1;
-  } else {
-    // update of PE k: downdate by row k and border with b~ = b without its k entry
-    double bk = 0.0;
+    C bu = czero<C>();
+#pragma unroll 1
     for (int a = lane; a < np; a += 32)
-      if (W.ovi[a] == kk) bk = W.ovb[a];
-    bk = wsum(bk);
-    for (int i = lane; i < N; i += 32) {
-      double s = 0.0;
-      for (int a = 0; a < np; ++a) {
-        const int qa = W.ovi[a];
-        if (qa != kk) s = fma(Cp[(size_t)qa * ld + i], W.ovb[a], s);
-      }
-      W.uv[i] = s;                        // w = C^-1 b~
-      W.cv[i] = Cp[(size_t)kk * ld + i];  // c = row k
-    }
+      if (W.ovi[a] != skip) bu = cfma(W.ovb[a], W.uv[W.ovi[a]], bu);
+    bu = csum(bu);
+    idl = crcp(csub(cadd(rr, mv.aa), bu));
+    // t = (b~^T v_- - mu b~^T u' - h_new) / delta with v_- = v after removing PE k and h_new the
+    // new PE's a^T y on the residual without PE k
+    const C bvm = jump == 2 ? csub(csub(mv.bv, cmul(bk, mv.vk)), cmul(wk, fv)) : mv.bv;
+    const C hnew = csub(cadd(mv.ay, cmul(mu, bk)), cmul(mu, mv.aa));
+    t = cmul(csub(csub(bvm, cmul(mu, bu)), hnew), idl);
+  }
+  if (jump == 0 && N + 1 > ld && Cp != Cg) {  // the tile is full: move C^-1 to the global slot
+#pragma unroll 1
+    for (int i = 0; i < N; ++i)
+#pragma unroll 1
+      for (int j = lane; j < N; j += 32) Cg[(size_t)i * ldc + j] = Cp[(size_t)i * ld + j];
+    Cp = Cg;
+    ld = ldc;
     __syncwarp();
-    const double ig = 1.0 / W.cv[kk], wk = W.uv[kk];
-    for (int i = lane; i < N; i += 32) W.uv[i] = (i == kk) ? 0.0 : fma(-W.cv[i] * ig, wk, W.uv[i]);  // u'
-    __syncwarp();
-    double bu = 0.0;
-    for (int a = lane; a < np; a += 32) {
-      const int qa = W.ovi[a];
-      if (qa != kk) bu = fma(W.ovb[a], W.uv[qa], bu);
-    }
-    bu = wsum(bu);
-    const double idl = 1.0 / (rr + mv.aa - bu);
-    for (int j0 = 0; j0 < N; j0 += 32) {
-      const int j = j0 + lane;
-      if (j < N) {
-        const double cj = W.cv[j] * ig, uj = W.uv[j] * idl;
-        for (int i = 0; i < N; ++i) {
-          double* Ci = Cp + (size_t)i * ld;
-          if (i == kk) Ci[j] = (j == kk) ? idl : -uj;
-          else if (j == kk) Ci[j] = -W.uv[i] * idl;
-          else Ci[j] = fma(W.uv[i], uj, fma(-W.cv[i], cj, Ci[j]));
-        }
+  }
+  // C^-1 in place: reads never touch a cell written earlier in the pass (row / column k are only
+  // read through cv, and the last row / column are read but not written for a death)
+  const C nig = cneg(ig);
+  const int kmap = jump == 1 ? kk : -1;  // the slot the last PE moves into
+#pragma unroll 1
+  for (int j0 = 0; j0 < Nout; j0 += 32) {
+    const int j = j0 + lane;
+    if (j < Nout) {
+      const int mj = (j == kmap) ? last : j;
+      const C cj = cmul(W.cv[mj], nig);
+      const C uj = cmul(W.uv[j], idl);
+      const C sj = (j == s) ? idl : cneg(uj);  // row / column s
+#pragma unroll 1
+      for (int i = 0; i < Nout; ++i) {
+        const int mi = (i == kmap) ? last : i;
+        const C val = cfma(W.uv[i], uj, cfma(W.cv[mi], cj, Cp[(size_t)mi * ld + mj]));
+        Cp[(size_t)i * ld + j] = (i == s) ? sj : ((j == s) ? cneg(cmul(W.uv[i], idl)) : val);
       }
     }
-    // v: death of k (v_mid), then the birth at slot k on the reduced system
-    const double fv = (mv.vk + mu) * ig;
-    const double bvm = (mv.bv - bk * mv.vk) - wk * fv;
-    const double hnew = mv.ay + mu * bk - mu * mv.aa;
-    const double t = (bvm - mu * bu - hnew) * idl;
-    for (int i = lane; i < N; i += 32)
-      W.v[i] = (i == kk) ? -t : fma(t - mu, W.uv[i], fma(-W.cv[i], fv, W.v[i]));
+  }
+  // v' = v_m - c_m fv + (t - mu) u', v'_s = -t
+  const C tm = csub(t, mu), nfv = cneg(fv);
+#pragma unroll 1
+  for (int i = lane; i < Nout; i += 32) {
+    const int mi = (i == kmap) ? last : i;
+    const C val = cfma(tm, W.uv[i], cfma(W.cv[mi], nfv, W.v[mi]));
+    W.v[i] = (i == s) ? cneg(t) : val;
+  }
+  // residual and PE list
+  unsigned long long wds = (unsigned long long)N * np + 2ull * Nout * Nout + 2ull * Nout;
+  if (has_m) {
     const Sup sm = pe_sup(M, n, mv.jm);
+#pragma unroll 1
     for (int i = sm.ilo + lane; i < sm.ihi; i += 32) W.y[sm.w0 + i] += muT * Vs[sm.ph + i * R];
+    wds += 2 * (sm.ihi - sm.ilo) + N;
     __syncwarp();
+  }
+  if (has_p) {
+    const Sup sp = mv.sp;
+#pragma unroll 1
     for (int i = sp.ilo + lane; i < sp.ihi; i += 32) W.y[sp.w0 + i] -= muT * Vs[sp.ph + i * R];
-    if (lane == 0) W.list[kk] = mv.jp;
-    *words += (unsigned long long)N * np + N + 2ull * N * N + 2 * N + 2 * (sm.ihi - sm.ilo) + 2 * (sp.ihi - sp.ilo);
+    wds += 2 * (sp.ihi - sp.ilo);
+  }
+  if (lane == 0) {
+    if (jump == 0) W.list[N] = mv.jp;
+    else if (jump == 1) W.list[kk] = W.list[last];
+    else W.list[kk] = mv.jp;
   }
   __syncwarp();
-  for (int i = lane; i < N; i += 32) W.vT[i] = (T)W.v[i];
-  __syncwarp();
-  *Cpp = Cp;
-  *ldp = ld;
-  return N;
+  return AcceptOut<C>{Cp, ld, Nout, wds};
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlots G) {
+__global__ void __launch_bounds__(kPeMaxThreads, 4)
+    pe_kernel(const __grid_constant__ DevModel M, const __grid_constant__ BatchView B, const __grid_constant__ PeSlots G) {
+  using C = typename PeTab<T>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool fp32 = sizeof(T) == 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -485,18 +609,18 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
   T* Vs = reinterpret_cast<T*>(smem_raw);
   T* lgN = reinterpret_cast<T*>(smem_raw + a16(sizeof(T) * M.Lt));
   for (int m = threadIdx.x; m < M.Lt; m += blockDim.x) Vs[m] = PeTab<T>::V(M)[m];
-  for (int i = threadIdx.x; i < n_cap + 2; i += blockDim.x) lgN[i] = i > 0 ? (T)log((double)i) : (T)0;
+  for (int i = threadIdx.x; i < n_cap + 2; i += blockDim.x)
+    lgN[i] = i > 0 ? (fp32 ? (T)logf((float)i) : (T)log((double)i)) : (T)0;
   __syncthreads();
   PeWarp<T> W = pe_carve<T>(smem_raw + pe_block_bytes<T>(M.Lt, n_cap) +
                                 (size_t)warp * pe_warp_bytes<T>(n_cap, n_alloc, M.win_extra, Ns),
                             n_cap, n_alloc, M.win_extra, Ns);
   PeStats& S = *W.st;
   const size_t slot = (size_t)blockIdx.x * nwarps + warp;
-  double* const Cg = G.C ? G.C + slot * G.c_stride : nullptr;
+  C* const Cg = G.C ? reinterpret_cast<C*>(G.C) + slot * G.c_stride : nullptr;
   double* const ws = G.ws ? G.ws + slot * G.ws_stride : nullptr;
-  const double* __restrict__ tc = M.tc64;
-  const double iq = 1.0 / M.sq2, rr = M.se2 / M.sq2;
-  const T q = (T)M.sq2, mu = (T)M.mu_q;
+  const C* __restrict__ tc = PeTab<T>::tc(M);
+  const T q = (T)M.sq2, mu = (T)M.mu_q, rrT = (T)(M.se2 / M.sq2), iqT = (T)(1.0 / M.sq2), ise2T = (T)M.inv_se2;
   const T Jt = (T)M.J, logJ = (T)M.log_J, inv_gT = (T)M.inv_g;
   const int R = M.R;
 
@@ -552,7 +676,7 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
     for (int k = lane; k <= k0_hi - k0_lo; k += 32) {
       const int kq = k0_lo + k;
       const double tot = pe_cphi<double>(M, T_hi - 1 - kq) - pe_cphi<double>(M, T_lo - 1 - kq);
-      W.lPhi[k] = tot > 0.0 ? (T)log(tot * M.g) : (T)-INFINITY;
+      W.lPhi[k] = tot > 0.0 ? (fp32 ? (T)logf((float)(tot * M.g)) : (T)log(tot * M.g)) : (T)-INFINITY;
     }
     // empty z: y = w
     double wsq = 0.0;
@@ -565,42 +689,51 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
     if (lane == 0) {
       S.sN = S.sN2 = S.sK = S.sK2 = 0;
       S.sQ = S.sQ2 = 0.0; S.q_cur = 0.0; S.q_from = 0;
-      S.logdet = n * log(M.se2);
+      S.logdet = n * M.log_se2;
       S.logL = -0.5 * (n * kLog2Pi + S.logdet + wsq * M.inv_se2);
       S.drift_max = 0.0; S.alg_words = 0;
       for (int k = 0; k < 3; ++k) { S.acc[k] = 0; S.prop[k] = 0; }
       S.acc_t0 = S.prop_t0 = S.n_refresh = S.status = S.n_acc_refresh = S.refresh_fail = 0;
     }
     __syncwarp();
-    const T log_lambda0 = (T)log(lambda0);
-    double* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1, row stride ld
+    const T log_lambda0 = fp32 ? (T)logf((float)lambda0) : (T)log(lambda0);
+    C* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1, row stride ld
     int ld = Ns > 0 ? Ns : G.ldc;
     int N = 0;
 
     for (int step = 0; step < n_steps; ++step) {
       // ---- random draws of the next kPeRB steps: lane l takes step step + l
       if ((step & (kPeRB - 1)) == 0) {
-        double u[8];
+        PeRand<T> rd;
 #pragma unroll 1
         for (int blk = 0; blk < 2; ++blk) {
           uint64_t c[4] = {(uint64_t)(step + lane), (uint64_t)blk, 0, 0};
           philox4x64_10(c, seed, wf_id);
-          for (int k = 0; k < 4; ++k) u[4 * blk + k] = u01_from_bits(c[k]);
+          if (fp32) {
+            const float a = u01_float(c[0]), b = u01_float(c[1]), d = u01_float(c[2]), e = u01_float(c[3]);
+            if (blk == 0) {
+              rd.z1 = (T)(sqrtf(-2.0f * logf(a)) * cosf(6.2831853f * b));
+              rd.lu0 = (T)logf(d);
+              rd.u3 = (T)e;
+            } else {
+              rd.u4 = (T)a;
+              rd.z2 = (T)(sqrtf(-2.0f * logf(b)) * cosf(6.2831853f * d));
+              rd.lu = (T)logf(e);
+            }
+          } else {
+            const double a = u01_from_bits(c[0]), b = u01_from_bits(c[1]), d = u01_from_bits(c[2]),
+                         e = u01_from_bits(c[3]);
+            if (blk == 0) {
+              rd.z1 = (T)(sqrt(-2.0 * log(a)) * cos(kTwoPi * b));
+              rd.lu0 = (T)log(d);
+              rd.u3 = (T)e;
+            } else {
+              rd.u4 = (T)a;
+              rd.z2 = (T)(sqrt(-2.0 * log(b)) * cos(kTwoPi * d));
+              rd.lu = (T)log(e);
+            }
+          }
         }
-        PeRand<T> rd;
-        if (!fp32) {
-          rd.z1 = (T)(sqrt(-2.0 * log(u[0])) * cos(kTwoPi * u[1]));
-          rd.lu0 = (T)log(u[2]);
-          rd.z2 = (T)(sqrt(-2.0 * log(u[5])) * cos(kTwoPi * u[6]));
-          rd.lu = (T)log(u[7]);
-        } else {
-          rd.z1 = (T)(sqrtf(-2.0f * logf((float)u[0])) * cosf(6.2831853f * (float)u[1]));
-          rd.lu0 = (T)logf((float)u[2]);
-          rd.z2 = (T)(sqrtf(-2.0f * logf((float)u[5])) * cosf(6.2831853f * (float)u[6]));
-          rd.lu = (T)logf((float)u[7]);
-        }
-        rd.u3 = (T)u[3];
-        rd.u4 = (T)u[4];
         W.rnd[lane] = rd;
         __syncwarp();
       }
@@ -619,6 +752,7 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
           la0 = (T)-INFINITY;
         } else {
           T part = (T)0;
+#pragma unroll 1
           for (int k = lane; k < N; k += 32) {
             const int j = W.list[k];
             part += pe_logphi<T>(M, j - k0p) - pe_logphi<T>(M, j - k0);
@@ -664,12 +798,12 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
           }
         }
       }
-      // ---- scoring: the 2x2 quantities in PE space (FP64), then the 2x2 algebra in T
-      PeMove mv;
+      // ---- scoring: the 2x2 quantities in PE space, then the 2x2 algebra in T
+      PeMove<C> mv;
       mv.jump = jump; mv.kk = kk; mv.jp = jp; mv.jm = jm; mv.np = 0;
-      mv.aa = mv.quad = mv.bv = mv.vk = mv.ay = 0.0;
+      mv.aa = mv.quad = mv.bv = mv.vk = mv.ay = czero<C>();
       mv.sp = Sup{0, 0, 0, 0};
-      double mmm = 0, mmp = 0, mpp = 0, gm = 0, gp = 0, em = 1;
+      T mmm = 0, mmp = 0, mpp = 0, gm = 0, gp = 0, em = 1;
       unsigned long long words = 0;
       if (valid) {
         if (jump != 1) {
@@ -677,14 +811,15 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
           mv.sp = sp;
           // PEs overlapping a_+, with b_q = a_q^T a_+
           int np = 0;
+#pragma unroll 1
           for (int base = 0; base < N; base += 32) {
             const int qi = base + lane;
-            double bq = 0.0;
+            C bq = czero<C>();
             if (qi < N) {
               const int o = jp - W.list[qi];
-              if (o > -M.Lt && o < M.Lt) bq = xcorr<double>(M, tc, sp, o);
+              if (o > -M.Lt && o < M.Lt) bq = xcorr<C>(M, tc, sp, o);
             }
-            const bool ov = bq != 0.0;
+            const bool ov = cnz(bq);
             const unsigned m = __ballot_sync(kFull, ov);
             if (ov) {
               const int pos = np + __popc(m & ((1u << lane) - 1u));
@@ -695,52 +830,59 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
           }
           __syncwarp();
           mv.np = np;
-          mv.aa = xcorr<double>(M, tc, sp, 0);
-          // rows of C^-1 b on the overlap set: lane a holds (C^-1 b)_{ovi[a]} (FP64), so that
-          // b^T C^-1 b reduces over np lanes and (C^-1 b)_k is one of them for an update
-          T ayp = (T)0, bvp = (T)0;
+          mv.aa = xcorr<C>(M, tc, sp, 0);
+          // rows of C^-1 b on the overlap set: lane a holds (C^-1 b)_{ovi[a]}, so that b^T C^-1 b
+          // and b^T v reduce over np lanes and (C^-1 b)_k is one of them for an update
+          T ayp = (T)0;
+#pragma unroll 1
           for (int i = sp.ilo + lane; i < sp.ihi; i += 32) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
-          double qp = 0.0, ck = 0.0;
+          C qp = czero<C>(), bvp = czero<C>(), ck = czero<C>();
           int kpos = -1;
+#pragma unroll 1
           for (int a0 = 0; a0 < np; a0 += 32) {
             const int a = a0 + lane;
             if (a < np) {
-              const double* Crow = Cp + (size_t)W.ovi[a] * ld;
-              double rq = 0.0;
-              for (int b = 0; b < np; ++b) rq = fma(Crow[W.ovi[b]], W.ovb[b], rq);
-              const double ba = W.ovb[a];
-              qp = fma(ba, rq, qp);
-              bvp += (T)ba * W.vT[W.ovi[a]];
+              const C* Crow = Cp + (size_t)W.ovi[a] * ld;
+              C rq = czero<C>();
+#pragma unroll 1
+              for (int b = 0; b < np; ++b) rq = cfma(Crow[W.ovi[b]], W.ovb[b], rq);
+              const C ba = W.ovb[a];
+              qp = cfma(ba, rq, qp);
+              bvp = cfma(ba, W.v[W.ovi[a]], bvp);
               if (jump == 2 && W.ovi[a] == kk) { ck = rq; kpos = a; }
             }
           }
-          mv.quad = np <= 32 ? __shfl_sync(kFull, wsum_first(qp, np), 0) : wsum(qp);
-          const T bvT = wsum(bvp);
+          if (np <= 32) {
+            mv.quad = csum_first(qp, np);
+            mv.bv = csum_first(bvp, np);
+          } else {
+            mv.quad = csum(qp);
+            mv.bv = csum(bvp);
+          }
           const T ayT = wsum(ayp);
-          mv.ay = (double)ayT;
-          mv.bv = (double)bvT;
+          mv.ay = cfromf(ayT);
           if (jump == 2) {
-            // (C^-1 b)_k: from the lane that holds PE k's row, else (no overlap with the
-            // old position) a separate dot product
+            // (C^-1 b)_k: from the lane that holds PE k's row, else (no overlap with the old
+            // position) a separate dot product
             const unsigned hk = __ballot_sync(kFull, kpos >= 0);
             if (hk) {
-              ck = __shfl_sync(kFull, ck, __ffs(hk) - 1);
+              ck = cshfl(ck, __ffs(hk) - 1);
             } else {
-              double c2 = 0.0;
-              for (int a = lane; a < np; a += 32) c2 = fma(Cp[(size_t)kk * ld + W.ovi[a]], W.ovb[a], c2);
-              ck = wsum(c2);
+              C c2 = czero<C>();
+              for (int a = lane; a < np; a += 32) c2 = cfma(Cp[(size_t)kk * ld + W.ovi[a]], W.ovb[a], c2);
+              ck = csum(c2);
             }
           }
-          mpp = (mv.aa - mv.quad) * M.inv_se2;
-          gp = (double)((ayT - bvT) * (T)M.inv_se2);
-          mmp = ck * iq;
+          mpp = (T)cnum(csub(mv.aa, mv.quad)) * ise2T;
+          gp = (T)cnum(csub(mv.ay, mv.bv)) * ise2T;
+          mmp = (T)cnum(ck) * iqT;
           words += (unsigned long long)(N + 2 * np + 2 * (sp.ihi - sp.ilo) + np * np + np);
         }
         if (jump != 0) {
           mv.vk = W.v[kk];
-          em = rr * Cp[(size_t)kk * ld + kk];
-          mmm = (1.0 - em) * iq;
-          gm = (double)(W.vT[kk] * (T)iq);
+          em = rrT * (T)cnum(Cp[(size_t)kk * ld + kk]);
+          mmm = ((T)1 - em) * iqT;
+          gm = (T)cnum(mv.vk) * iqT;
           words += 2;
         }
       }
@@ -748,16 +890,15 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
       int st_c = 0;
       if (valid) {
         // det(I + Lambda M), Lambda = sigma_q^2 diag(-1, 1), with 1 - q m_-- = em
-        const T tmm = (T)mmm, tmp = (T)mmp, tpp = (T)mpp, tgm = (T)gm, tgp = (T)gp, tem = (T)em;
-        const T Dd = tem * ((T)1 + q * tpp) + q * q * tmp * tmp;
+        const T Dd = em * ((T)1 + q * mpp) + q * q * mmp * mmp;
         if (!(Dd > (T)0)) {
           la = (T)-INFINITY;
           st_c |= FSMP_ST_BADDET;
         } else {
           const T iD = (T)1 / Dd;
-          const T B11 = -q * ((T)1 + q * tpp) * iD, B12 = q * q * tmp * iD, B22 = q * tem * iD;
-          const T rm = tgm - mu * (tmp - tmm), rp = tgp - mu * (tpp - tmp);
-          const T dR = (T)-2 * mu * (tgp - tgm) + mu * mu * (tmm - (T)2 * tmp + tpp) -
+          const T B11 = -q * ((T)1 + q * mpp) * iD, B12 = q * q * mmp * iD, B22 = q * em * iD;
+          const T rm = gm - mu * (mmp - mmm), rp = gp - mu * (mpp - mmp);
+          const T dR = (T)-2 * mu * (gp - gm) + mu * mu * (mmm - (T)2 * mmp + mpp) -
                        (B11 * rm * rm + (T)2 * B12 * rm * rp + B22 * rp * rp);
           dT = log(Dd);
           dnu = (T)-0.5 * (dT + dR);
@@ -774,13 +915,19 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
 
       // ---- accepted move: C^-1, v, y and the PE list
       if (apply) {
-        N = pe_accept<T>(M, W, Vs, &Cp, &ld, Cg, G.ldc, mv, n, N, lane, &words);
-        double qs = 0.0;
-        for (int i = lane; i < N; i += 32) qs += W.v[i];
-        qs = wsum(qs);
+        {
+          const AcceptOut<C> ao = pe_accept<T>(M, W, Vs, Cp, ld, Cg, G.ldc, mv, n, N, lane);
+          Cp = ao.Cp;
+          ld = ao.ld;
+          N = ao.N;
+          words += ao.words;
+        }
+        C qs = czero<C>();
+        for (int i = lane; i < N; i += 32) qs = cadd(qs, W.v[i]);
+        qs = csum(qs);
         if (lane == 0) {
           close_hold(S, step, burn_in);
-          S.q_cur = N * M.mu_q + qs;
+          S.q_cur = N * M.mu_q + c64(qs);
           S.q_from = step;
           S.logdet += (double)dT;
           S.logL += (double)dnu;
@@ -788,19 +935,18 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
         }
         __syncwarp();
         if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          double ldv = 0.0, llv = 0.0, dr = 0.0;
-          const bool ok = pe_refresh<T>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane, ldv, llv, dr);
-          double qr = 0.0;
-          for (int i = lane; i < N; i += 32) qr += W.v[i];
-          qr = wsum(qr);
+          const RefreshOut ro = pe_refresh<T>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+          C qr = czero<C>();
+          for (int i = lane; i < N; i += 32) qr = cadd(qr, W.v[i]);
+          qr = csum(qr);
           if (lane == 0) {
             S.n_acc_refresh = 0;
-            if (ok) {
-              S.logdet = ldv; S.logL = llv;
-              S.drift_max = fmax(S.drift_max, dr);
-              if (dr > M.drift_tol) S.status |= FSMP_ST_DRIFT;
+            if (ro.ok) {
+              S.logdet = ro.logdet; S.logL = ro.logL;
+              S.drift_max = fmax(S.drift_max, ro.drift);
+              if (ro.drift > M.drift_tol) S.status |= FSMP_ST_DRIFT;
               S.n_refresh++;
-              S.q_cur = N * M.mu_q + qr;
+              S.q_cur = N * M.mu_q + c64(qr);
             } else {
               S.status |= FSMP_ST_DRIFT;
               S.refresh_fail++;
@@ -835,13 +981,12 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
     // ------------------------------------------------------------- chain end
     if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
       // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      double ldv = 0.0, llv = 0.0, dr = 0.0;
-      const bool ok = pe_refresh<T>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane, ldv, llv, dr);
+      const RefreshOut ro = pe_refresh<T>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
       if (lane == 0) {
-        if (ok) {
-          S.logdet = ldv; S.logL = llv;
-          S.drift_max = fmax(S.drift_max, dr);
-          if (dr > M.drift_tol) S.status |= FSMP_ST_DRIFT;
+        if (ro.ok) {
+          S.logdet = ro.logdet; S.logL = ro.logL;
+          S.drift_max = fmax(S.drift_max, ro.drift);
+          if (ro.drift > M.drift_tol) S.status |= FSMP_ST_DRIFT;
           S.n_refresh++;
         } else {
           S.status |= FSMP_ST_DRIFT;
@@ -869,6 +1014,15 @@ __global__ void __launch_bounds__(256) pe_kernel(DevModel M, BatchView B, PeSlot
   }
 }
 
+// Float-float copy of an FP64 table: hi = fl(x), lo = fl(x - hi).
+__global__ void split_ff_kernel(const double* a, float* out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h = (float)a[i];
+  out[2 * i] = h;
+  out[2 * i + 1] = (float)(a[i] - (double)h);
+}
+
 }  // namespace
 
 size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns) {
@@ -880,6 +1034,12 @@ size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns) {
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc) { return pe_ws_doubles(n_cap, n_alloc); }
 
 int pe_ldc(int n_cap) { return (n_cap + 31) / 32 * 32; }
+
+cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  split_ff_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, out, n);
+  return cudaGetLastError();
+}
 
 cudaError_t pe_kernel_attributes(int precision, int max_smem) {
   if (precision == FSMP_FP64)
@@ -898,7 +1058,7 @@ int pe_kernel_occupancy(int precision, int threads, size_t smem) {
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas, int Ns, size_t smem, void* cinv,
                       size_t c_stride, double* ws, size_t ws_stride, int* counter, cudaStream_t st) {
   PeSlots G;
-  G.C = reinterpret_cast<double*>(cinv);
+  G.C = cinv;
   G.c_stride = c_stride;
   G.ldc = pe_ldc(M.n_cap);
   G.ws = ws;

@@ -99,6 +99,7 @@ struct fsmp_ctx {
   // serving streams, then one for fsmp_run_device), each with slots for every resident warp
   double* tc64 = nullptr;
   float* tc32 = nullptr;
+  float* tcff = nullptr;
   struct PeSet {
     void* cinv = nullptr;    // C^-1 slots
     double* ws = nullptr;    // FP64 refresh workspace slots
@@ -190,7 +191,7 @@ void free_ctx(fsmp_ctx* c) {
   cudaFree(c->V64); cudaFree(c->V32); cudaFree(c->phi); cudaFree(c->logphi); cudaFree(c->cphi);
   cudaFree(c->scan); cudaFree(c->Lt_dev); cudaFree(c->gscratch);
   cudaFree(c->phi32); cudaFree(c->logphi32); cudaFree(c->cphi32); cudaFree(c->rscratch);
-  cudaFree(c->tc64); cudaFree(c->tc32);
+  cudaFree(c->tc64); cudaFree(c->tc32); cudaFree(c->tcff);
   for (auto& ps : c->pe_sets) { cudaFree(ps.cinv); cudaFree(ps.ws); cudaFree(ps.counter); }
   for (auto s : c->streams) cudaStreamDestroy(s);
   if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
@@ -651,6 +652,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   M.D = (int)D;
   M.mu_q = p.mu_q; M.sigma_q = p.sigma_q; M.sq2 = p.sigma_q * p.sigma_q;
   M.se2 = p.sigma_noise * p.sigma_noise; M.inv_se2 = 1.0 / M.se2;
+  M.log_se2 = log(M.se2); M.log_r = log(M.se2 / M.sq2);
   M.t0_lo = p.t0_lo; M.t0_hi = p.t0_hi; M.sample_t0 = p.sample_t0 ? 1 : 0;
   M.J = p.jump_J; M.log_J = log(p.jump_J);
   M.n_cap = p.n_cap;
@@ -689,9 +691,11 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     const size_t ntc = (size_t)M.R * xcorr_rows(M.Lt, M.R) * (2 * M.Lt - 1);
     CK(cudaMalloc(&c->tc64, sizeof(double) * ntc));
     CK(cudaMalloc(&c->tc32, sizeof(float) * ntc));
+    CK(cudaMalloc(&c->tcff, 2 * sizeof(float) * ntc));
     CK(launch_xcorr_table(c->V64, M.Lt, M.R, c->tc64, c->tc32, 0));
+    CK(launch_split_ff(c->tc64, c->tcff, ntc, 0));
     CK(cudaDeviceSynchronize());
-    M.tc64 = c->tc64; M.tc32 = c->tc32; M.tcM = xcorr_rows(M.Lt, M.R);
+    M.tc64 = c->tc64; M.tc32 = c->tc32; M.tcff = c->tcff; M.tcM = xcorr_rows(M.Lt, M.R);
   }
   c->n_smem_max = smem_n_max(c.get());
   int max_smem = (int)c->prop.sharedMemPerBlockOptin;
@@ -725,7 +729,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   // PE-space kernel: per-warp slots of C^-1 (when the shared tile can overflow) and of the FP64
   // refresh workspace (FP32 mode), one set per launch stream
   if (p.kernel == FSMP_KERNEL_PE) {
-    c->pe_warps = p.threads_per_chain > 0 ? p.threads_per_chain / 32 : 4;
+    c->pe_warps = p.threads_per_chain > 0 ? std::min(4, p.threads_per_chain / 32) : 4;
     const size_t esz = 8;  // C^-1 is FP64 in both modes
     c->pe_tile = p.pe_tile > 0 ? std::min(p.pe_tile, p.n_cap) : std::min(p.n_cap, 24);
     CK(pe_kernel_attributes(p.precision, max_smem));
