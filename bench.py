@@ -244,10 +244,10 @@ def device_batches(torch, wl, dev, n_smem_max, one_launch=False):
     return subs
 
 
-def load_traffic(kernel_src):
-    """DRAM traffic per launch of the chain kernel from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "chain_kernel_dram_traffic.json")
+def load_traffic(kernel_src, name):
+    """DRAM traffic per launch of a chain kernel from the committed ncu summary
+    profiles/<name>_dram_traffic.json, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", name + "_dram_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
@@ -280,7 +280,8 @@ def run_ours(args):
     ctx = fsmp.Context(params)
     info = ctx.info()
     peaks = ctx.measure_peaks()
-    subs = device_batches(torch, wl, dev, info["n_smem_max"], one_launch=args.kernel == "pe")
+    pe = args.kernel in ("auto", "pe")
+    subs = device_batches(torch, wl, dev, info["n_smem_max"], one_launch=pe)
     n_steps = int(b["n_steps"])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -339,8 +340,8 @@ def run_ours(args):
     kdom = int(np.argmax(mean_dur))
     alg_bytes = float(summ[kdom]["alg_bytes"].sum())
     achieved = alg_bytes / (mean_dur[kdom] * 1e-3) / 1e9
-    kernel_src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_chain.cu")
-    tr = load_traffic(kernel_src)
+    kernel_src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_pe.cu" if pe else "fsmp_chain.cu")
+    tr = load_traffic(kernel_src, "pe_kernel" if pe else "chain_kernel")
     allsum = np.concatenate(summ)
     acc = allsum["acc"].sum(0)
     prop = allsum["prop"].sum(0)
@@ -349,7 +350,7 @@ def run_ours(args):
                 "traffic": None if tr is None else tr["traffic_bytes_per_launch"] * (
                     (summ[kdom]["prop"].sum() / max(1.0, tr["units_per_launch"])) if tr.get("scale_by_units") else 1.0),
                 "peak_source": "measured live: fsmp_measure_peaks (16-byte shared loads, 4 CTAs/SM)",
-                "kernel": ("pe_kernel<%s>, one launch, n<=%d (%d chains)" if args.kernel == "pe" else
+                "kernel": ("pe_kernel<%s>, one launch, n<=%d (%d chains)" if pe else
                            "chain_kernel<%s, smem>, bucket n<=%d (%d chains)") % (
                     "float" if prec == fsmp.FP32_REFRESH else "double", subs[kdom][1], subs[kdom][2]),
                 "alg_bytes_per_launch": alg_bytes, "launch_ms": float(mean_dur[kdom]),

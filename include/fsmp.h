@@ -57,7 +57,7 @@ extern "C" {
                                    Sigma^-1, s and log|Sigma| every refresh_every accepts      */
 
 /* ---- kernel form ---- */
-#define FSMP_KERNEL_AUTO 0      /* library choice (autotuned)                                */
+#define FSMP_KERNEL_AUTO 0      /* library choice: FSMP_KERNEL_PE                            */
 #define FSMP_KERNEL_SMEM 1      /* persistent kernel, one CTA per chain, packed Sigma^-1 in
                                    shared memory                                            */
 #define FSMP_KERNEL_GLOBAL 2    /* same kernel with packed Sigma^-1 in global memory (L2/HBM),

@@ -632,6 +632,8 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   if (params->device < 0 || params->device >= ndev) FAIL(FSMP_ERR_INVALID, "no such device");
   std::unique_ptr<fsmp_ctx, void (*)(fsmp_ctx*)> c(new fsmp_ctx(), free_ctx);
   c->p = *params;
+  // the automatic choice is the PE-space kernel (fastest form at every measured window length)
+  if (c->p.kernel == FSMP_KERNEL_AUTO) c->p.kernel = FSMP_KERNEL_PE;
   if (c->p.refresh_every <= 0) c->p.refresh_every = 64;
   if (!(c->p.drift_tol > 0)) c->p.drift_tol = 5e-2;
   if (c->p.device_mem_budget == 0) c->p.device_mem_budget = (size_t)4 << 30;
@@ -876,10 +878,19 @@ int fsmp_get_info(fsmp_ctx* c, fsmp_info* o) {
   o->R = c->M.R;
   o->L_V = c->M.L_V;
   o->n_smem_max = c->n_smem_max;
-  LaunchShape s;
-  if (make_shape(c, std::min(c->p.n_max, c->n_smem_max), true, &s) == FSMP_OK) {
-    o->threads_per_chain = s.threads;
-    o->ctas_per_sm = s.ctas / c->prop.multiProcessorCount;
+  if (c->p.kernel == FSMP_KERNEL_PE) {  // a warp per chain, pe_warps chains per CTA
+    int ctas = 0;
+    size_t sm = 0;
+    if (pe_shape(c, c->p.n_max, &ctas, &sm) == FSMP_OK) {
+      o->threads_per_chain = 32;
+      o->ctas_per_sm = ctas / c->prop.multiProcessorCount;
+    }
+  } else {
+    LaunchShape s;
+    if (make_shape(c, std::min(c->p.n_max, c->n_smem_max), true, &s) == FSMP_OK) {
+      o->threads_per_chain = s.threads;
+      o->ctas_per_sm = s.ctas / c->prop.multiProcessorCount;
+    }
   }
   o->scratch_bytes = c->gscratch_bytes + c->rscratch_stride * (size_t)c->rscratch_slots + c->pe_bytes;
   snprintf(o->name, sizeof(o->name), "%.63s", c->prop.name);

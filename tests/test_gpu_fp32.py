@@ -43,7 +43,7 @@ def _params(wl, **kw):
     return dict(wl["params"], n_max=max(64, n_max), precision=fsmp.FP32_REFRESH, **kw)
 
 
-KERNELS = [pytest.param(fsmp.KERNEL_AUTO, id="sigma"), pytest.param(fsmp.KERNEL_PE, id="pe")]
+KERNELS = [pytest.param(fsmp.KERNEL_SMEM, id="sigma"), pytest.param(fsmp.KERNEL_PE, id="pe")]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)

@@ -33,7 +33,9 @@ def test_noalloc_matches_run_device_twice():
     keep = np.nonzero(np.diff(b["offsets"]) <= 256)[0]
     b = workloads.subset(b, keep)
     n_max = int(np.diff(b["offsets"]).max())
-    params = dict(wl["params"], precision=fsmp.FP32_REFRESH, refresh_every=64, n_cap=64, n_max=n_max)
+    # the entry point runs the Sigma^-1 kernel with shared-memory state; compare with that form
+    params = dict(wl["params"], precision=fsmp.FP32_REFRESH, refresh_every=64, n_cap=64, n_max=n_max,
+                  kernel=fsmp.KERNEL_SMEM)
     dev = torch.device("cuda", 0)
     inp, W = _device_inputs(torch, b, dev)
     nbytes = W * fsmp.SUMMARY_DTYPE.itemsize
