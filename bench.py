@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--window-range", default="", help="lo,hi: keep only windows of lo..hi samples (profiling)")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: offered events/s (0: the workload's)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the arrival stream")
+    ap.add_argument("--serve-pool", type=int, default=1024, help="serving: distinct events replayed by the stream")
     return ap.parse_args()
 
 
@@ -64,8 +67,21 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def serving_workload(name):
+    from paper_2403_03156_gb300 import workloads
+    return "rate_hz" in workloads.CONFIGS[name]
+
+
 def shard_workload(args, rank):
     from paper_2403_03156_gb300 import workloads
+    if serving_workload(args.workload):  # events of the pool, as one batch
+        params, events = workloads.make_events(args.workload, min(args.serve_pool, 256), seed=args.seed + 1000 * rank,
+                                               n_steps=args.mcmc_steps or None)
+        batch = concat_events(events)
+        batch["burn_in"] = int(batch["n_steps"]) // 5
+        cfg = workloads.CONFIGS[args.workload]
+        return dict(name=args.workload, params=params, batch=batch,
+                    meta=dict(precision=cfg["precision"], refresh_every=cfg.get("refresh_every", 0)))
     wl = workloads.make_workload(args.workload, n_waveforms=args.n_waveforms or None,
                                  seed=args.seed + 1000 * rank, n_steps=args.mcmc_steps or None)
     # burn-in of one fifth of the chain for the posterior summaries (it costs the same steps)
@@ -80,6 +96,21 @@ def shard_workload(args, rank):
         keep = np.nonzero((n >= lo) & (n <= hi))[0]
         wl["batch"] = workloads.subset(b, keep)
     return wl
+
+
+def concat_events(events):
+    """The events' waveforms as one batch (each keeps its RNG index)."""
+    offs, samples, ids = [0], [], []
+    for e in events:
+        samples.append(e["samples"])
+        offs.extend((offs[-1] + e["offsets"][1:]).tolist())
+        ids.append(np.uint64(e["index_base"]) + np.arange(len(e["offsets"]) - 1, dtype=np.uint64))
+    out = dict(samples=np.concatenate(samples), offsets=np.asarray(offs, np.int32),
+               lambda0=np.concatenate([e["lambda0"] for e in events]),
+               t_origin_ns=np.concatenate([e["t_origin_ns"] for e in events]),
+               wf_ids=np.concatenate(ids), seed=events[0]["seed"], index_base=0,
+               n_steps=events[0]["n_steps"], burn_in=events[0].get("burn_in", 0))
+    return out
 
 
 # ------------------------------------------------------------------------ CPU oracle arm
@@ -409,10 +440,116 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """The serving loop under a Poisson stream of events (submit / poll through the C ABI, host
+    buffers, copies included): steps/s of the served events and p50/p99 event latency (submit
+    to result). Events are replayed from a pool of distinct simulated events, each arrival with
+    its own RNG seed."""
+    import threading
+    import torch
+    import torch.distributed as dist
+    from paper_2403_03156_gb300 import build, fsmp, workloads
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    cfg = workloads.CONFIGS[args.workload]
+    params, pool = workloads.make_events(args.workload, args.serve_pool, seed=args.seed + 1000 * rank,
+                                         n_steps=args.mcmc_steps or None)
+    n_steps = int(pool[0]["n_steps"])
+    for e in pool:
+        e["burn_in"] = n_steps // 5
+    rate = args.rate or cfg["rate_hz"]
+    ctx = fsmp.Context(dict(params, precision=fsmp.FP32_REFRESH, refresh_every=cfg.get("refresh_every", 64),
+                            n_max=cfg["win_max"], device=local, max_queued=1 << 20))
+    # warm-up: the first requests pay for lazy initialisation
+    for i in range(args.warmup):
+        ctx.run(pool[i % len(pool)], request_id=(1 << 40) + i)
+    rng = np.random.default_rng(1234 + rank)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * args.serve_seconds * 1.2) + 16))
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    n_ev = len(arrivals)
+    sizes = np.zeros(n_ev, np.int64)
+    lat = np.full(n_ev, np.nan)
+    t_done_last = [0.0]
+    done = [0]
+    stop = threading.Event()
+
+    def poller():
+        while not stop.is_set() or done[0] < n_ev:
+            for r in ctx.poll(4096, 50):
+                i = int(r["request_id"])
+                lat[i] = r["latency_s"]
+                done[0] += 1
+                t_done_last[0] = time.perf_counter()
+            if stop.is_set() and done[0] >= n_ev:
+                break
+
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches0 = ctx.info()["n_launches"]
+    clocks = Clocks(local)
+    clocks.start()
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    busy = 0
+    for i in range(n_ev):
+        ev = dict(pool[i % len(pool)])
+        ev["seed"] = int(args.seed) * 1000003 + i  # each arrival is a new event for the sampler
+        sizes[i] = len(ev["offsets"]) - 1
+        wait = t0 + arrivals[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        while ctx.submit(ev, request_id=i) == fsmp.ERR_BUSY:
+            busy += 1
+            time.sleep(0.001)
+    t_sub = time.perf_counter() - t0
+    stop.set()
+    th.join()
+    t_all = t_done_last[0] - t0
+    clk = clocks.stop()
+    launches = ctx.info()["n_launches"] - launches0
+    ctx.close()
+    steps = float(sizes.sum()) * n_steps
+    value = steps / t_all
+    if world > 1:
+        tv = torch.tensor([steps, t_all], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tv[:1], op=dist.ReduceOp.SUM)
+        tmax = torch.tensor([t_all], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        value = float(tv[0].item()) / float(tmax.item())
+    completed_rate = n_ev / t_all
+    bytes_in = sum(int(pool[i % len(pool)]["samples"].nbytes) for i in range(n_ev)) / n_ev
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_ev,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / n_ev, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "offered_rate_hz": rate, "submitted_in_s": t_sub,
+                       "stream_s": args.serve_seconds, "events": n_ev, "waveforms": int(sizes.sum()),
+                       "mcmc_steps_per_chain": n_steps, "completed_rate_hz": completed_rate,
+                       "sustained": bool(completed_rate >= 0.95 * rate), "busy_retries": busy,
+                       "timing": "host wall clock from the first submit to the last result (end to end)",
+                       "kernel": "pe_kernel<float> (serving loop, one launch per pack)"},
+            "latency": {"p50_s": float(np.nanpercentile(lat, 50)), "p99_s": float(np.nanpercentile(lat, 99)),
+                        "mean_s": float(np.nanmean(lat)), "max_s": float(np.nanmax(lat))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(bytes_in),
+                    "d2h_bytes_per_step": int(sizes.mean() * fsmp.SUMMARY_DTYPE.itemsize)},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        emit(line)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif serving_workload(args.workload):
+        run_serving(args)
     else:
         run_ours(args)
 

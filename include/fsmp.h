@@ -191,6 +191,7 @@ typedef struct {
   int threads_per_chain, ctas_per_sm;
   size_t scratch_bytes;          /* device scratch the context holds                     */
   char name[64];
+  long long n_launches;          /* chain-kernel launches made by this context so far     */
 } fsmp_info;
 
 /* Create a context on params->device: validates params, computes the SER and phi tables on

@@ -108,6 +108,7 @@ struct fsmp_ctx {
   std::vector<PeSet> pe_sets;
   int pe_slots = 0, pe_warps = 4, pe_tile = 0;
   size_t pe_c_stride = 0, pe_ws_stride = 0, pe_bytes = 0;
+  std::atomic<long long> n_launches{0};  // chain-kernel launches
   // serving loop
   std::vector<cudaStream_t> streams;
   cudaStream_t gmem_stream = nullptr;
@@ -231,6 +232,7 @@ int run_pe(fsmp_ctx* c, BatchView B, int set, cudaStream_t st) {
   const fsmp_ctx::PeSet& ps = c->pe_sets[set];
   cudaError_t e = launch_pe(c->M, B, c->pe_warps, ctas, c->pe_tile, smem, ps.cinv, c->pe_c_stride, ps.ws,
                             c->pe_ws_stride, ps.counter, st);
+  c->n_launches++;
   if (e != cudaSuccess) { set_error("launch_pe", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
   return FSMP_OK;
 }
@@ -268,6 +270,7 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st, int set) {
       }
       b1.order = nullptr;
       cudaError_t e = launch_chains(c->M, b1, FSMP_KERNEL_GLOBAL, s, c->gscratch, c->gscratch_bytes, nullptr, 0, 0, st);
+      c->n_launches++;
       if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
     }
     return FSMP_OK;
@@ -290,6 +293,7 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st, int set) {
   s.ctas = std::min(s.ctas, B.n_waveforms);
   cudaError_t e = launch_chains(c->M, B, form, s, c->gscratch, c->gscratch_bytes, c->rscratch,
                                 c->rscratch_stride, c->rscratch_slots, st);
+  c->n_launches++;
   if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
   return FSMP_OK;
 }
@@ -894,6 +898,7 @@ int fsmp_get_info(fsmp_ctx* c, fsmp_info* o) {
   }
   o->scratch_bytes = c->gscratch_bytes + c->rscratch_stride * (size_t)c->rscratch_slots + c->pe_bytes;
   snprintf(o->name, sizeof(o->name), "%.63s", c->prop.name);
+  o->n_launches = c->n_launches.load();
   return FSMP_OK;
 }
 

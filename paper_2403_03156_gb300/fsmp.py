@@ -73,7 +73,8 @@ class Info(ctypes.Structure):
     _fields_ = [("device", _c_int), ("sm_count", _c_int), ("smem_per_block_optin", _c_int),
                 ("ser_len", _c_int), ("R", _c_int), ("L_V", _c_int), ("n_smem_max", _c_int),
                 ("threads_per_chain", _c_int), ("ctas_per_sm", _c_int),
-                ("scratch_bytes", ctypes.c_size_t), ("name", ctypes.c_char * 64)]
+                ("scratch_bytes", ctypes.c_size_t), ("name", ctypes.c_char * 64),
+                ("n_launches", ctypes.c_longlong)]
 
 
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",

@@ -192,6 +192,29 @@ def make_workload(name, n_waveforms=None, seed=0, n_steps=None, burn_in=0):
     return dict(name=name, params=params, batch=batch, truth=truth, meta=meta)
 
 
+def make_events(name, n_events, seed=0, n_steps=None, burn_in=0):
+    """Events of the serving configuration: each event is one physics event seen by U{1..64}
+    channels (waveforms) that share the event's lambda (log-uniform, per event) and t0; each
+    channel draws its own PEs, charges and noise, and its own window length U{64..512}.
+    Returns (params, events) with each event a batch dict whose ``index_base`` gives its
+    waveforms distinct RNG indices across the list."""
+    cfg = CONFIGS[name]
+    params = dict(cfg["params"])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = cfg["wf_per_event"]
+    events, base = [], 0
+    for e in range(n_events):
+        nw = int(rng.integers(lo, hi + 1))
+        lam = float(_draw_lambda(rng, cfg["lam"], 1)[0])
+        t0 = float(rng.uniform(params["t0_lo"], params["t0_hi"]))
+        batch, _ = simulate(params, np.full(nw, lam), np.full(nw, t0), rng, cfg["window"],
+                            cfg["win_min"], cfg["win_max"])
+        batch.update(seed=seed, index_base=base, n_steps=int(n_steps or cfg["n_steps"]), burn_in=int(burn_in))
+        base += nw
+        events.append(batch)
+    return params, events
+
+
 def subset(batch, idx):
     """Batch restricted to the waveforms ``idx`` (keeps each waveform's RNG index)."""
     idx = np.asarray(idx, np.int64)
