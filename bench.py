@@ -47,12 +47,16 @@ def parse():
     ap.add_argument("--mcmc-steps", type=int, default=0, help="override MCMC steps per chain (testing)")
     ap.add_argument("--precision", default="", help="fp32 | fp64 (default: the workload's)")
     ap.add_argument("--threads", type=int, default=0, help="threads per chain CTA (0: library default)")
+    ap.add_argument("--pe-tile", type=int, default=0, help="PE kernel: shared-memory C^-1 tile (0: default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="PE kernel: resident CTAs per SM (0: max)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "smem", "global", "plain", "pe"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--window-range", default="", help="lo,hi: keep only windows of lo..hi samples (profiling)")
+    ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
+                    help="capture each step's launches in a CUDA graph (auto: on for lowocc_bulk_1m)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered events/s (0: the workload's)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the arrival stream")
     ap.add_argument("--serve-pool", type=int, default=1024, help="serving: distinct events replayed by the stream")
@@ -306,6 +310,7 @@ def run_ours(args):
     lengths = np.diff(b["offsets"])
     params = dict(wl["params"], precision=prec, refresh_every=wl["meta"].get("refresh_every") or 64,
                   n_max=int(max(lengths.max(), 64)), device=local, threads_per_chain=args.threads,
+                  pe_tile=args.pe_tile, pe_ctas_per_sm=args.ctas_per_sm,
                   kernel={"auto": fsmp.KERNEL_AUTO, "smem": fsmp.KERNEL_SMEM, "global": fsmp.KERNEL_GLOBAL,
                           "plain": fsmp.KERNEL_PLAIN, "pe": fsmp.KERNEL_PE}[args.kernel])
     ctx = fsmp.Context(params)
@@ -330,6 +335,21 @@ def run_ours(args):
         flush.zero_()
         one_step()
     torch.cuda.synchronize(dev)
+    use_graph = args.graph == "on" or (args.graph == "auto" and args.workload == "lowocc_bulk_1m")
+    graph = None
+    if use_graph:
+        # one CUDA graph per step: the chain launches (counter reset + kernel) replayed as a unit
+        graph = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(graph, stream=cs):
+                for (t, nm, _) in subs:
+                    ctx.run_device(t, n_steps=n_steps, burn_in=int(b.get("burn_in", 0)), seed=int(b["seed"]),
+                                   n_max_hint=nm, stream=cs)
+        stream.wait_stream(cs)
+        graph.replay()
+        torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     clocks = Clocks(local)
@@ -344,7 +364,12 @@ def run_ours(args):
     t_start.record(stream)
     for i in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (256 MiB write)
-        one_step(evs[i])
+        if graph is not None:
+            evs[i][0][0].record(stream)
+            graph.replay()
+            evs[i][0][1].record(stream)
+        else:
+            one_step(evs[i])
     t_end.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -365,8 +390,12 @@ def run_ours(args):
 
     # per-launch roofline of the dominant kernel (the longest bucket launch)
     summ = [fsmp.summaries_from_bytes(t["out"].cpu().numpy()) for (t, _, _) in subs]
-    durs = np.array([[evs[i][k][0].elapsed_time(evs[i][k][1]) for k in range(len(subs))]
-                     for i in range(args.steps)])
+    if graph is not None:  # one timed interval per step: the whole graph
+        durs = np.array([[evs[i][0][0].elapsed_time(evs[i][0][1])] + [0.0] * (len(subs) - 1)
+                         for i in range(args.steps)])
+    else:
+        durs = np.array([[evs[i][k][0].elapsed_time(evs[i][k][1]) for k in range(len(subs))]
+                         for i in range(args.steps)])
     mean_dur = durs.mean(0)
     kdom = int(np.argmax(mean_dur))
     alg_bytes = float(summ[kdom]["alg_bytes"].sum())
@@ -400,6 +429,7 @@ def run_ours(args):
                        "refresh_every": params["refresh_every"],
                        "window_samples": [int(lengths.min()), int(np.median(lengths)), int(lengths.max())],
                        "launches_per_step": len(subs), "threads_per_chain": info["threads_per_chain"],
+                       "cuda_graph": graph is not None,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "accept_rate": float(acc.sum() / max(1, prop.sum())),
                        "accepts_per_type": [int(x) for x in acc], "proposals_per_type": [int(x) for x in prop]},

@@ -108,6 +108,8 @@ typedef struct {
   int n_streams;           /* concurrent launch streams of the serving loop (0: 4)           */
   int pe_tile;             /* FSMP_KERNEL_PE: PEs per chain whose C^-1 stays in shared memory
                               (0: autotuned); a chain moves C^-1 to global memory beyond it */
+  int pe_ctas_per_sm;      /* FSMP_KERNEL_PE: resident CTAs per SM (0: as many as fit); fewer
+                              keep the chains' global C^-1 slots in L2 when chains are large  */
 } fsmp_params;
 
 /* One waveform's posterior summaries (after burn_in steps). t0 is in absolute ns.

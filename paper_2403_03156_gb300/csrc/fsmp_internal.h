@@ -127,7 +127,8 @@ size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
 int pe_ldc(int n_cap);
 cudaError_t pe_kernel_attributes(int precision, int max_smem);
 cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st);
-int pe_kernel_occupancy(int precision, int threads, size_t smem);
+int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big);
+bool pe_big(int n_cap);
 // counter: one int of device memory, zeroed on `st` before the launch.
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas, int Ns, size_t smem, void* cinv,
                       size_t c_stride, double* ws, size_t ws_stride, int* counter, cudaStream_t st);

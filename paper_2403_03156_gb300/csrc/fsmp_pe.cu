@@ -125,6 +125,49 @@ template <typename C> __device__ __forceinline__ C csum_first(C v, int m) {
   return cshfl(v, 0);
 }
 
+// sum_a row[idx[a]] b[a] over a < m (skipping idx[a] == skip), four independent partial sums
+// so that the gathers of consecutive terms overlap
+template <typename C>
+__device__ __forceinline__ C dot_gather(const C* __restrict__ row, const int* __restrict__ idx,
+                                        const C* __restrict__ b, int m, int skip) {
+  C s0 = czero<C>(), s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
+  int a = 0;
+#pragma unroll 1
+  for (; a + 3 < m; a += 4) {
+    const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
+    const C r0 = row[i0], r1 = row[i1], r2 = row[i2], r3 = row[i3];
+    if (i0 != skip) s0 = cfma(r0, b[a], s0);
+    if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
+    if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
+    if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
+  }
+#pragma unroll 1
+  for (; a < m; ++a)
+    if (idx[a] != skip) s0 = cfma(row[idx[a]], b[a], s0);
+  return cadd(cadd(s0, s1), cadd(s2, s3));
+}
+// the same down column `col` of a row-major matrix: sum_a M[idx[a]][col] b[a]
+template <typename C>
+__device__ __forceinline__ C dot_gather_col(const C* __restrict__ Mx, int ld, int col, const int* __restrict__ idx,
+                                            const C* __restrict__ b, int m, int skip) {
+  C s0 = czero<C>(), s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
+  int a = 0;
+#pragma unroll 1
+  for (; a + 3 < m; a += 4) {
+    const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
+    const C r0 = Mx[(size_t)i0 * ld + col], r1 = Mx[(size_t)i1 * ld + col];
+    const C r2 = Mx[(size_t)i2 * ld + col], r3 = Mx[(size_t)i3 * ld + col];
+    if (i0 != skip) s0 = cfma(r0, b[a], s0);
+    if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
+    if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
+    if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
+  }
+#pragma unroll 1
+  for (; a < m; ++a)
+    if (idx[a] != skip) s0 = cfma(Mx[(size_t)idx[a] * ld + col], b[a], s0);
+  return cadd(cadd(s0, s1), cadd(s2, s3));
+}
+
 template <typename T> __device__ __forceinline__ T wsum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -313,7 +356,7 @@ struct RefreshOut {
 // FP64 rebuild of C^-1, v, y, log|Sigma| and the log-likelihood from the PE list (FP32 mode).
 // ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
 // value (no address of the caller's locals escapes, so they stay in registers).
-template <typename T>
+template <typename T, bool BIG>
 __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T> W, typename PeTab<T>::C* Cp, int ld,
                                               double* ws, int n_cap, int lvec, const float* w, int n, int N,
                                               int lane) {
@@ -389,16 +432,31 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
 #pragma unroll 1
     for (int j = lane; j < N; j += 32) colk[j] *= ip;  // the row multipliers
     __syncwarp();
+    // rows i != k: A_ij -= f_i A_kj (A_ik = -f_i); row k: A_kj / pivot. Lanes over columns
+    // (BIG: four rows per iteration so that their loads overlap).
 #pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      double* Ai = A + (size_t)i * ws_ld;
-      if (i == k) {
+    for (int j = lane; j < N; j += 32) {
+      const double rkj = rowk[j];
+      int i = 0;
+      if constexpr (BIG) {
 #pragma unroll 1
-        for (int j = lane; j < N; j += 32) Ai[j] = (j == k) ? ip : rowk[j] * ip;
-      } else {
+        for (; i + 3 < N; i += 4) {
+          double x[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) x[r] = A[(size_t)(i + r) * ws_ld + j];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int ir = i + r;
+            const double f = colk[ir];
+            A[(size_t)ir * ws_ld + j] = (ir == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x[r]));
+          }
+        }
+      }
+#pragma unroll 1
+      for (; i < N; ++i) {
         const double f = colk[i];
-#pragma unroll 1
-        for (int j = lane; j < N; j += 32) Ai[j] = (j == k) ? -f : fma(-f, rowk[j], Ai[j]);
+        const double x = A[(size_t)i * ws_ld + j];
+        A[(size_t)i * ws_ld + j] = (i == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x));
       }
     }
     __syncwarp();
@@ -407,10 +465,18 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
   // v = C^-1 h (C^-1 symmetric: lanes over columns)
 #pragma unroll 1
   for (int i = lane; i < N; i += 32) {
-    double s = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
 #pragma unroll 1
-    for (int j = 0; j < N; ++j) s = fma(A[(size_t)j * ws_ld + i], h[j], s);
-    rowk[i] = s;
+    for (; BIG && j + 3 < N; j += 4) {
+      s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
+      s1 = fma(A[(size_t)(j + 1) * ws_ld + i], h[j + 1], s1);
+      s2 = fma(A[(size_t)(j + 2) * ws_ld + i], h[j + 2], s2);
+      s3 = fma(A[(size_t)(j + 3) * ws_ld + i], h[j + 3], s3);
+    }
+#pragma unroll 1
+    for (; j < N; ++j) s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
+    rowk[i] = (s0 + s1) + (s2 + s3);
   }
   __syncwarp();
   double hv = 0.0;
@@ -467,7 +533,7 @@ template <typename C> struct AcceptOut {
 // Apply an accepted move to C^-1, v, y and the PE list (out of line: it runs on a minority of
 // steps and keeps the per-step code compact). Returns the new N, and the new C^-1 storage when
 // it moves from the shared tile to the global slot.
-template <typename T>
+template <typename T, bool BIG>
 __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel& M, const PeWarp<T> W, const T* Vs,
                                                                   typename PeTab<T>::C* Cp, int ld,
                                                                   typename PeTab<T>::C* Cg, int ldc,
@@ -497,11 +563,15 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   for (int i = lane; i < N; i += 32) {
     const C ci = Cp[(size_t)krow * ld + i];
     W.cv[i] = has_m ? ci : czero<C>();
-    C acc = czero<C>();
+    if constexpr (BIG) {
+      W.uv[i] = npu > 0 ? dot_gather_col<C>(Cp, ld, i, W.ovi, W.ovb, npu, skip) : czero<C>();
+    } else {
+      C acc = czero<C>();
 #pragma unroll 1
-    for (int a = 0; a < npu; ++a)
-      if (W.ovi[a] != skip) acc = cfma(Cp[(size_t)W.ovi[a] * ld + i], W.ovb[a], acc);
-    W.uv[i] = acc;
+      for (int a = 0; a < npu; ++a)
+        if (W.ovi[a] != skip) acc = cfma(Cp[(size_t)W.ovi[a] * ld + i], W.ovb[a], acc);
+      W.uv[i] = acc;
+    }
   }
   if (lane == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth
   __syncwarp();
@@ -557,8 +627,21 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
       const C cj = cmul(W.cv[mj], nig);
       const C uj = cmul(W.uv[j], idl);
       const C sj = (j == s) ? idl : cneg(uj);  // row / column s
+      int i = 0;
 #pragma unroll 1
-      for (int i = 0; i < Nout; ++i) {
+      for (; BIG && i + 3 < Nout; i += 4) {  // four rows per iteration: the loads overlap
+        C x[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[r] = Cp[(size_t)((i + r) == kmap ? last : (i + r)) * ld + mj];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int ir = i + r, mi = (ir == kmap) ? last : ir;
+          const C val = cfma(W.uv[ir], uj, cfma(W.cv[mi], cj, x[r]));
+          Cp[(size_t)ir * ld + j] = (ir == s) ? sj : ((j == s) ? cneg(cmul(W.uv[ir], idl)) : val);
+        }
+      }
+#pragma unroll 1
+      for (; i < Nout; ++i) {
         const int mi = (i == kmap) ? last : i;
         const C val = cfma(W.uv[i], uj, cfma(W.cv[mi], cj, Cp[(size_t)mi * ld + mj]));
         Cp[(size_t)i * ld + j] = (i == s) ? sj : ((j == s) ? cneg(cmul(W.uv[i], idl)) : val);
@@ -597,7 +680,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   return AcceptOut<C>{Cp, ld, Nout, wds};
 }
 
-template <typename T>
+template <typename T, bool BIG>
 __global__ void __launch_bounds__(kPeMaxThreads, 4)
     pe_kernel(const __grid_constant__ DevModel M, const __grid_constant__ BatchView B, const __grid_constant__ PeSlots G) {
   using C = typename PeTab<T>::C;
@@ -844,8 +927,12 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
             if (a < np) {
               const C* Crow = Cp + (size_t)W.ovi[a] * ld;
               C rq = czero<C>();
+              if constexpr (BIG) {
+                rq = dot_gather<C>(Crow, W.ovi, W.ovb, np, -1);
+              } else {
 #pragma unroll 1
-              for (int b = 0; b < np; ++b) rq = cfma(Crow[W.ovi[b]], W.ovb[b], rq);
+                for (int b = 0; b < np; ++b) rq = cfma(Crow[W.ovi[b]], W.ovb[b], rq);
+              }
               const C ba = W.ovb[a];
               qp = cfma(ba, rq, qp);
               bvp = cfma(ba, W.v[W.ovi[a]], bvp);
@@ -916,7 +1003,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       // ---- accepted move: C^-1, v, y and the PE list
       if (apply) {
         {
-          const AcceptOut<C> ao = pe_accept<T>(M, W, Vs, Cp, ld, Cg, G.ldc, mv, n, N, lane);
+          const AcceptOut<C> ao = pe_accept<T, BIG>(M, W, Vs, Cp, ld, Cg, G.ldc, mv, n, N, lane);
           Cp = ao.Cp;
           ld = ao.ld;
           N = ao.N;
@@ -935,7 +1022,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
         __syncwarp();
         if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          const RefreshOut ro = pe_refresh<T>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+          const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
           C qr = czero<C>();
           for (int i = lane; i < N; i += 32) qr = cadd(qr, W.v[i]);
           qr = csum(qr);
@@ -981,7 +1068,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     // ------------------------------------------------------------- chain end
     if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
       // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      const RefreshOut ro = pe_refresh<T>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+      const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
       if (lane == 0) {
         if (ro.ok) {
           S.logdet = ro.logdet; S.logL = ro.logL;
@@ -1041,17 +1128,32 @@ cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t 
   return cudaGetLastError();
 }
 
+// The pile-up variant (BIG) unrolls the gathers and row passes over C^-1 four ways so that
+// their loads overlap; it pays off when chains carry many PEs (C^-1 in global memory) and costs
+// registers otherwise.
+bool pe_big(int n_cap) { return n_cap > 192; }
+
 cudaError_t pe_kernel_attributes(int precision, int max_smem) {
-  if (precision == FSMP_FP64)
-    return cudaFuncSetAttribute(pe_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  return cudaFuncSetAttribute(pe_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaError_t e;
+  if (precision == FSMP_FP64) {
+    e = cudaFuncSetAttribute(pe_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pe_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
+  }
+  e = cudaFuncSetAttribute(pe_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pe_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  return e;
 }
 
-int pe_kernel_occupancy(int precision, int threads, size_t smem) {
+int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big) {
   int n = 0;
-  cudaError_t e = precision == FSMP_FP64
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<double>, threads, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<float>, threads, smem);
+  cudaError_t e;
+  if (precision == FSMP_FP64)
+    e = big ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<double, true>, threads, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<double, false>, threads, smem);
+  else
+    e = big ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<float, true>, threads, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<float, false>, threads, smem);
   return e == cudaSuccess ? n : 0;
 }
 
@@ -1067,8 +1169,14 @@ cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas
   G.Ns = Ns;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  if (M.precision == FSMP_FP64) pe_kernel<double><<<ctas, warps * 32, smem, st>>>(M, B, G);
-  else pe_kernel<float><<<ctas, warps * 32, smem, st>>>(M, B, G);
+  const bool big = pe_big(M.n_cap);
+  if (M.precision == FSMP_FP64) {
+    if (big) pe_kernel<double, true><<<ctas, warps * 32, smem, st>>>(M, B, G);
+    else pe_kernel<double, false><<<ctas, warps * 32, smem, st>>>(M, B, G);
+  } else {
+    if (big) pe_kernel<float, true><<<ctas, warps * 32, smem, st>>>(M, B, G);
+    else pe_kernel<float, false><<<ctas, warps * 32, smem, st>>>(M, B, G);
+  }
   return cudaGetLastError();
 }
 

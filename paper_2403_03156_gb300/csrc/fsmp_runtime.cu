@@ -180,6 +180,7 @@ int validate_params(const fsmp_params* p) {
   if (p->precision != FSMP_FP64 && p->precision != FSMP_FP32_REFRESH) return FSMP_ERR_INVALID;
   if (p->kernel < 0 || p->kernel > 4) return FSMP_ERR_INVALID;
   if (p->pe_tile < 0 || p->pe_tile > 128) return FSMP_ERR_INVALID;
+  if (p->pe_ctas_per_sm < 0 || p->pe_ctas_per_sm > 64) return FSMP_ERR_INVALID;
   if (p->threads_per_chain != 0 && (p->threads_per_chain < 32 || p->threads_per_chain > 512 ||
                                     p->threads_per_chain % 32))
     return FSMP_ERR_INVALID;
@@ -215,8 +216,9 @@ void CUDART_CB pack_done_cb(void* arg) {
 int pe_shape(fsmp_ctx* c, int n_alloc, int* ctas, size_t* smem) {
   *smem = pe_smem_bytes(c->M, n_alloc, c->pe_warps, c->pe_tile);
   if (*smem > (size_t)c->prop.sharedMemPerBlockOptin) return FSMP_ERR_INVALID;
-  const int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem);
+  int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem, pe_big(c->p.n_cap));
   if (per_sm < 1) return FSMP_ERR_INVALID;
+  if (c->p.pe_ctas_per_sm > 0) per_sm = std::min(per_sm, c->p.pe_ctas_per_sm);
   *ctas = per_sm * c->prop.multiProcessorCount;
   return FSMP_OK;
 }
