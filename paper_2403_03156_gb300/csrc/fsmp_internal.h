@@ -124,7 +124,7 @@ cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, d
 // (FP32 mode); row stride of a global C^-1 slot.
 size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns);
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
-int pe_ldc(int n_cap);
+size_t pe_c_entries(int n_cap);  // entries of a global C^-1 slot (packed triangle)
 cudaError_t pe_kernel_attributes(int precision, int max_smem);
 cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st);
 int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big);

@@ -125,47 +125,43 @@ template <typename C> __device__ __forceinline__ C csum_first(C v, int m) {
   return cshfl(v, 0);
 }
 
-// sum_a row[idx[a]] b[a] over a < m (skipping idx[a] == skip), four independent partial sums
-// so that the gathers of consecutive terms overlap
-template <typename C>
-__device__ __forceinline__ C dot_gather(const C* __restrict__ row, const int* __restrict__ idx,
-                                        const C* __restrict__ b, int m, int skip) {
-  C s0 = czero<C>(), s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
-  int a = 0;
-#pragma unroll 1
-  for (; a + 3 < m; a += 4) {
-    const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
-    const C r0 = row[i0], r1 = row[i1], r2 = row[i2], r3 = row[i3];
-    if (i0 != skip) s0 = cfma(r0, b[a], s0);
-    if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
-    if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
-    if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
-  }
-#pragma unroll 1
-  for (; a < m; ++a)
-    if (idx[a] != skip) s0 = cfma(row[idx[a]], b[a], s0);
-  return cadd(cadd(s0, s1), cadd(s2, s3));
+// C^-1 is symmetric and stored as its lower triangle, row by row: entry (i, j), j <= i, at
+// tri(i) + j. The storage has no row stride, so a chain's C^-1 moves from the shared tile to
+// its global slot by a plain copy.
+__host__ __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+__device__ __forceinline__ int pk(int i, int j) { return i >= j ? tri(i) + j : tri(j) + i; }
+// (i, j) of packed position e (j <= i); the FP32 square root is exact enough below 2^22
+__device__ __forceinline__ void untri(int e, int& i, int& j) {
+  i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  if (tri(i + 1) <= e) ++i;
+  if (tri(i) > e) --i;
+  j = e - tri(i);
 }
-// the same down column `col` of a row-major matrix: sum_a M[idx[a]][col] b[a]
-template <typename C>
-__device__ __forceinline__ C dot_gather_col(const C* __restrict__ Mx, int ld, int col, const int* __restrict__ idx,
-                                            const C* __restrict__ b, int m, int skip) {
-  C s0 = czero<C>(), s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
+
+// sum_a C^-1[q][idx[a]] b[a] over a < m (skipping idx[a] == skip); BIG: four independent
+// partial sums so that the gathers of consecutive terms overlap
+template <typename C, bool BIG>
+__device__ __forceinline__ C dot_row(const C* __restrict__ Cp, int q, const int* __restrict__ idx,
+                                     const C* __restrict__ b, int m, int skip) {
+  C s0 = czero<C>();
   int a = 0;
+  if constexpr (BIG) {
+    C s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
 #pragma unroll 1
-  for (; a + 3 < m; a += 4) {
-    const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
-    const C r0 = Mx[(size_t)i0 * ld + col], r1 = Mx[(size_t)i1 * ld + col];
-    const C r2 = Mx[(size_t)i2 * ld + col], r3 = Mx[(size_t)i3 * ld + col];
-    if (i0 != skip) s0 = cfma(r0, b[a], s0);
-    if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
-    if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
-    if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
+    for (; a + 3 < m; a += 4) {
+      const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
+      const C r0 = Cp[pk(q, i0)], r1 = Cp[pk(q, i1)], r2 = Cp[pk(q, i2)], r3 = Cp[pk(q, i3)];
+      if (i0 != skip) s0 = cfma(r0, b[a], s0);
+      if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
+      if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
+      if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
+    }
+    s0 = cadd(cadd(s0, s1), cadd(s2, s3));
   }
 #pragma unroll 1
   for (; a < m; ++a)
-    if (idx[a] != skip) s0 = cfma(Mx[(size_t)idx[a] * ld + col], b[a], s0);
-  return cadd(cadd(s0, s1), cadd(s2, s3));
+    if (idx[a] != skip) s0 = cfma(Cp[pk(q, idx[a])], b[a], s0);
+  return s0;
 }
 
 template <typename T> __device__ __forceinline__ T wsum(T v) {
@@ -293,12 +289,12 @@ template <typename T> struct PeWarp {
   C* uv;       // second work vector [n_cap]
   T* y;        // residual [n_alloc]
   T* lPhi;     // log(Phi_T(t0) g) on the chain's t0 grid [win_extra]
-  C* Cs;       // C^-1 tile [Ns * Ns]
+  C* Cs;       // C^-1 tile: packed triangle of Ns PEs
 };
 template <typename T> __host__ __device__ inline size_t pe_warp_bytes(int n_cap, int n_alloc, int win_extra, int Ns) {
   return a16(sizeof(PeStats)) + a16(sizeof(PeRand<T>) * kPeRB) + 2 * a16(sizeof(int) * n_cap) +
          4 * a16(8 * (size_t)n_cap) + a16(sizeof(T) * n_alloc) + a16(sizeof(T) * win_extra) +
-         a16(8 * (size_t)Ns * Ns);
+         a16(8 * (size_t)tri(Ns));
 }
 template <typename T> __host__ __device__ inline size_t pe_block_bytes(int Lt, int n_cap) {
   return a16(sizeof(T) * Lt) + a16(sizeof(T) * (n_cap + 2));
@@ -323,9 +319,8 @@ template <typename T> __device__ PeWarp<T> pe_carve(unsigned char* p, int n_cap,
 
 // Global per-warp slots.
 struct PeSlots {
-  void* C;             // C^-1 slots (8-byte entries): n_cap rows of ldc entries each
+  void* C;             // C^-1 slots (8-byte entries): the packed triangle of n_cap PEs
   size_t c_stride;     // entries per slot
-  int ldc;
   double* ws;          // FP64 refresh workspace slots (FP32 mode)
   size_t ws_stride;    // doubles per slot
   int* counter;        // next chain of the launch (zeroed before the launch)
@@ -357,13 +352,13 @@ struct RefreshOut {
 // ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
 // value (no address of the caller's locals escapes, so they stay in registers).
 template <typename T, bool BIG>
-__device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T> W, typename PeTab<T>::C* Cp, int ld,
+__device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T> W, typename PeTab<T>::C* Cp,
                                               double* ws, int n_cap, int lvec, const float* w, int n, int N,
                                               int lane) {
   using C = typename PeTab<T>::C;
   RefreshOut out{0, 0.0, 0.0, 0.0};
-  const int ws_ld = n_cap;
-  double* A = ws;                               // C, then C^-1 (row-major, stride n_cap)
+  const int ws_ld = N > 0 ? N : 1;
+  double* A = ws;                               // C, then C^-1 (row-major N x N)
   double* yres = A + (size_t)n_cap * n_cap;     // residual y (FP64)
   double* h = yres + lvec;                      // A^T y
   double* rowk = h + lvec;                      // staged pivot row
@@ -487,17 +482,16 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
 #pragma unroll 1
   for (int x = lane; x < n; x += 32) yy += yres[x] * yres[x];
   yy = wsum(yy);
-  // drift of the incremental state, then the refreshed state
+  // drift of the incremental state, then the refreshed state (packed lower triangle)
   double dmax = 0.0, amax = 0.0;
 #pragma unroll 1
-  for (int i = 0; i < N; ++i) {
-#pragma unroll 1
-    for (int j = lane; j < N; j += 32) {
-      const double nv = A[(size_t)i * ws_ld + j];
-      dmax = fmax(dmax, fabs(nv - c64(Cp[(size_t)i * ld + j])));
-      amax = fmax(amax, fabs(nv));
-      Cp[(size_t)i * ld + j] = cfrom64<C>(nv);
-    }
+  for (int e = lane; e < tri(N); e += 32) {
+    int i, j;
+    untri(e, i, j);
+    const double nv = A[(size_t)i * ws_ld + j];
+    dmax = fmax(dmax, fabs(nv - c64(Cp[e])));
+    amax = fmax(amax, fabs(nv));
+    Cp[e] = cfrom64<C>(nv);
   }
   double vd = 0.0, va = 0.0;
 #pragma unroll 1
@@ -526,17 +520,17 @@ template <typename C> struct PeMove {
 
 template <typename C> struct AcceptOut {
   C* Cp;
-  int ld, N;
+  int cap, N;
   unsigned long long words;
 };
 
 // Apply an accepted move to C^-1, v, y and the PE list (out of line: it runs on a minority of
 // steps and keeps the per-step code compact). Returns the new N, and the new C^-1 storage when
-// it moves from the shared tile to the global slot.
+// it moves from the shared tile (capacity cap PEs) to the global slot (n_cap PEs).
 template <typename T, bool BIG>
 __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel& M, const PeWarp<T> W, const T* Vs,
-                                                                  typename PeTab<T>::C* Cp, int ld,
-                                                                  typename PeTab<T>::C* Cg, int ldc,
+                                                                  typename PeTab<T>::C* Cp, int cap,
+                                                                  typename PeTab<T>::C* Cg,
                                                                   const PeMove<typename PeTab<T>::C> mv, int n, int N,
                                                                   int lane) {
   // One form for the three moves. With c = row k of C^-1 (death, update), gamma = c_k, and
@@ -561,19 +555,11 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   const int npu = has_p ? np : 0;
 #pragma unroll 1
   for (int i = lane; i < N; i += 32) {
-    const C ci = Cp[(size_t)krow * ld + i];
+    const C ci = Cp[pk(krow, i)];
     W.cv[i] = has_m ? ci : czero<C>();
-    if constexpr (BIG) {
-      W.uv[i] = npu > 0 ? dot_gather_col<C>(Cp, ld, i, W.ovi, W.ovb, npu, skip) : czero<C>();
-    } else {
-      C acc = czero<C>();
-#pragma unroll 1
-      for (int a = 0; a < npu; ++a)
-        if (W.ovi[a] != skip) acc = cfma(Cp[(size_t)W.ovi[a] * ld + i], W.ovb[a], acc);
-      W.uv[i] = acc;
-    }
+    W.uv[i] = dot_row<C, BIG>(Cp, i, W.ovi, W.ovb, npu, skip);
   }
-  if (lane == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth
+  if (lane == 0 && jump == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth (N < n_cap)
   __syncwarp();
   C ig = czero<C>(), idl = czero<C>(), t = czero<C>(), fv = czero<C>();
   if (has_m) {
@@ -606,47 +592,26 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     const C hnew = csub(cadd(mv.ay, cmul(mu, bk)), cmul(mu, mv.aa));
     t = cmul(csub(csub(bvm, cmul(mu, bu)), hnew), idl);
   }
-  if (jump == 0 && N + 1 > ld && Cp != Cg) {  // the tile is full: move C^-1 to the global slot
+  if (jump == 0 && N + 1 > cap && Cp != Cg) {  // the tile is full: move C^-1 to the global slot
 #pragma unroll 1
-    for (int i = 0; i < N; ++i)
-#pragma unroll 1
-      for (int j = lane; j < N; j += 32) Cg[(size_t)i * ldc + j] = Cp[(size_t)i * ld + j];
+    for (int e = lane; e < tri(N); e += 32) Cg[e] = Cp[e];
     Cp = Cg;
-    ld = ldc;
+    cap = M.n_cap;
     __syncwarp();
   }
-  // C^-1 in place: reads never touch a cell written earlier in the pass (row / column k are only
-  // read through cv, and the last row / column are read but not written for a death)
+  // C^-1 in place over the packed triangle, all lanes on consecutive entries. A pass reads an
+  // entry only where it writes it, or in the last row for a death (which it does not write).
   const C nig = cneg(ig);
   const int kmap = jump == 1 ? kk : -1;  // the slot the last PE moves into
 #pragma unroll 1
-  for (int j0 = 0; j0 < Nout; j0 += 32) {
-    const int j = j0 + lane;
-    if (j < Nout) {
-      const int mj = (j == kmap) ? last : j;
-      const C cj = cmul(W.cv[mj], nig);
-      const C uj = cmul(W.uv[j], idl);
-      const C sj = (j == s) ? idl : cneg(uj);  // row / column s
-      int i = 0;
-#pragma unroll 1
-      for (; BIG && i + 3 < Nout; i += 4) {  // four rows per iteration: the loads overlap
-        C x[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) x[r] = Cp[(size_t)((i + r) == kmap ? last : (i + r)) * ld + mj];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int ir = i + r, mi = (ir == kmap) ? last : ir;
-          const C val = cfma(W.uv[ir], uj, cfma(W.cv[mi], cj, x[r]));
-          Cp[(size_t)ir * ld + j] = (ir == s) ? sj : ((j == s) ? cneg(cmul(W.uv[ir], idl)) : val);
-        }
-      }
-#pragma unroll 1
-      for (; i < Nout; ++i) {
-        const int mi = (i == kmap) ? last : i;
-        const C val = cfma(W.uv[i], uj, cfma(W.cv[mi], cj, Cp[(size_t)mi * ld + mj]));
-        Cp[(size_t)i * ld + j] = (i == s) ? sj : ((j == s) ? cneg(cmul(W.uv[i], idl)) : val);
-      }
-    }
+  for (int e = lane; e < tri(Nout); e += 32) {  // rows 0 .. Nout-1
+    int i, j;
+    untri(e, i, j);
+    const int mi = (i == kmap) ? last : i, mj = (j == kmap) ? last : j;
+    const C old = Cp[pk(mi, mj)];
+    const C val = cfma(W.uv[i], cmul(W.uv[j], idl), cfma(W.cv[mi], cmul(W.cv[mj], nig), old));
+    const C sv = (i == s && j == s) ? idl : cneg(cmul(W.uv[i == s ? j : i], idl));
+    Cp[e] = (i == s || j == s) ? sv : val;
   }
   // v' = v_m - c_m fv + (t - mu) u', v'_s = -t
   const C tm = csub(t, mu), nfv = cneg(fv);
@@ -657,7 +622,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     W.v[i] = (i == s) ? cneg(t) : val;
   }
   // residual and PE list
-  unsigned long long wds = (unsigned long long)N * np + 2ull * Nout * Nout + 2ull * Nout;
+  unsigned long long wds = (unsigned long long)N * np + 2ull * tri(Nout) + 2ull * Nout;
   if (has_m) {
     const Sup sm = pe_sup(M, n, mv.jm);
 #pragma unroll 1
@@ -677,7 +642,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     else W.list[kk] = mv.jp;
   }
   __syncwarp();
-  return AcceptOut<C>{Cp, ld, Nout, wds};
+  return AcceptOut<C>{Cp, cap, Nout, wds};
 }
 
 template <typename T, bool BIG>
@@ -780,8 +745,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     }
     __syncwarp();
     const T log_lambda0 = fp32 ? (T)logf((float)lambda0) : (T)log(lambda0);
-    C* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1, row stride ld
-    int ld = Ns > 0 ? Ns : G.ldc;
+    C* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1 (packed), room for cap PEs
+    int cap = Ns > 0 ? Ns : n_cap;
     int N = 0;
 
     for (int step = 0; step < n_steps; ++step) {
@@ -925,14 +890,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           for (int a0 = 0; a0 < np; a0 += 32) {
             const int a = a0 + lane;
             if (a < np) {
-              const C* Crow = Cp + (size_t)W.ovi[a] * ld;
-              C rq = czero<C>();
-              if constexpr (BIG) {
-                rq = dot_gather<C>(Crow, W.ovi, W.ovb, np, -1);
-              } else {
-#pragma unroll 1
-                for (int b = 0; b < np; ++b) rq = cfma(Crow[W.ovi[b]], W.ovb[b], rq);
-              }
+              const C rq = dot_row<C, BIG>(Cp, W.ovi[a], W.ovi, W.ovb, np, -1);
               const C ba = W.ovb[a];
               qp = cfma(ba, rq, qp);
               bvp = cfma(ba, W.v[W.ovi[a]], bvp);
@@ -956,7 +914,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
               ck = cshfl(ck, __ffs(hk) - 1);
             } else {
               C c2 = czero<C>();
-              for (int a = lane; a < np; a += 32) c2 = cfma(Cp[(size_t)kk * ld + W.ovi[a]], W.ovb[a], c2);
+              for (int a = lane; a < np; a += 32) c2 = cfma(Cp[pk(kk, W.ovi[a])], W.ovb[a], c2);
               ck = csum(c2);
             }
           }
@@ -967,7 +925,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
         if (jump != 0) {
           mv.vk = W.v[kk];
-          em = rrT * (T)cnum(Cp[(size_t)kk * ld + kk]);
+          em = rrT * (T)cnum(Cp[tri(kk) + kk]);
           mmm = ((T)1 - em) * iqT;
           gm = (T)cnum(mv.vk) * iqT;
           words += 2;
@@ -1003,9 +961,9 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       // ---- accepted move: C^-1, v, y and the PE list
       if (apply) {
         {
-          const AcceptOut<C> ao = pe_accept<T, BIG>(M, W, Vs, Cp, ld, Cg, G.ldc, mv, n, N, lane);
+          const AcceptOut<C> ao = pe_accept<T, BIG>(M, W, Vs, Cp, cap, Cg, mv, n, N, lane);
           Cp = ao.Cp;
-          ld = ao.ld;
+          cap = ao.cap;
           N = ao.N;
           words += ao.words;
         }
@@ -1022,7 +980,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
         __syncwarp();
         if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+          const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
           C qr = czero<C>();
           for (int i = lane; i < N; i += 32) qr = cadd(qr, W.v[i]);
           qr = csum(qr);
@@ -1068,7 +1026,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     // ------------------------------------------------------------- chain end
     if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
       // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ld, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+      const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
       if (lane == 0) {
         if (ro.ok) {
           S.logdet = ro.logdet; S.logL = ro.logL;
@@ -1120,7 +1078,7 @@ size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns) {
 
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc) { return pe_ws_doubles(n_cap, n_alloc); }
 
-int pe_ldc(int n_cap) { return (n_cap + 31) / 32 * 32; }
+size_t pe_c_entries(int n_cap) { return (size_t)tri(n_cap); }
 
 cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -1162,7 +1120,6 @@ cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas
   PeSlots G;
   G.C = cinv;
   G.c_stride = c_stride;
-  G.ldc = pe_ldc(M.n_cap);
   G.ws = ws;
   G.ws_stride = ws_stride;
   G.counter = counter;

@@ -739,7 +739,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   if (p.kernel == FSMP_KERNEL_PE) {
     c->pe_warps = p.threads_per_chain > 0 ? std::min(4, p.threads_per_chain / 32) : 4;
     const size_t esz = 8;  // C^-1 is FP64 in both modes
-    c->pe_tile = p.pe_tile > 0 ? std::min(p.pe_tile, p.n_cap) : std::min(p.n_cap, 24);
+    c->pe_tile = p.pe_tile > 0 ? std::min(p.pe_tile, p.n_cap) : std::min(p.n_cap, 32);
     CK(pe_kernel_attributes(p.precision, max_smem));
     int slots = 0;
     for (int nn : {std::min(64, p.n_max), p.n_max}) {
@@ -749,8 +749,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     }
     if (slots < 1) FAIL(FSMP_ERR_INVALID, "n_max too large for the PE-space kernel");
     c->pe_slots = slots;
-    const int ldc = pe_ldc(p.n_cap);
-    c->pe_c_stride = c->pe_tile < p.n_cap ? (size_t)p.n_cap * ldc : 0;
+    c->pe_c_stride = c->pe_tile < p.n_cap ? pe_c_entries(p.n_cap) : 0;
     c->pe_ws_stride = p.precision == FSMP_FP64 ? 0 : pe_ws_slot_doubles(p.n_cap, p.n_max);
     for (int i = 0; i <= p.n_streams; ++i) {
       fsmp_ctx::PeSet ps;
