@@ -86,14 +86,13 @@ def shard_workload(args, rank):
         cfg = workloads.CONFIGS[args.workload]
         return dict(name=args.workload, params=params, batch=batch,
                     meta=dict(precision=cfg["precision"], refresh_every=cfg.get("refresh_every", 0)))
-    wl = workloads.make_workload(args.workload, n_waveforms=args.n_waveforms or None,
-                                 seed=args.seed + 1000 * rank, n_steps=args.mcmc_steps or None)
+    from paper_2403_03156_gb300 import sharding
+    # RNG ids unique across ranks: rank r owns waveforms [r W, (r+1) W) of the job
+    wl = sharding.rank_workload(args.workload, rank, n_waveforms=args.n_waveforms or None, seed=args.seed,
+                                n_steps=args.mcmc_steps or None)
     # burn-in of one fifth of the chain for the posterior summaries (it costs the same steps)
     wl["batch"]["burn_in"] = int(wl["batch"]["n_steps"]) // 5
     b = wl["batch"]
-    W = len(b["offsets"]) - 1
-    # RNG ids unique across ranks: rank r owns waveforms [r W, (r+1) W) of the job
-    b["wf_ids"] = (np.arange(W, dtype=np.uint64) + np.uint64(rank * W))
     if args.window_range:
         lo, hi = (int(x) for x in args.window_range.split(","))
         n = np.diff(b["offsets"])
@@ -294,7 +293,7 @@ def load_traffic(kernel_src, name):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_2403_03156_gb300 import build, fsmp, workloads
+    from paper_2403_03156_gb300 import build, fsmp, sharding, workloads
 
     rank, world, local = dist_env()
     if world > 1:
@@ -376,15 +375,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-        tw = torch.tensor([W], dtype=torch.float64, device=dev)
-        dist.all_reduce(tw, op=dist.ReduceOp.SUM)
-        W_total = int(tw.item())
-    else:
-        W_total = W
+    W_total, elapsed_ms = sharding.job_totals(dist if world > 1 else None, W, elapsed_ms, device=dev)
     ms_per_step = elapsed_ms / args.steps
     value = W_total * n_steps / (ms_per_step / 1000.0)
 
