@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="PE kernel: resident CTAs per SM (0: max)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "smem", "global", "plain", "pe"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="PE kernel: keep the default launch shape")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
     ap.add_argument("--seed", type=int, default=0)
@@ -320,6 +321,10 @@ def run_ours(args):
     n_steps = int(b["n_steps"])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tuned = None
+    if pe and not args.no_autotune:  # launch shape from timed trials on a sample (not timed)
+        t0_, nm0, _ = subs[0]
+        tuned = ctx.autotune(t0_, sample=8192, trial_steps=128, seed=int(b["seed"]), n_max_hint=nm0)
 
     def one_step(ev=None):
         for k, (t, nm, _) in enumerate(subs):
@@ -420,7 +425,7 @@ def run_ours(args):
                        "refresh_every": params["refresh_every"],
                        "window_samples": [int(lengths.min()), int(np.median(lengths)), int(lengths.max())],
                        "launches_per_step": len(subs), "threads_per_chain": info["threads_per_chain"],
-                       "cuda_graph": graph is not None,
+                       "cuda_graph": graph is not None, "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "accept_rate": float(acc.sum() / max(1, prop.sum())),
                        "accepts_per_type": [int(x) for x in acc], "proposals_per_type": [int(x) for x in prop]},

@@ -224,6 +224,27 @@ int fsmp_destroy(fsmp_ctx* ctx);
  * launch fails. */
 int fsmp_run_device(fsmp_ctx* ctx, const fsmp_device_batch* batch, void* stream);
 
+/* Launch shape of the PE-space kernel chosen by fsmp_autotune. */
+typedef struct {
+  int pe_tile;                   /* PEs per chain whose C^-1 stays in shared memory          */
+  int chains_per_cta;            /* warps (one chain each) per CTA                           */
+  int ctas_per_sm;               /* resident CTAs per SM (0: as many as fit)                 */
+  int n_tried;                   /* candidate shapes timed                                   */
+  double best_steps_per_s;       /* MCMC steps/s of the chosen shape on the trial            */
+  double default_steps_per_s;    /* the same for the shape the context started with          */
+} fsmp_tune;
+
+/* Autotune the launch shape of the PE-space kernel (FSMP_KERNEL_PE contexts) on a device
+ * batch laid out as for fsmp_run_device: time trial runs of its first `sample` waveforms for
+ * `trial_steps` MCMC steps in each candidate shape -- shared-memory tile of C^-1, chains per
+ * CTA and resident CTAs per SM -- and keep the fastest for the context's later launches. The
+ * batch's own output and trace buffers are not touched (the trials write to scratch), and
+ * later results do not depend on the shape: a chain's arithmetic is the same in every one.
+ * Blocks until the trials finish. Call it with no request in flight on the context. Returns
+ * FSMP_OK (out, if not NULL, describes the choice), FSMP_ERR_INVALID (not a PE-space context,
+ * bad arguments) or FSMP_ERR_CUDA / FSMP_ERR_NOMEM. */
+int fsmp_autotune(fsmp_ctx* ctx, const fsmp_device_batch* batch, int sample, int trial_steps, fsmp_tune* out);
+
 /* fsmp_run_device for callers that cannot allocate device memory. The paper has no
  * counterpart: this is an integration aid. Some callers cannot call cudaMalloc -- code that
  * runs under a framework allocator owning all device memory, or in a service that forbids

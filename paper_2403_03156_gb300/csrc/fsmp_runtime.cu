@@ -109,6 +109,7 @@ struct fsmp_ctx {
   int pe_slots = 0, pe_warps = 4, pe_tile = 0;
   size_t pe_c_stride = 0, pe_ws_stride = 0, pe_bytes = 0;
   std::atomic<long long> n_launches{0};  // chain-kernel launches
+  std::mutex tune_mu;                    // serialises fsmp_autotune calls
   // serving loop
   std::vector<cudaStream_t> streams;
   cudaStream_t gmem_stream = nullptr;
@@ -854,6 +855,100 @@ int fsmp_run_device(fsmp_ctx* c, const fsmp_device_batch* b, void* stream) {
   B.out = b->out; B.trace = b->trace;
   { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   return run_view(c, B, (cudaStream_t)stream, (int)c->streams.size());
+}
+
+int fsmp_autotune(fsmp_ctx* c, const fsmp_device_batch* b, int sample, int trial_steps, fsmp_tune* out) {
+  g_last_error[0] = 0;
+  if (!c || !b || b->n_waveforms < 1 || !b->samples || !b->offsets || !b->lambda0 || sample < 1 || trial_steps < 1)
+    FAIL(FSMP_ERR_INVALID, "fsmp_autotune: bad arguments");
+  if (c->p.kernel != FSMP_KERNEL_PE || c->pe_sets.empty()) FAIL(FSMP_ERR_INVALID, "fsmp_autotune needs a PE-space context");
+  { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
+  std::lock_guard<std::mutex> lk(c->tune_mu);
+  const int W = std::min(sample, b->n_waveforms);
+  BatchView B{};
+  B.n_waveforms = W;
+  B.n_steps = trial_steps;
+  B.burn_in = 0;
+  B.n_max = b->n_max_hint > 0 ? b->n_max_hint : c->p.n_max;
+  if (B.n_max > c->p.n_max) FAIL(FSMP_ERR_INVALID, "fsmp_autotune: window longer than n_max");
+  B.seed = b->seed;
+  B.index_base = b->index_base;
+  B.samples = b->samples; B.offsets = b->offsets; B.lambda0 = b->lambda0; B.t_origin = b->t_origin_ns;
+  B.T_lo = b->T_lo; B.T_hi = b->T_hi; B.t0_init = b->t0_init; B.wf_ids = b->wf_ids;
+  fsmp_summary* scratch = nullptr;
+  CK(cudaMalloc(&scratch, sizeof(fsmp_summary) * (size_t)W));
+  B.out = scratch;
+  B.trace = nullptr;
+  cudaStream_t st = c->gmem_stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int set = (int)c->streams.size();
+  const int tile0 = c->pe_tile, warps0 = c->pe_warps, ctas0 = c->p.pe_ctas_per_sm;
+  auto trial = [&](int tile, int warps, int ctas, double* rate) -> int {
+    c->pe_tile = tile; c->pe_warps = warps; c->p.pe_ctas_per_sm = ctas;
+    int cc = 0;
+    size_t sm = 0;
+    if (pe_shape(c, B.n_max, &cc, &sm) != FSMP_OK) { *rate = -1.0; return FSMP_OK; }
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches and the code
+      if (cudaEventRecord(e0, st) != cudaSuccess) return FSMP_ERR_CUDA;
+      int rc = run_pe(c, B, set, st);
+      if (rc) return rc;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return FSMP_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best_ms = std::min(best_ms, ms);
+    }
+    *rate = (double)W * trial_steps / (best_ms * 1e-3);
+    return FSMP_OK;
+  };
+  // candidates: a tile needs the global C^-1 slots unless it covers n_cap
+  const bool have_slots = c->pe_c_stride > 0;
+  std::vector<int> tiles;
+  for (int t : {8, 16, 24, 32, 48, 64})
+    if (t < c->p.n_cap ? have_slots : true) tiles.push_back(std::min(t, c->p.n_cap));
+  if (!have_slots) tiles = {tile0};
+  std::sort(tiles.begin(), tiles.end());
+  tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
+  double r0 = 0.0, best = -1.0;
+  int bt = tile0, bw = warps0, bc = ctas0, n_tried = 0;
+  int rc = trial(tile0, warps0, ctas0, &r0);
+  if (rc == FSMP_OK) {
+    best = r0; ++n_tried;
+    // coordinate search: tile, then chains per CTA, then resident CTAs per SM
+    for (int t : tiles) {
+      double r;
+      if ((rc = trial(t, bw, bc, &r)) != FSMP_OK) break;
+      ++n_tried;
+      if (r > best) { best = r; bt = t; }
+    }
+    for (int w : {1, 2, 4}) {
+      double r;
+      if (rc != FSMP_OK || (rc = trial(bt, w, bc, &r)) != FSMP_OK) break;
+      ++n_tried;
+      if (r > best) { best = r; bw = w; }
+    }
+    for (int k : {1, 2, 3}) {
+      double r;
+      if (rc != FSMP_OK || (rc = trial(bt, bw, k, &r)) != FSMP_OK) break;
+      ++n_tried;
+      if (r > best) { best = r; bc = k; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  if (rc != FSMP_OK) {
+    c->pe_tile = tile0; c->pe_warps = warps0; c->p.pe_ctas_per_sm = ctas0;
+    return rc;
+  }
+  c->pe_tile = bt; c->pe_warps = bw; c->p.pe_ctas_per_sm = bc;
+  if (out) {
+    out->pe_tile = bt; out->chains_per_cta = bw; out->ctas_per_sm = bc; out->n_tried = n_tried;
+    out->best_steps_per_s = best; out->default_steps_per_s = r0;
+  }
+  return FSMP_OK;
 }
 
 int fsmp_get_tables(fsmp_ctx* c, double* ser_out, int max_ser, int* ser_len, int d_lo, int count,

@@ -69,6 +69,11 @@ class DeviceBatch(ctypes.Structure):
                 ("trace", _vp)]
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("pe_tile", _c_int), ("chains_per_cta", _c_int), ("ctas_per_sm", _c_int), ("n_tried", _c_int),
+                ("best_steps_per_s", _c_double), ("default_steps_per_s", _c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("device", _c_int), ("sm_count", _c_int), ("smem_per_block_optin", _c_int),
                 ("ser_len", _c_int), ("R", _c_int), ("L_V", _c_int), ("n_smem_max", _c_int),
@@ -79,7 +84,7 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
-           "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc"]
+           "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc", "fsmp_autotune"]
 
 _lib = None
 
@@ -105,6 +110,7 @@ def load(build_if_missing: bool = False):
     L.fsmp_destroy.argtypes = [_vp]
     L.fsmp_run_device.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _vp]
     L.fsmp_run_device_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(DeviceBatch), _vp]
+    L.fsmp_autotune.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _c_int, _c_int, ctypes.POINTER(Tune)]
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
     L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
     L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
@@ -277,6 +283,16 @@ class Context:
         b.out, b.trace = p("out"), p("trace")
         st = None if stream is None else int(stream.cuda_stream)
         _check(load().fsmp_run_device(self.h, ctypes.byref(b), st), "fsmp_run_device")
+
+    def autotune(self, dev: dict, sample: int = 8192, trial_steps: int = 128, n_steps: int = 0, seed: int = 0,
+                 n_max_hint: int = 0) -> dict:
+        """fsmp_autotune on device tensors laid out as for run_device: times trial runs of
+        the first `sample` waveforms in candidate launch shapes and keeps the fastest."""
+        b = _device_batch(dev, n_steps, 0, seed, 0, n_max_hint)
+        t = Tune()
+        _check(load().fsmp_autotune(self.h, ctypes.byref(b), int(sample), int(trial_steps), ctypes.byref(t)),
+               "fsmp_autotune")
+        return {k: getattr(t, k) for k, _ in Tune._fields_}
 
     # ---------------------------------------------------------------- testing aids
     def tables(self, d_lo: int = 0, count: int = 0):

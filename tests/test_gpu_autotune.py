@@ -1,0 +1,45 @@
+"""fsmp_autotune: the chosen launch shape is valid and the chains' results do not depend on it."""
+import numpy as np
+import pytest
+
+from paper_2403_03156_gb300 import fsmp, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_03156_gb300 import build
+    build.build()
+    return fsmp.load()
+
+
+def test_autotune_keeps_results(lib):
+    torch = pytest.importorskip("torch")
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=2000, n_steps=300, seed=9, burn_in=50)
+    b = wl["batch"]
+    n_max = int(np.diff(b["offsets"]).max())
+    dev = torch.device("cuda", 0)
+    W = len(b["offsets"]) - 1
+    t = {"samples": torch.from_numpy(b["samples"]).to(dev),
+         "offsets": torch.from_numpy(b["offsets"].astype(np.int32)).to(dev),
+         "lambda0": torch.from_numpy(b["lambda0"]).to(dev),
+         "t_origin_ns": torch.from_numpy(b["t_origin_ns"]).to(dev),
+         "T_lo": torch.from_numpy(b["T_lo"]).to(dev), "T_hi": torch.from_numpy(b["T_hi"]).to(dev)}
+    params = dict(wl["params"], precision=fsmp.FP32_REFRESH, refresh_every=64, n_max=n_max, kernel=fsmp.KERNEL_PE)
+    with fsmp.Context(params) as ctx:
+        out0 = torch.zeros(W * fsmp.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        ctx.run_device(dict(t, out=out0), n_steps=300, burn_in=50, seed=b["seed"], n_max_hint=n_max)
+        torch.cuda.synchronize()
+        tune = ctx.autotune(t, sample=1000, trial_steps=64, seed=b["seed"], n_max_hint=n_max)
+        assert tune["n_tried"] >= 2
+        assert 1 <= tune["chains_per_cta"] <= 4 and tune["pe_tile"] >= 1 and tune["ctas_per_sm"] >= 0
+        assert tune["best_steps_per_s"] >= tune["default_steps_per_s"] > 0
+        out1 = torch.zeros_like(out0)
+        ctx.run_device(dict(t, out=out1), n_steps=300, burn_in=50, seed=b["seed"], n_max_hint=n_max)
+        torch.cuda.synchronize()
+    s0 = fsmp.summaries_from_bytes(out0.cpu().numpy())
+    s1 = fsmp.summaries_from_bytes(out1.cpu().numpy())
+    for f in ("mean_N", "var_N", "mean_t0", "mean_Q", "var_Q", "logL", "logdet", "acc", "prop", "N_final", "status"):
+        np.testing.assert_array_equal(s0[f], s1[f], err_msg=f)
+    print("autotune:", tune)
