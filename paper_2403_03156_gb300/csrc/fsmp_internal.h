@@ -24,6 +24,7 @@ struct DevModel {
   int win_extra;              // phi window per chain: n R + win_extra grid offsets (t0 range + 2)
   double mu_q, sigma_q, sq2, se2, inv_se2;
   double log_se2, log_r;       // log sigma_eps^2 and log(sigma_eps^2 / sigma_q^2)
+  float mu_hi, mu_lo, r_hi, r_lo;  // mu_q and sigma_eps^2 / sigma_q^2 as float pairs (hi + lo)
   double t0_lo, t0_hi;
   int sample_t0;
   double J, log_J;
@@ -44,6 +45,12 @@ struct DevModel {
   const float* tcff;          // float-float pairs (hi, lo) of tc64
   int tcM;                    // rows per phase: ceil(Lt / R) + 1
 };
+
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi) (host side).
+inline void split_pair(double x, float* hi, float* lo) {
+  *hi = (float)x;
+  *lo = (float)(x - (double)*hi);
+}
 
 // Rows per phase of the cross-correlation table: prefix lengths 0 .. ceil(Lt / R).
 FSMP_HD int xcorr_rows(int Lt, int R) { return (Lt + R - 1) / R + 1; }

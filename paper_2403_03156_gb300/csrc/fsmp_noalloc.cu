@@ -173,6 +173,7 @@ extern "C" int fsmp_run_device_noalloc(const fsmp_params* p, const fsmp_device_b
     M.mu_q = p->mu_q; M.sigma_q = p->sigma_q; M.sq2 = p->sigma_q * p->sigma_q;
     M.se2 = p->sigma_noise * p->sigma_noise; M.inv_se2 = 1.0 / M.se2;
     M.log_se2 = log(M.se2); M.log_r = log(M.se2 / M.sq2);
+    split_pair(M.mu_q, &M.mu_hi, &M.mu_lo); split_pair(M.se2 / M.sq2, &M.r_hi, &M.r_lo);
     M.t0_lo = p->t0_lo; M.t0_hi = p->t0_hi; M.sample_t0 = p->sample_t0 ? 1 : 0;
     M.J = p->jump_J; M.log_J = log(p->jump_J);
     M.n_cap = p->n_cap;

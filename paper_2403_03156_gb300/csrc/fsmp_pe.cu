@@ -110,8 +110,13 @@ template <> __device__ __forceinline__ ff cfrom64<ff>(double a) {
   const float h = (float)a;
   return ff{h, (float)(a - (double)h)};
 }
-// a model constant as a state value
-template <typename C> __device__ __forceinline__ C cconst(double a) { return cfrom64<C>(a); }
+// mu_q and r = sigma_eps^2 / sigma_q^2 as state values (split into pairs on the host)
+template <typename C> __device__ __forceinline__ C c_mu(const DevModel& M);
+template <> __device__ __forceinline__ double c_mu<double>(const DevModel& M) { return M.mu_q; }
+template <> __device__ __forceinline__ ff c_mu<ff>(const DevModel& M) { return ff{M.mu_hi, M.mu_lo}; }
+template <typename C> __device__ __forceinline__ C c_r(const DevModel& M);
+template <> __device__ __forceinline__ double c_r<double>(const DevModel& M) { return M.se2 / M.sq2; }
+template <> __device__ __forceinline__ ff c_r<ff>(const DevModel& M) { return ff{M.r_hi, M.r_lo}; }
 
 // warp sums of state values: over all lanes, or over lanes [0, m) (zero beyond m)
 template <typename C> __device__ __forceinline__ C csum(C v) {
@@ -269,7 +274,7 @@ __device__ __forceinline__ float u01_float(uint64_t x) {
 // Per-chain statistics (shared memory, written by lane 0).
 struct PeStats {
   long long sN, sN2, sK, sK2;
-  double sQ, sQ2, q_cur, logdet, logL, drift_max;
+  double sQ, sQ2, q_cur, logdet, logL, drift_max, wsq;
   unsigned long long alg_words;
   int acc[3], prop[3], acc_t0, prop_t0, n_refresh, status, q_from, n_acc_refresh, refresh_fail, pad;
 };
@@ -353,29 +358,17 @@ struct RefreshOut {
 // value (no address of the caller's locals escapes, so they stay in registers).
 template <typename T, bool BIG>
 __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T> W, typename PeTab<T>::C* Cp,
-                                              double* ws, int n_cap, int lvec, const float* w, int n, int N,
-                                              int lane) {
+                                              double* ws, int n_cap, int lvec, const float* w, double wsq, int n,
+                                              int N, int lane) {
   using C = typename PeTab<T>::C;
   RefreshOut out{0, 0.0, 0.0, 0.0};
   const int ws_ld = N > 0 ? N : 1;
   double* A = ws;                               // C, then C^-1 (row-major N x N)
-  double* yres = A + (size_t)n_cap * n_cap;     // residual y (FP64)
-  double* h = yres + lvec;                      // A^T y
+  double* h = A + (size_t)n_cap * n_cap;        // A^T y
   double* rowk = h + lvec;                      // staged pivot row
   double* colk = rowk + lvec;                   // staged pivot column
   const double* V = M.V64;
   const double mu = M.mu_q, r = M.se2 / M.sq2;
-  // residual y = w - mu sum_k a_k
-#pragma unroll 1
-  for (int x = lane; x < n; x += 32) yres[x] = (double)w[x];
-  __syncwarp();
-#pragma unroll 1
-  for (int k = 0; k < N; ++k) {
-    const Sup s = pe_sup(M, n, W.list[k]);
-#pragma unroll 1
-    for (int i = s.ilo + lane; i < s.ihi; i += 32) yres[s.w0 + i] -= mu * V[s.ph + i * M.R];
-    __syncwarp();
-  }
   // C = r I + A^T A (full, row-major)
 #pragma unroll 1
   for (int i = 0; i < N; ++i) {
@@ -389,7 +382,10 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
       A[(size_t)i * ws_ld + j] = c;
     }
   }
-  // h = A^T y
+  __syncwarp();
+  // With y = w - mu A 1: h = A^T y = A^T w - mu (A^T A) 1, and
+  // y^T y = w^T w - 2 mu 1^T A^T w + mu^2 1^T A^T A 1 -- no FP64 copy of y is needed.
+  double awt = 0.0, rst = 0.0;
 #pragma unroll 1
   for (int k = lane; k < N; k += 32) {
     const Sup s = pe_sup(M, n, W.list[k]);
@@ -397,11 +393,31 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     int i = s.ilo;
 #pragma unroll 1
     for (; i + 1 < s.ihi; i += 2) {
-      a0 = fma(V[s.ph + i * M.R], yres[s.w0 + i], a0);
-      a1 = fma(V[s.ph + (i + 1) * M.R], yres[s.w0 + i + 1], a1);
+      a0 = fma(V[s.ph + i * M.R], (double)w[s.w0 + i], a0);
+      a1 = fma(V[s.ph + (i + 1) * M.R], (double)w[s.w0 + i + 1], a1);
     }
-    if (i < s.ihi) a0 = fma(V[s.ph + i * M.R], yres[s.w0 + i], a0);
-    h[k] = a0 + a1;
+    if (i < s.ihi) a0 = fma(V[s.ph + i * M.R], (double)w[s.w0 + i], a0);
+    double rs = -r;
+#pragma unroll 1
+    for (int j = 0; j < N; ++j) rs += A[(size_t)k * ws_ld + j];
+    const double aw = a0 + a1;
+    h[k] = aw - mu * rs;
+    awt += aw;
+    rst += rs;
+  }
+  awt = wsum(awt);
+  rst = wsum(rst);
+  const double yy = wsq - 2.0 * mu * awt + mu * mu * rst;
+  // the FP32 residual, each sample summed in FP64 over the PEs that cover it
+#pragma unroll 1
+  for (int x = lane; x < n; x += 32) {
+    double yv = (double)w[x];
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      const int idx = x * M.R - W.list[k];
+      if (idx >= 0 && idx < M.Lt) yv = fma(-mu, V[idx], yv);
+    }
+    W.y[x] = (T)yv;
   }
   __syncwarp();
   // Gauss-Jordan inversion in place with diagonal pivots (C is SPD: the pivots are the
@@ -478,10 +494,6 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
 #pragma unroll 1
   for (int i = lane; i < N; i += 32) hv += h[i] * rowk[i];
   hv = wsum(hv);
-  double yy = 0.0;
-#pragma unroll 1
-  for (int x = lane; x < n; x += 32) yy += yres[x] * yres[x];
-  yy = wsum(yy);
   // drift of the incremental state, then the refreshed state (packed lower triangle)
   double dmax = 0.0, amax = 0.0;
 #pragma unroll 1
@@ -500,8 +512,6 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     va = fmax(va, fabs(rowk[i]));
     W.v[i] = cfrom64<C>(rowk[i]);
   }
-#pragma unroll 1
-  for (int x = lane; x < n; x += 32) W.y[x] = (T)yres[x];
   dmax = wmax(dmax); amax = wmax(amax); vd = wmax(vd); va = wmax(va);
   __syncwarp();
   out.ok = 1;
@@ -541,7 +551,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   // where s is the slot of the new PE (N for a birth, k for an update; none for a death) and
   // m moves the last PE into slot k for a death (identity otherwise). v changes the same way.
   using C = typename PeTab<T>::C;
-  const C mu = cconst<C>(M.mu_q), rr = cconst<C>(M.se2 / M.sq2);
+  const C mu = c_mu<C>(M), rr = c_r<C>(M);
   const T muT = (T)M.mu_q;
   const int R = M.R, np = mv.np, kk = mv.kk, jump = mv.jump;
   const bool has_m = jump != 0, has_p = jump != 1;
@@ -567,6 +577,11 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     fv = cmul(cadd(mv.vk, mu), ig);
   }
   if (has_p) {
+    // b^T v in full state precision (the scoring used an FP32 sum)
+    C bvf = czero<C>();
+#pragma unroll 1
+    for (int a = lane; a < np; a += 32) bvf = cfma(W.ovb[a], W.v[W.ovi[a]], bvf);
+    bvf = csum(bvf);
     C bk = czero<C>(), wk = czero<C>();
     if (jump == 2) {
       // u' = w - c w_k / gamma on the system without PE k
@@ -588,7 +603,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     idl = crcp(csub(cadd(rr, mv.aa), bu));
     // t = (b~^T v_- - mu b~^T u' - h_new) / delta with v_- = v after removing PE k and h_new the
     // new PE's a^T y on the residual without PE k
-    const C bvm = jump == 2 ? csub(csub(mv.bv, cmul(bk, mv.vk)), cmul(wk, fv)) : mv.bv;
+    const C bvm = jump == 2 ? csub(csub(bvf, cmul(bk, mv.vk)), cmul(wk, fv)) : bvf;
     const C hnew = csub(cadd(mv.ay, cmul(mu, bk)), cmul(mu, mv.aa));
     t = cmul(csub(csub(bvm, cmul(mu, bu)), hnew), idl);
   }
@@ -739,6 +754,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       S.sQ = S.sQ2 = 0.0; S.q_cur = 0.0; S.q_from = 0;
       S.logdet = n * M.log_se2;
       S.logL = -0.5 * (n * kLog2Pi + S.logdet + wsq * M.inv_se2);
+      S.wsq = wsq;
       S.drift_max = 0.0; S.alg_words = 0;
       for (int k = 0; k < 3; ++k) { S.acc[k] = 0; S.prop[k] = 0; }
       S.acc_t0 = S.prop_t0 = S.n_refresh = S.status = S.n_acc_refresh = S.refresh_fail = 0;
@@ -884,7 +900,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           T ayp = (T)0;
 #pragma unroll 1
           for (int i = sp.ilo + lane; i < sp.ihi; i += 32) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
-          C qp = czero<C>(), bvp = czero<C>(), ck = czero<C>();
+          C qp = czero<C>(), ck = czero<C>();
+          T bvp = (T)0;
           int kpos = -1;
 #pragma unroll 1
           for (int a0 = 0; a0 < np; a0 += 32) {
@@ -893,17 +910,12 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
               const C rq = dot_row<C, BIG>(Cp, W.ovi[a], W.ovi, W.ovb, np, -1);
               const C ba = W.ovb[a];
               qp = cfma(ba, rq, qp);
-              bvp = cfma(ba, W.v[W.ovi[a]], bvp);
+              bvp += (T)cnum(ba) * (T)cnum(W.v[W.ovi[a]]);
               if (jump == 2 && W.ovi[a] == kk) { ck = rq; kpos = a; }
             }
           }
-          if (np <= 32) {
-            mv.quad = csum_first(qp, np);
-            mv.bv = csum_first(bvp, np);
-          } else {
-            mv.quad = csum(qp);
-            mv.bv = csum(bvp);
-          }
+          mv.quad = np <= 32 ? csum_first(qp, np) : csum(qp);
+          const T bvT = wsum(bvp);  // b^T v at the scoring precision (the accept recomputes it)
           const T ayT = wsum(ayp);
           mv.ay = cfromf(ayT);
           if (jump == 2) {
@@ -919,7 +931,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
             }
           }
           mpp = (T)cnum(csub(mv.aa, mv.quad)) * ise2T;
-          gp = (T)cnum(csub(mv.ay, mv.bv)) * ise2T;
+          gp = (ayT - bvT) * ise2T;
           mmp = (T)cnum(ck) * iqT;
           words += (unsigned long long)(N + 2 * np + 2 * (sp.ihi - sp.ilo) + np * np + np);
         }
@@ -980,7 +992,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
         __syncwarp();
         if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+          const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, lane);
           C qr = czero<C>();
           for (int i = lane; i < N; i += 32) qr = cadd(qr, W.v[i]);
           qr = csum(qr);
@@ -1026,7 +1038,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     // ------------------------------------------------------------- chain end
     if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
       // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, n, N, lane);
+      const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, lane);
       if (lane == 0) {
         if (ro.ok) {
           S.logdet = ro.logdet; S.logL = ro.logL;
