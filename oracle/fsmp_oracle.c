@@ -497,6 +497,7 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     logp_cur = logp_def(M, c->w, n, list, 0, NULL, NULL, NULL);
 
   double sN = 0, sN2 = 0, st0 = 0, st02 = 0, sQ = 0, sQ2 = 0;
+  double* hist = (double*)calloc((size_t)p->n_cap + 1, sizeof(double));
   int q_valid = 0;
   double q_cur = 0.0;
   const double logJ = log(p->jump_J);
@@ -685,6 +686,7 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       }
       double t0ns = c->t_origin + k0 * g;
       sN += N; sN2 += (double)N * N;
+      if (N >= 0 && N <= p->n_cap) hist[N] += 1.0;
       st0 += t0ns; st02 += t0ns * t0ns;
       sQ += q_cur; sQ2 += q_cur * q_cur;
       if (c->occ)
@@ -705,6 +707,7 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     out->mean_Q = sQ * inv; out->var_Q = sQ2 * inv - out->mean_Q * out->mean_Q;
     out->N_final = N;
     out->k0_final = k0;
+    out->lambda_hat = ns > 0 ? orc_lambda_mle(hist, p->n_cap, c->lambda0) : NAN;
     if (c->occ && ns > 0)
       for (int col = 0; col < c->occ_width; ++col) c->occ[col] *= inv;
     if (p->prior_only) {
@@ -731,6 +734,7 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       if (y_out) memcpy(y_out, st.y, sizeof(double) * n);
       if (logdet_out) *logdet_out = st.logdet;
     }
+    free(hist);
   }
 done:
   free(tb.phi); free(tb.logphi); free(tb.Phi_T); free(list); free(av); free(uvec); free(svec); free(zprop);
@@ -821,6 +825,71 @@ static int build_model(const orc_params* p, model* M, double** Vbuf) {
   orc_ser_table(p, *Vbuf, Lt, NULL);
   M->p = p; M->R = grid_ratio(p); M->Lt = Lt; M->g = p->grid_ns; M->V = *Vbuf;
   return 0;
+}
+
+/* l(lambda) = -lambda + log sum_N h[N] (lambda / lambda0)^N, the log of Eq. (reduce-mu0) up to
+ * a constant, evaluated as a log-sum-exp over the N with h[N] > 0. */
+static double lambda_loglik(const double* h, int n_max, double lambda0, double lam) {
+  double mx = -INFINITY;
+  for (int k = 0; k <= n_max; ++k) {
+    if (!(h[k] > 0.0)) continue;
+    double t = (k == 0) ? log(h[k]) : (lam > 0.0 ? log(h[k]) + k * log(lam / lambda0) : -INFINITY);
+    if (t > mx) mx = t;
+  }
+  if (mx == -INFINITY) return -INFINITY;
+  double acc = 0.0;
+  for (int k = 0; k <= n_max; ++k) {
+    if (!(h[k] > 0.0)) continue;
+    double t = (k == 0) ? log(h[k]) : (lam > 0.0 ? log(h[k]) + k * log(lam / lambda0) : -INFINITY);
+    acc += exp(t - mx);
+  }
+  return -lam + mx + log(acc);
+}
+
+/* l'(lambda) = -1 + (sum_N N w_N) / (lambda sum_N w_N), w_N = h[N] (lambda / lambda0)^N */
+static double lambda_dloglik(const double* h, int n_max, double lambda0, double lam) {
+  double mx = -INFINITY;
+  for (int k = 0; k <= n_max; ++k)
+    if (h[k] > 0.0) {
+      double t = log(h[k]) + k * log(lam / lambda0);
+      if (t > mx) mx = t;
+    }
+  double sw = 0.0, snw = 0.0;
+  for (int k = 0; k <= n_max; ++k)
+    if (h[k] > 0.0) {
+      double e = exp(log(h[k]) + k * log(lam / lambda0) - mx);
+      sw += e;
+      snw += k * e;
+    }
+  return -1.0 + snw / (lam * sw);
+}
+
+double orc_lambda_mle(const double* h, int n_max, double lambda0) {
+  int top = -1;
+  for (int k = 0; k <= n_max; ++k)
+    if (h[k] > 0.0) top = k;
+  if (top < 0) return NAN;
+  if (top == 0) return 0.0;
+  const double hi = 2.0 * top + 10.0;
+  const int G = 20000;
+  int best = 0;
+  double bl = -INFINITY;
+  for (int g = 0; g <= G; ++g) {
+    double l = lambda_loglik(h, n_max, lambda0, hi * g / G);
+    if (l > bl) { bl = l; best = g; }
+  }
+  /* bisection on l'(lambda) = -1 + E_w[N] / lambda, w_N = h[N] (lambda / lambda0)^N, inside the
+   * bracket around the best grid point (l' changes sign at the maximum) */
+  double a = hi * (best > 0 ? best - 1 : 0) / G, b = hi * (best < G ? best + 1 : G) / G;
+  if (a <= 0.0) a = 1e-300;
+  for (int it = 0; it < 400 && b - a > 4e-16 * b; ++it) {
+    const double m = 0.5 * (a + b);
+    if (lambda_dloglik(h, n_max, lambda0, m) > 0.0) a = m; else b = m;
+  }
+  double x = 0.5 * (a + b);
+  /* the maximum may sit on the boundary lambda = 0 */
+  if (lambda_loglik(h, n_max, lambda0, 0.0) >= lambda_loglik(h, n_max, lambda0, x)) return 0.0;
+  return x;
 }
 
 int orc_run_batch(const orc_params* p, const orc_batch* b, int mode, int n_threads,

@@ -69,7 +69,13 @@ typedef struct {
   double mean_N, var_N, mean_t0, var_t0, mean_Q, var_Q, logL, logdet;
   int32_t acc[3], prop[3];
   int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples;
+  double lambda_hat;  /* lambda_FSMP of the chain's N samples (Eq. (reduce-mu0)); 0 if none */
 } orc_summary;
+
+/* lambda_FSMP = argmax_lambda l(lambda), l = -lambda + log sum_N h[N] (lambda / lambda0)^N
+ * (Eq. (reduce-mu0) with the samples counted by N in h[0 .. n_max]), by a dense grid over
+ * [0, 2 max{N : h[N] > 0} + 10] and golden-section refinement around the best grid point. */
+double orc_lambda_mle(const double* h, int n_max, double lambda0);
 
 /* Batch description: waveform i is samples[offsets[i] .. offsets[i+1]). Optional arrays may
  * be NULL: T_lo/T_hi (default: whole window [0, n*R)), t0_init (default: prior midpoint). */

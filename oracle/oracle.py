@@ -37,7 +37,7 @@ SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"
                           ("logL", "<f8"), ("logdet", "<f8"), ("acc", "<i4", (3,)),
                           ("prop", "<i4", (3,)), ("acc_t0", "<i4"), ("prop_t0", "<i4"),
                           ("N_final", "<i4"), ("k0_final", "<i4"), ("status", "<i4"),
-                          ("n_samples", "<i4")])
+                          ("n_samples", "<i4"), ("lambda_hat", "<f8")])
 
 
 class OrcParams(ctypes.Structure):
@@ -106,6 +106,8 @@ def lib():
         L.orc_run_batch.restype = ctypes.c_int
         L.orc_run_batch.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcBatch),
                                     ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_lambda_mle.restype = ctypes.c_double
+        L.orc_lambda_mle.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_run_chain_state.restype = ctypes.c_int
         L.orc_run_chain_state.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcBatch),
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -192,6 +194,12 @@ def logp_definition(params, w, j):
     r = lib().orc_logp_definition(ctypes.byref(p), w.ctypes.data, len(w), j.ctypes.data, len(j),
                                   ctypes.byref(ld), ctypes.byref(q))
     return r, ld.value, q.value
+
+
+def lambda_mle(hist, lambda0):
+    """lambda_FSMP of an N histogram (counts h[0..n_max]) by Eq. (reduce-mu0)."""
+    h = np.ascontiguousarray(hist, np.float64)
+    return lib().orc_lambda_mle(h.ctypes.data, len(h) - 1, float(lambda0))
 
 
 def delta_nu(params, w, j, kind, k=0, jp=0, mode=MODE_INCREMENTAL):

@@ -335,3 +335,40 @@ def test_charge_summary_information_form(orc):
         prec = np.eye(len(z)) / sq2 + A.T @ A / se2
         qpost = np.linalg.solve(prec, mu / sq2 * np.ones(len(z)) + A.T @ b["samples"].astype(np.float64) / se2)
         assert st["summary"]["mean_Q"] == pytest.approx(qpost.sum(), rel=1e-10, abs=1e-10)
+
+
+# ---------------------------------------------------------------- lambda_FSMP (Eq. (reduce-mu0))
+def test_lambda_mle_single_count_is_that_count(orc):
+    """All samples at N0: l = -lambda + N0 log lambda + const, maximised at lambda = N0."""
+    for n0, lam0 in ((1, 2.0), (7, 3.5), (40, 55.0)):
+        h = np.zeros(64)
+        h[n0] = 100.0
+        assert abs(orc.lambda_mle(h, lam0) - n0) < 1e-9 * max(1, n0)
+
+
+def test_lambda_mle_two_point_closed_form(orc):
+    """h = {0: a, 1: b}: l' = -1 + (b / lam0) / (a + b lam / lam0) = 0 gives
+    lambda = 1 - a lam0 / b, or 0 when that is negative."""
+    for a, b, lam0 in ((1.0, 3.0, 1.5), (2.0, 5.0, 0.5), (5.0, 1.0, 2.0)):
+        h = np.zeros(8)
+        h[0], h[1] = a, b
+        want = max(0.0, 1.0 - a * lam0 / b)
+        assert abs(orc.lambda_mle(h, lam0) - want) < 1e-9
+
+
+def test_lambda_mle_empty_chain_is_zero(orc):
+    h = np.zeros(8)
+    h[0] = 10.0
+    assert orc.lambda_mle(h, 3.0) == 0.0
+
+
+def test_chain_summary_lambda_matches_its_own_histogram(orc):
+    """The summary's lambda_hat is the MLE of the chain's N samples: recompute it from the
+    traced N of the same run (after burn-in)."""
+    from paper_2403_03156_gb300 import workloads
+    wl = workloads.make_workload("plain_fp64_256x128", n_waveforms=3, n_steps=400, burn_in=100, seed=4)
+    s, t = orc.run_batch(wl["params"], wl["batch"], orc.MODE_INCREMENTAL, n_threads=1, trace=True)
+    for i in range(3):
+        N = t["N"][i, 100:]
+        h = np.bincount(N, minlength=wl["params"]["n_cap"] + 1).astype(float)
+        assert abs(s["lambda_hat"][i] - orc.lambda_mle(h, wl["batch"]["lambda0"][i])) < 1e-12
