@@ -126,6 +126,9 @@ typedef struct {
 typedef struct {
   double mean_N, var_N, mean_t0, var_t0, mean_Q, var_Q, logL, logdet;
   double drift_max, alg_bytes;
+  double lambda_hat;             /* lambda_FSMP = argmax_lambda -lambda + log sum_N h_N
+                                    (lambda / lambda0)^N over the chain's N samples h
+                                    (Eq. (reduce-mu0)); 0 if every sample has N = 0 */
   int32_t acc[3], prop[3];
   int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples, n_refresh, reserved;
 } fsmp_summary;
@@ -223,6 +226,20 @@ int fsmp_destroy(fsmp_ctx* ctx);
  * streams must not overlap. Returns FSMP_ERR_INVALID for bad arguments, FSMP_ERR_CUDA if a
  * launch fails. */
 int fsmp_run_device(fsmp_ctx* ctx, const fsmp_device_batch* batch, void* stream);
+
+/* Gelman-Rubin potential scale reduction R of one scalar over m >= 2 chains of the same
+ * waveform (the convergence check of Sec. 3), from their summaries. With n samples per chain
+ * (n_samples, equal for all, n >= 2), chain means x_j and variances v_j of the field
+ * (FSMP_RHAT_N: N; FSMP_RHAT_T0: t0; FSMP_RHAT_Q: the charge summary):
+ *   W = (1/m) sum_j v_j n / (n - 1),   B / n = (1/(m-1)) sum_j (x_j - mean x)^2,
+ *   V = (n - 1) / n W + B / n,          R = sqrt(V / W)
+ * (the point estimate of Gelman and Rubin, 1992, without a degrees-of-freedom correction).
+ * *rhat = 1 when W = 0 and all means agree, +inf when W = 0 and they do not. Host only.
+ * Returns FSMP_OK or FSMP_ERR_INVALID. The paper has no code for it; it quotes R < 1.1. */
+#define FSMP_RHAT_N 0
+#define FSMP_RHAT_T0 1
+#define FSMP_RHAT_Q 2
+int fsmp_gelman_rubin(const fsmp_summary* chains, int m, int field, double* rhat);
 
 /* Launch shape of the PE-space kernel chosen by fsmp_autotune. */
 typedef struct {

@@ -157,6 +157,7 @@ struct ChainScalars {
   int q_from, q_pending, pending_step;
   unsigned long long alg_words;
   double drift_max;
+  double lambda_hat;
   int acc[3], prop[3], acc_t0, prop_t0, n_refresh, refresh_fail;
 };
 
@@ -165,6 +166,7 @@ template <typename T> struct Layout {
   T* red;                   // [kMaxWarps][8] per-warp partial sums (T view of redd)
   double* redd;             // the same region as [kMaxWarps][8] doubles (block-reduction scratch)
   int* list;                // [n_cap]
+  int* hist;                // counts of N after burn-in [n_cap + 1]
   StepRand<T>* rnd;         // [kRB]
   unsigned long long* raw;  // [2 kRB][4] Philox output of a batch
   T* a2;                    // [LU][2]: (a_-, a_+) interleaved
@@ -191,6 +193,7 @@ __host__ __device__ inline size_t layout_bytes(int n_alloc, int n_cap, int LU, b
   size_t b = align16(sizeof(ChainScalars<T>));
   b += align16(sizeof(double) * kMaxWarps * 8);
   b += align16(sizeof(int) * n_cap);
+  b += align16(sizeof(int) * (n_cap + 1));
   b += align16(sizeof(StepRand<T>) * kRB);
   b += align16(sizeof(unsigned long long) * 2 * kRB * 4);
   b += align16(sizeof(T) * 2 * LU);
@@ -211,6 +214,7 @@ __device__ inline Layout<T> carve(unsigned char* base, int n_alloc, int n_cap, i
   L.redd = reinterpret_cast<double*>(base + o);
   o += align16(sizeof(double) * kMaxWarps * 8);
   L.list = reinterpret_cast<int*>(base + o); o += align16(sizeof(int) * n_cap);
+  L.hist = reinterpret_cast<int*>(base + o); o += align16(sizeof(int) * (n_cap + 1));
   L.rnd = reinterpret_cast<StepRand<T>*>(base + o); o += align16(sizeof(StepRand<T>) * kRB);
   L.raw = reinterpret_cast<unsigned long long*>(base + o); o += align16(sizeof(unsigned long long) * 2 * kRB * 4);
   L.a2 = reinterpret_cast<T*>(base + o); o += align16(sizeof(T) * 2 * LU);
@@ -542,7 +546,7 @@ __device__ __forceinline__ void close_charge_hold(ChainScalars<T>& S, int upto) 
 // algorithmic-byte count, summary sums after burn-in, the trace record. It runs on a warp that
 // is idle while warp 0 works on the next proposal.
 template <typename T>
-__device__ void bookkeep(ChainScalars<T>& S) {
+__device__ void bookkeep(ChainScalars<T>& S, int* hist) {
   const int jump = S.bk_jump, fl = S.bk_flags;
   S.prop[jump]++;
   if (fl & 1) { S.prop_t0++; if (fl & 2) S.acc_t0++; }
@@ -556,6 +560,7 @@ __device__ void bookkeep(ChainScalars<T>& S) {
   if (S.bk_step >= S.burn_in) {
     const long long Nn = S.bk_N, kk = S.bk_k0;
     S.sN += Nn; S.sN2 += Nn * Nn; S.sK += kk; S.sK2 += kk * kk;
+    hist[S.bk_N] += 1;
   }
   if (S.trace) {
     fsmp_trace tr;
@@ -627,12 +632,13 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       S.acc_t0 = 0; S.prop_t0 = 0; S.n_refresh = 0;
       S.alg_words = 0; S.drift_max = 0.0;
     }
+    for (int k = tid; k <= M.n_cap; k += blockDim.x) L.hist[k] = 0;
     __syncthreads();
     if (S.invalid) {
       if (tid == 0) {
         fsmp_summary o;
         o.mean_N = o.var_N = o.mean_t0 = o.var_t0 = o.mean_Q = o.var_Q = o.logL = o.logdet = NAN;
-        o.drift_max = 0.0; o.alg_bytes = 0.0;
+        o.drift_max = 0.0; o.alg_bytes = 0.0; o.lambda_hat = NAN;
         for (int k = 0; k < 3; ++k) { o.acc[k] = 0; o.prop[k] = 0; }
         o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
         o.status = FSMP_ST_INVALID;
@@ -714,7 +720,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
             S.q_pending = 0;
           }
         }
-        if (lane == 0 && S.bk_pending) bookkeep(S);
+        if (lane == 0 && S.bk_pending) bookkeep(S, L.hist);
         __syncwarp();
       }
       if (warp == 0) {
@@ -1089,7 +1095,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
           S.q_pending = 0;
         }
       }
-      if (lane == 0 && S.bk_pending) bookkeep(S);
+      if (lane == 0 && S.bk_pending) bookkeep(S, L.hist);
     }
     __syncthreads();
     if constexpr (fp32) {
@@ -1097,6 +1103,11 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       // rebuild, not from the FP32 increments accumulated since the last refresh
       if (M.refresh_every > 0 && S.n_acc_refresh > 0) refresh_state<T>(M, L, P, ws, n, n_alloc);
     }
+    if (warp == 0) {  // lambda_FSMP of the chain's N samples (Eq. (reduce-mu0))
+      const double lh = warp_lambda_mle(L.hist, M.n_cap, S.lambda0, lane);
+      if (lane == 0) S.lambda_hat = lh;
+    }
+    __syncthreads();
     if (tid == 0) {
       close_charge_hold(S, n_steps);
       fsmp_summary o;
@@ -1109,6 +1120,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       o.mean_Q = S.sQ * inv; o.var_Q = S.sQ2 * inv - o.mean_Q * o.mean_Q;
       o.logL = S.logL; o.logdet = S.logdet;
       o.drift_max = S.drift_max; o.alg_bytes = (double)S.alg_words * (double)sizeof(T);
+      o.lambda_hat = S.lambda_hat;
       for (int k = 0; k < 3; ++k) { o.acc[k] = S.acc[k]; o.prop[k] = S.prop[k]; }
       o.acc_t0 = S.acc_t0; o.prop_t0 = S.prop_t0; o.N_final = S.N; o.k0_final = k0;
       o.status = S.status; o.n_samples = ns; o.n_refresh = S.n_refresh; o.reserved = 0;

@@ -101,6 +101,58 @@ FSMP_HD void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
 
 FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
 
+#ifdef __CUDACC__
+// lambda_FSMP of a chain (Eq. (reduce-mu0)): the maximiser of
+//   l(lambda) = -lambda + log sum_N h[N] (lambda / lambda0)^N
+// over its N-sample counts h[0 .. n_max], by Newton steps on
+//   l'(lambda) = -1 + E_w[N] / lambda,  l''(lambda) = (Var_w[N] - E_w[N]) / lambda^2,
+// w_N ∝ h[N] (lambda / lambda0)^N, from the sample mean (fixed-point steps lambda <- E_w[N]
+// where l'' >= 0); the boundary lambda = 0 when l(0) is not smaller. One warp, all lanes
+// call it and get the result; NAN if h is empty.
+__device__ inline double warp_lambda_mle(const int* h, int n_max, double lambda0, int lane) {
+  double c = 0.0, cn = 0.0;
+  int top = -1;
+  for (int k = lane; k <= n_max; k += 32)
+    if (h[k] > 0) { c += h[k]; cn += (double)k * h[k]; top = k; }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    cn += __shfl_xor_sync(0xffffffffu, cn, o);
+    top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+  }
+  if (top < 0) return NAN;
+  if (top == 0) return 0.0;
+  double lam = cn / c, ll = -INFINITY;
+  for (int it = 0; it < 200; ++it) {
+    const double s = log(lam / lambda0);
+    double mx = -INFINITY;
+    for (int k = lane; k <= n_max; k += 32)
+      if (h[k] > 0) mx = fmax(mx, log((double)h[k]) + k * s);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    double sw = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = lane; k <= n_max; k += 32)
+      if (h[k] > 0) {
+        const double e = exp(log((double)h[k]) + k * s - mx);
+        sw += e; s1 += k * e; s2 += (double)k * k * e;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const double E = s1 / sw, Vr = s2 / sw - E * E;
+    ll = -lam + mx + log(sw);
+    const double g = -1.0 + E / lam, H = (Vr - E) / (lam * lam);
+    double nl = H < 0.0 ? lam - g / H : E;
+    if (!(nl > 0.0)) nl = 0.5 * lam;
+    const bool done = fabs(nl - lam) <= 1e-14 * lam;
+    lam = nl;
+    if (done) break;
+  }
+  const double l0 = h[0] > 0 ? log((double)h[0]) : -INFINITY;  // l(0): only N = 0 contributes
+  return l0 >= ll ? 0.0 : lam;
+}
+#endif
+
 // Launchers (fsmp_tables.cu / fsmp_chain.cu). All return cudaError_t of the launch.
 cudaError_t launch_tables(const fsmp_params& p, int R, int D, int m_end, double* V64, float* V32,
                           double* phi, double* logphi, double* cphi, float* phi32, float* logphi32,

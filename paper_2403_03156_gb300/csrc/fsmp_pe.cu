@@ -287,6 +287,7 @@ template <typename T> struct PeWarp {
   PeStats* st;
   PeRand<T>* rnd;
   int* list;   // PE grid indices [n_cap]
+  int* hist;   // counts of N over the samples after burn-in [n_cap + 1]
   int* ovi;    // PEs overlapping the proposed one [n_cap]
   C* ovb;      // their inner products with it [n_cap]
   C* v;        // C^-1 A^T y [n_cap]
@@ -298,6 +299,7 @@ template <typename T> struct PeWarp {
 };
 template <typename T> __host__ __device__ inline size_t pe_warp_bytes(int n_cap, int n_alloc, int win_extra, int Ns) {
   return a16(sizeof(PeStats)) + a16(sizeof(PeRand<T>) * kPeRB) + 2 * a16(sizeof(int) * n_cap) +
+         a16(sizeof(int) * (n_cap + 1)) +
          4 * a16(8 * (size_t)n_cap) + a16(sizeof(T) * n_alloc) + a16(sizeof(T) * win_extra) +
          a16(8 * (size_t)tri(Ns));
 }
@@ -311,6 +313,7 @@ template <typename T> __device__ PeWarp<T> pe_carve(unsigned char* p, int n_cap,
   W.st = reinterpret_cast<PeStats*>(p + o); o += a16(sizeof(PeStats));
   W.rnd = reinterpret_cast<PeRand<T>*>(p + o); o += a16(sizeof(PeRand<T>) * kPeRB);
   W.list = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
+  W.hist = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * (n_cap + 1));
   W.ovi = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
   W.ovb = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
   W.v = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       if (lane == 0) {
         fsmp_summary o;
         o.mean_N = o.var_N = o.mean_t0 = o.var_t0 = o.mean_Q = o.var_Q = o.logL = o.logdet = NAN;
-        o.drift_max = 0.0; o.alg_bytes = 0.0;
+        o.drift_max = 0.0; o.alg_bytes = 0.0; o.lambda_hat = NAN;
         for (int k = 0; k < 3; ++k) { o.acc[k] = 0; o.prop[k] = 0; }
         o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
         o.status = FSMP_ST_INVALID;
@@ -741,6 +744,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       const double tot = pe_cphi<double>(M, T_hi - 1 - kq) - pe_cphi<double>(M, T_lo - 1 - kq);
       W.lPhi[k] = tot > 0.0 ? (fp32 ? (T)logf((float)(tot * M.g)) : (T)log(tot * M.g)) : (T)-INFINITY;
     }
+#pragma unroll 1
+    for (int k = lane; k <= n_cap; k += 32) W.hist[k] = 0;
     // empty z: y = w
     double wsq = 0.0;
     for (int x = lane; x < n; x += 32) {
@@ -1023,6 +1028,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         if (step >= burn_in) {
           const long long Nn = N, kq = k0;
           S.sN += Nn; S.sN2 += Nn * Nn; S.sK += kq; S.sK2 += kq * kq;
+          W.hist[N] += 1;
         }
         if (trace) {
           fsmp_trace tr;
@@ -1050,9 +1056,11 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
       }
     }
+    const double lam_hat = warp_lambda_mle(W.hist, n_cap, lambda0, lane);
     if (lane == 0) {
       close_hold(S, n_steps, burn_in);
       fsmp_summary o;
+      o.lambda_hat = lam_hat;
       int ns = n_steps - burn_in;
       if (ns < 0) ns = 0;
       const double inv = ns > 0 ? 1.0 / ns : NAN;

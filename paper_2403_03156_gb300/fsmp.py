@@ -22,7 +22,7 @@ KERNEL_AUTO, KERNEL_SMEM, KERNEL_GLOBAL, KERNEL_PLAIN, KERNEL_PE = 0, 1, 2, 3, 4
 SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"),
                           ("var_t0", "<f8"), ("mean_Q", "<f8"), ("var_Q", "<f8"),
                           ("logL", "<f8"), ("logdet", "<f8"), ("drift_max", "<f8"),
-                          ("alg_bytes", "<f8"), ("acc", "<i4", (3,)), ("prop", "<i4", (3,)),
+                          ("alg_bytes", "<f8"), ("lambda_hat", "<f8"), ("acc", "<i4", (3,)), ("prop", "<i4", (3,)),
                           ("acc_t0", "<i4"), ("prop_t0", "<i4"), ("N_final", "<i4"),
                           ("k0_final", "<i4"), ("status", "<i4"), ("n_samples", "<i4"),
                           ("n_refresh", "<i4"), ("reserved", "<i4")])
@@ -84,7 +84,8 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
-           "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc", "fsmp_autotune"]
+           "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc", "fsmp_autotune",
+           "fsmp_gelman_rubin"]
 
 _lib = None
 
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False):
     L.fsmp_run_device.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _vp]
     L.fsmp_run_device_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(DeviceBatch), _vp]
     L.fsmp_autotune.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _c_int, _c_int, ctypes.POINTER(Tune)]
+    L.fsmp_gelman_rubin.argtypes = [_vp, _c_int, _c_int, ctypes.POINTER(_c_double)]
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
     L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
     L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
@@ -356,6 +358,17 @@ def run_device_noalloc(params: dict, dev: dict, n_steps: int, burn_in: int = 0, 
     b = _device_batch(dev, n_steps, burn_in, seed, index_base, n_max_hint)
     st = None if stream is None else int(stream.cuda_stream)
     _check(load().fsmp_run_device_noalloc(ctypes.byref(prm), ctypes.byref(b), st), "fsmp_run_device_noalloc")
+
+
+RHAT_N, RHAT_T0, RHAT_Q = 0, 1, 2
+
+
+def gelman_rubin(summaries: np.ndarray, field: int = RHAT_N) -> float:
+    """fsmp_gelman_rubin over the chains of one waveform (a SUMMARY_DTYPE array)."""
+    s = np.ascontiguousarray(summaries, SUMMARY_DTYPE)
+    r = _c_double()
+    _check(load().fsmp_gelman_rubin(s.ctypes.data, len(s), int(field), ctypes.byref(r)), "fsmp_gelman_rubin")
+    return r.value
 
 
 def summaries_from_bytes(buf) -> np.ndarray:

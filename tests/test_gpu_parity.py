@@ -65,7 +65,30 @@ def test_lockstep_fp64_config1(lib, orc, kernel):
     gpu_util.compare_traces(t_gpu, t_orc)
     for f in ("mean_N", "var_N", "mean_t0", "var_t0"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12)
-    for f in ("mean_Q", "var_Q", "logL", "logdet"):
+    for f in ("mean_Q", "var_Q", "logL", "logdet", "lambda_hat"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f])
+
+
+def test_gelman_rubin_of_gpu_chains_matches_oracle(lib, orc):
+    """Four chains of each of 8 waveforms (distinct RNG streams, t0 started across the prior
+    range): R for N and t0 from the GPU summaries equals R from the oracle's (FP64, lockstep)."""
+    wl = workloads.make_workload("plain_fp64_256x128", n_waveforms=8, n_steps=1500, burn_in=300, seed=17)
+    b = wl["batch"]
+    m = 4
+    idx = np.repeat(np.arange(8), m)
+    rb = workloads.subset(b, idx)
+    rb["wf_ids"] = np.arange(len(idx), dtype=np.uint64) + np.uint64(10_000)
+    rb["t0_init"] = np.tile(np.linspace(C1["t0_lo"], C1["t0_hi"], m), 8)
+    with fsmp.Context(C1, n_max=128, precision=fsmp.FP64) as ctx:
+        s_gpu, _ = ctx.run(rb)
+    s_orc, _ = orc.run_batch(C1, rb, orc.MODE_INCREMENTAL, n_threads=16)
+    for w in range(8):
+        g = s_gpu[w * m:(w + 1) * m]
+        o = np.zeros(m, fsmp.SUMMARY_DTYPE)
+        for f in ("mean_N", "var_N", "mean_t0", "var_t0", "mean_Q", "var_Q", "n_samples"):
+            o[f] = s_orc[f][w * m:(w + 1) * m]
+        for field in (fsmp.RHAT_N, fsmp.RHAT_T0):
+            rg, ro = fsmp.gelman_rubin(g, field), fsmp.gelman_rubin(o, field)
+            assert np.isfinite(rg) and abs(rg - ro) <= 1e-9 * max(1.0, ro), (w, field, rg, ro)

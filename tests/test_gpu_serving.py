@@ -10,7 +10,7 @@ from paper_2403_03156_gb300 import fsmp, workloads
 pytestmark = pytest.mark.gpu
 
 FLOAT_FIELDS = ("mean_N", "var_N", "mean_t0", "var_t0", "mean_Q", "var_Q", "logL", "logdet", "drift_max",
-                "alg_bytes")
+                "alg_bytes", "lambda_hat")
 INT_FIELDS = ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status", "n_samples", "n_refresh")
 
 

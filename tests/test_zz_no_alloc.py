@@ -54,7 +54,8 @@ def test_noalloc_matches_run_device_twice():
                                 seed=b["seed"], n_max_hint=n_max)
         torch.cuda.synchronize(dev)
         got = fsmp.summaries_from_bytes(out.cpu().numpy())
-        for f in ("mean_N", "var_N", "mean_t0", "var_t0", "mean_Q", "var_Q", "logL", "logdet", "alg_bytes"):
+        for f in ("mean_N", "var_N", "mean_t0", "var_t0", "mean_Q", "var_Q", "logL", "logdet", "alg_bytes",
+                  "lambda_hat"):
             np.testing.assert_allclose(got[f], ref[f], rtol=1e-12, atol=0, err_msg="call %d field %s" % (call, f))
         for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status", "n_refresh"):
             np.testing.assert_array_equal(got[f], ref[f], err_msg="call %d field %s" % (call, f))
