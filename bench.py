@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=0, help="threads per chain CTA (0: library default)")
     ap.add_argument("--pe-tile", type=int, default=0, help="PE kernel: shared-memory C^-1 tile (0: default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="PE kernel: resident CTAs per SM (0: max)")
+    ap.add_argument("--pe-lanes", type=int, default=0, choices=[0, 16, 32],
+                    help="PE kernel: lanes per chain (0: chosen by the autotuner)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "smem", "global", "plain", "pe"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="PE kernel: keep the default launch shape")
@@ -310,7 +312,7 @@ def run_ours(args):
     lengths = np.diff(b["offsets"])
     params = dict(wl["params"], precision=prec, refresh_every=wl["meta"].get("refresh_every") or 64,
                   n_max=int(max(lengths.max(), 64)), device=local, threads_per_chain=args.threads,
-                  pe_tile=args.pe_tile, pe_ctas_per_sm=args.ctas_per_sm,
+                  pe_tile=args.pe_tile, pe_ctas_per_sm=args.ctas_per_sm, pe_lanes=args.pe_lanes,
                   kernel={"auto": fsmp.KERNEL_AUTO, "smem": fsmp.KERNEL_SMEM, "global": fsmp.KERNEL_GLOBAL,
                           "plain": fsmp.KERNEL_PLAIN, "pe": fsmp.KERNEL_PE}[args.kernel])
     ctx = fsmp.Context(params)

@@ -64,7 +64,7 @@ extern "C" {
                                    for windows too long for shared memory                   */
 #define FSMP_KERNEL_PLAIN 3     /* baseline: one launch per chain, full n x n FP64 Sigma^-1 in
                                    global memory                                            */
-#define FSMP_KERNEL_PE 4        /* persistent kernel, one warp per chain, state in PE space:
+#define FSMP_KERNEL_PE 4        /* persistent kernel, a warp (or half warp) per chain, state in PE space:
                                    the N x N inverse of C = (sigma_eps^2/sigma_q^2) I + A^T A
                                    (Woodbury on all of A), O(N^2) per accepted move          */
 
@@ -110,6 +110,10 @@ typedef struct {
                               (0: autotuned); a chain moves C^-1 to global memory beyond it */
   int pe_ctas_per_sm;      /* FSMP_KERNEL_PE: resident CTAs per SM (0: as many as fit); fewer
                               keep the chains' global C^-1 slots in L2 when chains are large  */
+  int pe_lanes;            /* FSMP_KERNEL_PE: lanes per chain, 32 (a warp) or 16 (two chains per
+                              warp; n_cap <= 192 only); 0: 32 until fsmp_autotune picks one.
+                              The lane count sets the order of the chain's sums, so results
+                              for another count agree up to rounding, not bit for bit       */
 } fsmp_params;
 
 /* One waveform's posterior summaries (after burn_in steps). t0 is in absolute ns.
@@ -244,19 +248,22 @@ int fsmp_gelman_rubin(const fsmp_summary* chains, int m, int field, double* rhat
 /* Launch shape of the PE-space kernel chosen by fsmp_autotune. */
 typedef struct {
   int pe_tile;                   /* PEs per chain whose C^-1 stays in shared memory          */
-  int chains_per_cta;            /* warps (one chain each) per CTA                           */
+  int chains_per_cta;            /* chains per CTA (warps x 32 / lanes_per_chain)            */
   int ctas_per_sm;               /* resident CTAs per SM (0: as many as fit)                 */
   int n_tried;                   /* candidate shapes timed                                   */
   double best_steps_per_s;       /* MCMC steps/s of the chosen shape on the trial            */
   double default_steps_per_s;    /* the same for the shape the context started with          */
+  int lanes_per_chain;           /* 32 or 16                                                  */
 } fsmp_tune;
 
 /* Autotune the launch shape of the PE-space kernel (FSMP_KERNEL_PE contexts) on a device
  * batch laid out as for fsmp_run_device: time trial runs of its first `sample` waveforms for
- * `trial_steps` MCMC steps in each candidate shape -- shared-memory tile of C^-1, chains per
- * CTA and resident CTAs per SM -- and keep the fastest for the context's later launches. The
- * batch's own output and trace buffers are not touched (the trials write to scratch), and
- * later results do not depend on the shape: a chain's arithmetic is the same in every one.
+ * `trial_steps` MCMC steps in each candidate shape -- lanes per chain (only if the context
+ * was created with pe_lanes = 0), shared-memory tile of C^-1, warps per CTA and resident CTAs
+ * per SM -- and keep the fastest for the context's later launches. The batch's own output and
+ * trace buffers are not touched (the trials write to scratch). Later results do not depend on
+ * the tile, warps or CTAs: a chain's arithmetic is the same in each. They do depend, up to
+ * rounding, on the lane count; fix pe_lanes for results reproducible bit for bit.
  * Blocks until the trials finish. Call it with no request in flight on the context. Returns
  * FSMP_OK (out, if not NULL, describes the choice), FSMP_ERR_INVALID (not a PE-space context,
  * bad arguments) or FSMP_ERR_CUDA / FSMP_ERR_NOMEM. */

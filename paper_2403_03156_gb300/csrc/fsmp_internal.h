@@ -107,17 +107,19 @@ FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x
 // over its N-sample counts h[0 .. n_max], by Newton steps on
 //   l'(lambda) = -1 + E_w[N] / lambda,  l''(lambda) = (Var_w[N] - E_w[N]) / lambda^2,
 // w_N ∝ h[N] (lambda / lambda0)^N, from the sample mean (fixed-point steps lambda <- E_w[N]
-// where l'' >= 0); the boundary lambda = 0 when l(0) is not smaller. One warp, all lanes
-// call it and get the result; NAN if h is empty.
-__device__ inline double warp_lambda_mle(const int* h, int n_max, double lambda0, int lane) {
+// where l'' >= 0); the boundary lambda = 0 when l(0) is not smaller. A group of L consecutive
+// lanes (mask gm, sl the lane within it) calls it and every lane gets the result; NAN if h is
+// empty.
+template <int L>
+__device__ inline double group_lambda_mle(const int* h, int n_max, double lambda0, int sl, unsigned gm) {
   double c = 0.0, cn = 0.0;
   int top = -1;
-  for (int k = lane; k <= n_max; k += 32)
+  for (int k = sl; k <= n_max; k += L)
     if (h[k] > 0) { c += h[k]; cn += (double)k * h[k]; top = k; }
-  for (int o = 16; o > 0; o >>= 1) {
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-    cn += __shfl_xor_sync(0xffffffffu, cn, o);
-    top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+  for (int o = L / 2; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(gm, c, o, L);
+    cn += __shfl_xor_sync(gm, cn, o, L);
+    top = max(top, __shfl_xor_sync(gm, top, o, L));
   }
   if (top < 0) return NAN;
   if (top == 0) return 0.0;
@@ -125,19 +127,19 @@ __device__ inline double warp_lambda_mle(const int* h, int n_max, double lambda0
   for (int it = 0; it < 200; ++it) {
     const double s = log(lam / lambda0);
     double mx = -INFINITY;
-    for (int k = lane; k <= n_max; k += 32)
+    for (int k = sl; k <= n_max; k += L)
       if (h[k] > 0) mx = fmax(mx, log((double)h[k]) + k * s);
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = L / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(gm, mx, o, L));
     double sw = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int k = lane; k <= n_max; k += 32)
+    for (int k = sl; k <= n_max; k += L)
       if (h[k] > 0) {
         const double e = exp(log((double)h[k]) + k * s - mx);
         sw += e; s1 += k * e; s2 += (double)k * k * e;
       }
-    for (int o = 16; o > 0; o >>= 1) {
-      sw += __shfl_xor_sync(0xffffffffu, sw, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    for (int o = L / 2; o > 0; o >>= 1) {
+      sw += __shfl_xor_sync(gm, sw, o, L);
+      s1 += __shfl_xor_sync(gm, s1, o, L);
+      s2 += __shfl_xor_sync(gm, s2, o, L);
     }
     const double E = s1 / sw, Vr = s2 / sw - E * E;
     ll = -lam + mx + log(sw);
@@ -150,6 +152,9 @@ __device__ inline double warp_lambda_mle(const int* h, int n_max, double lambda0
   }
   const double l0 = h[0] > 0 ? log((double)h[0]) : -INFINITY;  // l(0): only N = 0 contributes
   return l0 >= ll ? 0.0 : lam;
+}
+__device__ inline double warp_lambda_mle(const int* h, int n_max, double lambda0, int lane) {
+  return group_lambda_mle<32>(h, n_max, lambda0, lane, 0xffffffffu);
 }
 #endif
 
@@ -178,19 +183,24 @@ cudaError_t chain_kernel_attributes(int precision, bool sigma_in_smem, int max_s
 // Resident CTAs per SM of the chain kernel for this block size and dynamic shared memory.
 int chain_kernel_occupancy(int precision, bool sigma_in_smem, int threads, size_t smem);
 cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, double* fp32_tflops);
-// PE-space kernel (fsmp_pe.cu): one warp per chain. Shared memory per CTA of `warps` chains with
-// windows up to n_alloc and a Ns x Ns shared tile of C^-1; FP64 workspace doubles per warp slot
-// (FP32 mode); row stride of a global C^-1 slot.
-size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns);
+// PE-space kernel (fsmp_pe.cu): a chain on `lanes` (32 or 16) lanes, warps per CTA. Shared memory
+// per CTA with windows up to n_alloc and a shared tile of C^-1 for Ns PEs per chain; FP64
+// workspace doubles per chain slot (FP32 mode); entries of a global C^-1 slot; ints of an N
+// histogram slot.
+size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int Ns);
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
 size_t pe_c_entries(int n_cap);  // entries of a global C^-1 slot (packed triangle)
+inline size_t pe_hist_ints(int n_cap) { return (size_t)n_cap + 1; }
 cudaError_t pe_kernel_attributes(int precision, int max_smem);
 cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st);
-int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big);
+int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int lanes);
 bool pe_big(int n_cap);
+bool pe_lanes_ok(int lanes, int n_cap);
+// Slots (C^-1, workspace, histogram) are indexed by resident chain: CTA x warps x (32 / lanes).
 // counter: one int of device memory, zeroed on `st` before the launch.
-cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas, int Ns, size_t smem, void* cinv,
-                      size_t c_stride, double* ws, size_t ws_stride, int* counter, cudaStream_t st);
+cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
+                      void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
+                      cudaStream_t st);
 // Set (or, with what == nullptr, clear) the calling thread's fsmp_last_error() message.
 void record_error(const char* what, const char* detail);
 

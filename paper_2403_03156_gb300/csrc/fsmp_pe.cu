@@ -16,9 +16,12 @@
 // E[Q | z, w] = N mu_q + sum_k v_k. Inner products a_i^T a_j over the window come from the SER
 // cross-correlation prefix table.
 //
-// Layout: a CTA holds several independent chains, one per warp; a warp takes chains from a
-// launch-wide counter. C^-1 sits in a per-warp shared-memory tile of Ns x Ns while N <= Ns and
-// moves to the warp's global slot (n_cap x ldc) when a birth would exceed the tile.
+// Layout: a chain runs on a group of L consecutive lanes (L = 32: a warp; L = 16: two chains per
+// warp, for chains with few PEs, where most of a step is work that every lane repeats); a CTA
+// holds several independent chains and a group takes chains from a launch-wide counter. C^-1 sits
+// in a per-chain shared-memory tile (the packed triangle of Ns PEs) while N <= Ns and moves to the
+// chain's global slot (n_cap PEs) when a birth would exceed the tile. The counts of N after
+// burn-in (for lambda_FSMP) sit in a global slot per chain.
 //
 // Precision. For PEs close in time C is nearly singular (eigenvalues down to r) and C^-1 holds
 // entries near 1/r that cancel in b^T C^-1 b; stored in FP32 they cost about 1e-2 in log alpha per
@@ -36,9 +39,30 @@
 namespace fsmp {
 namespace {
 
-constexpr int kPeRB = 32;  // steps per batch of random draws
-constexpr int kPeMaxThreads = 128;  // chains (warps) per CTA: at most 4
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPeMaxThreads = 128;  // warps per CTA: at most 4
+
+// The lanes of one chain: L consecutive lanes of a warp. Exchanges and reductions stay inside the
+// group; gm is its lane mask. A step draws the random numbers of the next L steps (one per lane).
+template <int L> struct Lanes {
+  int sl;       // lane within the group
+  int g;        // group within the warp
+  unsigned gm;  // lane mask of the group
+};
+template <int L> __device__ __forceinline__ Lanes<L> pe_lanes() {
+  static_assert(L == 32 || L == 16, "a chain runs on 32 or 16 lanes");
+  const int lane = threadIdx.x & 31;
+  Lanes<L> r;
+  r.sl = lane & (L - 1);
+  r.g = lane / L;
+  r.gm = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (r.g * L));
+  return r;
+}
+// the group's lanes with p set, as bits 0 .. L-1
+template <int L> __device__ __forceinline__ unsigned gballot(bool p, const Lanes<L> ln) {
+  const unsigned b = __ballot_sync(ln.gm, p);
+  if constexpr (L == 32) return b;
+  else return (b >> (ln.g * L)) & ((1u << L) - 1u);
+}
 
 // ---------------------------------------------------------------- float-float arithmetic
 // A value hi + lo with |lo| <= ulp(hi) / 2. TwoSum (Knuth) and the FMA-based exact product
@@ -76,8 +100,12 @@ __device__ __forceinline__ double crcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ double cnum(double a) { return a; }   // to the scoring precision
 __device__ __forceinline__ double c64(double a) { return a; }    // to FP64
 __device__ __forceinline__ bool cnz(double a) { return a != 0.0; }
-__device__ __forceinline__ double cshfl_xor(double a, int o) { return __shfl_xor_sync(kFull, a, o); }
-__device__ __forceinline__ double cshfl(double a, int src) { return __shfl_sync(kFull, a, src); }
+template <int L> __device__ __forceinline__ double cshfl_xor(double a, int o, unsigned gm) {
+  return __shfl_xor_sync(gm, a, o, L);
+}
+template <int L> __device__ __forceinline__ double cshfl(double a, int src, unsigned gm) {
+  return __shfl_sync(gm, a, src, L);
+}
 __device__ __forceinline__ double cfromf(double a) { return a; }
 template <typename C> __device__ __forceinline__ C czero();
 template <> __device__ __forceinline__ double czero<double>() { return 0.0; }
@@ -95,11 +123,11 @@ __device__ __forceinline__ ff crcp(ff a) {  // one Newton step on the FP32 recip
 __device__ __forceinline__ float cnum(ff a) { return __fadd_rn(a.hi, a.lo); }
 __device__ __forceinline__ double c64(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ bool cnz(ff a) { return a.hi != 0.0f; }
-__device__ __forceinline__ ff cshfl_xor(ff a, int o) {
-  return ff{__shfl_xor_sync(kFull, a.hi, o), __shfl_xor_sync(kFull, a.lo, o)};
+template <int L> __device__ __forceinline__ ff cshfl_xor(ff a, int o, unsigned gm) {
+  return ff{__shfl_xor_sync(gm, a.hi, o, L), __shfl_xor_sync(gm, a.lo, o, L)};
 }
-__device__ __forceinline__ ff cshfl(ff a, int src) {
-  return ff{__shfl_sync(kFull, a.hi, src), __shfl_sync(kFull, a.lo, src)};
+template <int L> __device__ __forceinline__ ff cshfl(ff a, int src, unsigned gm) {
+  return ff{__shfl_sync(gm, a.hi, src, L), __shfl_sync(gm, a.lo, src, L)};
 }
 __device__ __forceinline__ ff cfromf(float a) { return ff{a, 0.0f}; }
 template <> __device__ __forceinline__ ff czero<ff>() { return ff{0.0f, 0.0f}; }
@@ -118,16 +146,16 @@ template <typename C> __device__ __forceinline__ C c_r(const DevModel& M);
 template <> __device__ __forceinline__ double c_r<double>(const DevModel& M) { return M.se2 / M.sq2; }
 template <> __device__ __forceinline__ ff c_r<ff>(const DevModel& M) { return ff{M.r_hi, M.r_lo}; }
 
-// warp sums of state values: over all lanes, or over lanes [0, m) (zero beyond m)
-template <typename C> __device__ __forceinline__ C csum(C v) {
+// group sums of state values: over all lanes, or over lanes [0, m) (zero beyond m)
+template <int L, typename C> __device__ __forceinline__ C csum(C v, const Lanes<L> ln) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = cadd(v, cshfl_xor(v, o));
+  for (int o = L / 2; o > 0; o >>= 1) v = cadd(v, cshfl_xor<L>(v, o, ln.gm));
   return v;
 }
-template <typename C> __device__ __forceinline__ C csum_first(C v, int m) {
-  for (int o = 16; o > 0; o >>= 1)
-    if (o < m) v = cadd(v, cshfl_xor(v, o));
-  return cshfl(v, 0);
+template <int L, typename C> __device__ __forceinline__ C csum_first(C v, int m, const Lanes<L> ln) {
+  for (int o = L / 2; o > 0; o >>= 1)
+    if (o < m) v = cadd(v, cshfl_xor<L>(v, o, ln.gm));
+  return cshfl<L>(v, 0, ln.gm);
 }
 
 // C^-1 is symmetric and stored as its lower triangle, row by row: entry (i, j), j <= i, at
@@ -169,14 +197,14 @@ __device__ __forceinline__ C dot_row(const C* __restrict__ Cp, int q, const int*
   return s0;
 }
 
-template <typename T> __device__ __forceinline__ T wsum(T v) {
+template <int L, typename T> __device__ __forceinline__ T wsum(T v, const Lanes<L> ln) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(ln.gm, v, o, L);
   return v;
 }
-template <typename T> __device__ __forceinline__ T wmax(T v) {
+template <int L, typename T> __device__ __forceinline__ T wmax(T v, const Lanes<L> ln) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(ln.gm, v, o, L));
   return v;
 }
 
@@ -232,18 +260,19 @@ template <typename C> __device__ __forceinline__ C xcorr(const DevModel& M, cons
   return v;
 }
 
-// Smallest j in [T_lo, T_hi) with cphi(j - k0) - base > target (32-ary warp search); if rounding
-// leaves none, the last j of T with phi > 0.
-template <typename T>
-__device__ int pe_birth_search(const DevModel& M, int T_lo, int T_hi, int k0, T base, T target, int lane) {
+// Smallest j in [T_lo, T_hi) with cphi(j - k0) - base > target (L-ary group search; cphi is
+// non-decreasing, so the answer does not depend on L); if rounding leaves none, the last j of T
+// with phi > 0.
+template <typename T, int L>
+__device__ int pe_birth_search(const DevModel& M, int T_lo, int T_hi, int k0, T base, T target, const Lanes<L> ln) {
   int lo = T_lo, hi = T_hi - 1;
   if ((pe_cphi<T>(M, hi - k0) - base) > target) {
     while (lo < hi) {
       const int len = hi - lo + 1;
-      const int step = (len + 31) / 32;
-      const int p = min(hi, lo + (lane + 1) * step - 1);
+      const int step = (len + L - 1) / L;
+      const int p = min(hi, lo + (ln.sl + 1) * step - 1);
       const bool pred = (pe_cphi<T>(M, p - k0) - base) > target;
-      const unsigned b = __ballot_sync(kFull, pred);
+      const unsigned b = gballot(pred, ln);
       const int f = __ffs(b) - 1;
       const int new_lo = lo + f * step;
       hi = min(hi, lo + (f + 1) * step - 1);
@@ -252,10 +281,10 @@ __device__ int pe_birth_search(const DevModel& M, int T_lo, int T_hi, int k0, T 
     return lo;
   }
   int last = -1;
-  for (int top = T_hi - 1; top >= T_lo; top -= 32) {
-    const int j = top - lane;
+  for (int top = T_hi - 1; top >= T_lo; top -= L) {
+    const int j = top - ln.sl;
     const bool ok = j >= T_lo && pe_logphi<T>(M, j - k0) > (T)-INFINITY;
-    const unsigned b = __ballot_sync(kFull, ok);
+    const unsigned b = gballot(ok, ln);
     if (b) { last = top - (__ffs(b) - 1); break; }
   }
   return last;
@@ -271,7 +300,7 @@ __device__ __forceinline__ float u01_float(uint64_t x) {
   return __ull2float_rn(((x >> 11) << 1) | 1ull) * 0x1.0p-54f;
 }
 
-// Per-chain statistics (shared memory, written by lane 0).
+// Per-chain statistics (shared memory, written by the group's first lane).
 struct PeStats {
   long long sN, sN2, sK, sK2;
   double sQ, sQ2, q_cur, logdet, logL, drift_max, wsq;
@@ -281,13 +310,12 @@ struct PeStats {
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Per-warp shared memory. C is the state type (8 bytes in both modes).
-template <typename T> struct PeWarp {
+// Per-chain shared memory. C is the state type (8 bytes in both modes).
+template <typename T> struct PeChain {
   using C = typename PeTab<T>::C;
   PeStats* st;
-  PeRand<T>* rnd;
+  PeRand<T>* rnd;  // draws of the next L steps [L]
   int* list;   // PE grid indices [n_cap]
-  int* hist;   // counts of N over the samples after burn-in [n_cap + 1]
   int* ovi;    // PEs overlapping the proposed one [n_cap]
   C* ovb;      // their inner products with it [n_cap]
   C* v;        // C^-1 A^T y [n_cap]
@@ -297,23 +325,21 @@ template <typename T> struct PeWarp {
   T* lPhi;     // log(Phi_T(t0) g) on the chain's t0 grid [win_extra]
   C* Cs;       // C^-1 tile: packed triangle of Ns PEs
 };
-template <typename T> __host__ __device__ inline size_t pe_warp_bytes(int n_cap, int n_alloc, int win_extra, int Ns) {
-  return a16(sizeof(PeStats)) + a16(sizeof(PeRand<T>) * kPeRB) + 2 * a16(sizeof(int) * n_cap) +
-         a16(sizeof(int) * (n_cap + 1)) +
+template <typename T, int L> __host__ __device__ inline size_t pe_chain_bytes(int n_cap, int n_alloc, int win_extra, int Ns) {
+  return a16(sizeof(PeStats)) + a16(sizeof(PeRand<T>) * L) + 2 * a16(sizeof(int) * n_cap) +
          4 * a16(8 * (size_t)n_cap) + a16(sizeof(T) * n_alloc) + a16(sizeof(T) * win_extra) +
          a16(8 * (size_t)tri(Ns));
 }
 template <typename T> __host__ __device__ inline size_t pe_block_bytes(int Lt, int n_cap) {
   return a16(sizeof(T) * Lt) + a16(sizeof(T) * (n_cap + 2));
 }
-template <typename T> __device__ PeWarp<T> pe_carve(unsigned char* p, int n_cap, int n_alloc, int win_extra, int Ns) {
+template <typename T, int L> __device__ PeChain<T> pe_carve(unsigned char* p, int n_cap, int n_alloc, int win_extra, int Ns) {
   using C = typename PeTab<T>::C;
-  PeWarp<T> W;
+  PeChain<T> W;
   size_t o = 0;
   W.st = reinterpret_cast<PeStats*>(p + o); o += a16(sizeof(PeStats));
-  W.rnd = reinterpret_cast<PeRand<T>*>(p + o); o += a16(sizeof(PeRand<T>) * kPeRB);
+  W.rnd = reinterpret_cast<PeRand<T>*>(p + o); o += a16(sizeof(PeRand<T>) * L);
   W.list = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
-  W.hist = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * (n_cap + 1));
   W.ovi = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
   W.ovb = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
   W.v = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
@@ -325,17 +351,18 @@ template <typename T> __device__ PeWarp<T> pe_carve(unsigned char* p, int n_cap,
   return W;
 }
 
-// Global per-warp slots.
+// Global per-chain slots (one per resident chain of the launch).
 struct PeSlots {
   void* C;             // C^-1 slots (8-byte entries): the packed triangle of n_cap PEs
   size_t c_stride;     // entries per slot
   double* ws;          // FP64 refresh workspace slots (FP32 mode)
   size_t ws_stride;    // doubles per slot
+  int* hist;           // N histogram slots, n_cap + 1 counts each
   int* counter;        // next chain of the launch (zeroed before the launch)
   int Ns;              // shared-memory tile of C^-1 (0: always global)
 };
 
-// FP64 refresh workspace of one warp: C (n_cap x n_cap) and four vectors of max(n_cap, n_alloc).
+// FP64 refresh workspace of one chain: C (n_cap x n_cap) and four vectors of max(n_cap, n_alloc).
 __host__ __device__ inline int pe_lvec(int n_cap, int n_alloc) { return n_cap > n_alloc ? n_cap : n_alloc; }
 __host__ __device__ inline size_t pe_ws_doubles(int n_cap, int n_alloc) {
   return (size_t)n_cap * n_cap + 4 * (size_t)pe_lvec(n_cap, n_alloc);
@@ -359,10 +386,10 @@ struct RefreshOut {
 // FP64 rebuild of C^-1, v, y, log|Sigma| and the log-likelihood from the PE list (FP32 mode).
 // ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
 // value (no address of the caller's locals escapes, so they stay in registers).
-template <typename T, bool BIG>
-__device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T> W, typename PeTab<T>::C* Cp,
+template <typename T, bool BIG, int L>
+__device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T> W, typename PeTab<T>::C* Cp,
                                               double* ws, int n_cap, int lvec, const float* w, double wsq, int n,
-                                              int N, int lane) {
+                                              int N, const Lanes<L> ln) {
   using C = typename PeTab<T>::C;
   RefreshOut out{0, 0.0, 0.0, 0.0};
   const int ws_ld = N > 0 ? N : 1;
@@ -378,19 +405,19 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     const int ji = W.list[i];
     const Sup si = pe_sup(M, n, ji);
 #pragma unroll 1
-    for (int j = lane; j < N; j += 32) {
+    for (int j = ln.sl; j < N; j += L) {
       const int o = ji - W.list[j];
       double c = (o > -M.Lt && o < M.Lt) ? xcorr<double>(M, M.tc64, si, o) : 0.0;
       if (j == i) c += r;
       A[(size_t)i * ws_ld + j] = c;
     }
   }
-  __syncwarp();
+  __syncwarp(ln.gm);
   // With y = w - mu A 1: h = A^T y = A^T w - mu (A^T A) 1, and
   // y^T y = w^T w - 2 mu 1^T A^T w + mu^2 1^T A^T A 1 -- no FP64 copy of y is needed.
   double awt = 0.0, rst = 0.0;
 #pragma unroll 1
-  for (int k = lane; k < N; k += 32) {
+  for (int k = ln.sl; k < N; k += L) {
     const Sup s = pe_sup(M, n, W.list[k]);
     double a0 = 0.0, a1 = 0.0;
     int i = s.ilo;
@@ -408,12 +435,12 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     awt += aw;
     rst += rs;
   }
-  awt = wsum(awt);
-  rst = wsum(rst);
+  awt = wsum(awt, ln);
+  rst = wsum(rst, ln);
   const double yy = wsq - 2.0 * mu * awt + mu * mu * rst;
   // the FP32 residual, each sample summed in FP64 over the PEs that cover it
 #pragma unroll 1
-  for (int x = lane; x < n; x += 32) {
+  for (int x = ln.sl; x < n; x += L) {
     double yv = (double)w[x];
 #pragma unroll 1
     for (int k = 0; k < N; ++k) {
@@ -422,7 +449,7 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     }
     W.y[x] = (T)yv;
   }
-  __syncwarp();
+  __syncwarp(ln.gm);
   // Gauss-Jordan inversion in place with diagonal pivots (C is SPD: the pivots are the
   // LDL^T pivots, all positive); log|C| = sum log pivot, kept as mantissa x 2^exponent
   double pm = 1.0;
@@ -430,11 +457,11 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
 #pragma unroll 1
   for (int k = 0; k < N; ++k) {
 #pragma unroll 1
-    for (int j = lane; j < N; j += 32) {
+    for (int j = ln.sl; j < N; j += L) {
       rowk[j] = A[(size_t)k * ws_ld + j];
       colk[j] = A[(size_t)j * ws_ld + k];
     }
-    __syncwarp();
+    __syncwarp(ln.gm);
     const double piv = rowk[k];
     if (!(piv > 0.0) || !isfinite(piv)) return out;
     const double ip = 1.0 / piv;
@@ -444,12 +471,12 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     pm = frexp(pm, &ex);
     pe += ex;
 #pragma unroll 1
-    for (int j = lane; j < N; j += 32) colk[j] *= ip;  // the row multipliers
-    __syncwarp();
+    for (int j = ln.sl; j < N; j += L) colk[j] *= ip;  // the row multipliers
+    __syncwarp(ln.gm);
     // rows i != k: A_ij -= f_i A_kj (A_ik = -f_i); row k: A_kj / pivot. Lanes over columns
     // (BIG: four rows per iteration so that their loads overlap).
 #pragma unroll 1
-    for (int j = lane; j < N; j += 32) {
+    for (int j = ln.sl; j < N; j += L) {
       const double rkj = rowk[j];
       int i = 0;
       if constexpr (BIG) {
@@ -473,12 +500,12 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
         A[(size_t)i * ws_ld + j] = (i == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x));
       }
     }
-    __syncwarp();
+    __syncwarp(ln.gm);
   }
   const double logdetC = log(pm) + (double)pe * 0.6931471805599453;
   // v = C^-1 h (C^-1 symmetric: lanes over columns)
 #pragma unroll 1
-  for (int i = lane; i < N; i += 32) {
+  for (int i = ln.sl; i < N; i += L) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int j = 0;
 #pragma unroll 1
@@ -492,15 +519,15 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
     for (; j < N; ++j) s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
     rowk[i] = (s0 + s1) + (s2 + s3);
   }
-  __syncwarp();
+  __syncwarp(ln.gm);
   double hv = 0.0;
 #pragma unroll 1
-  for (int i = lane; i < N; i += 32) hv += h[i] * rowk[i];
-  hv = wsum(hv);
+  for (int i = ln.sl; i < N; i += L) hv += h[i] * rowk[i];
+  hv = wsum(hv, ln);
   // drift of the incremental state, then the refreshed state (packed lower triangle)
   double dmax = 0.0, amax = 0.0;
 #pragma unroll 1
-  for (int e = lane; e < tri(N); e += 32) {
+  for (int e = ln.sl; e < tri(N); e += L) {
     int i, j;
     untri(e, i, j);
     const double nv = A[(size_t)i * ws_ld + j];
@@ -510,13 +537,13 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeWarp<T>
   }
   double vd = 0.0, va = 0.0;
 #pragma unroll 1
-  for (int i = lane; i < N; i += 32) {
+  for (int i = ln.sl; i < N; i += L) {
     vd = fmax(vd, fabs(rowk[i] - c64(W.v[i])));
     va = fmax(va, fabs(rowk[i]));
     W.v[i] = cfrom64<C>(rowk[i]);
   }
-  dmax = wmax(dmax); amax = wmax(amax); vd = wmax(vd); va = wmax(va);
-  __syncwarp();
+  dmax = wmax(dmax, ln); amax = wmax(amax, ln); vd = wmax(vd, ln); va = wmax(va, ln);
+  __syncwarp(ln.gm);
   out.ok = 1;
   out.drift = fmax(amax > 0.0 ? dmax / amax : 0.0, va > 0.0 ? vd / fmax(va, 1.0) : 0.0);
   out.logdet = n * M.log_se2 + logdetC - N * M.log_r;
@@ -540,12 +567,12 @@ template <typename C> struct AcceptOut {
 // Apply an accepted move to C^-1, v, y and the PE list (out of line: it runs on a minority of
 // steps and keeps the per-step code compact). Returns the new N, and the new C^-1 storage when
 // it moves from the shared tile (capacity cap PEs) to the global slot (n_cap PEs).
-template <typename T, bool BIG>
-__device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel& M, const PeWarp<T> W, const T* Vs,
+template <typename T, bool BIG, int L>
+__device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel& M, const PeChain<T> W, const T* Vs,
                                                                   typename PeTab<T>::C* Cp, int cap,
                                                                   typename PeTab<T>::C* Cg,
                                                                   const PeMove<typename PeTab<T>::C> mv, int n, int N,
-                                                                  int lane) {
+                                                                  const Lanes<L> ln) {
   // One form for the three moves. With c = row k of C^-1 (death, update), gamma = c_k, and
   // u' = C_-^-1 b~ (birth, update: C_- is C without PE k for an update, C itself for a birth;
   // b~ is b without its k entry), delta = r + |a_+|^2 - b~^T u':
@@ -567,13 +594,13 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   const int krow = has_m ? kk : 0;
   const int npu = has_p ? np : 0;
 #pragma unroll 1
-  for (int i = lane; i < N; i += 32) {
+  for (int i = ln.sl; i < N; i += L) {
     const C ci = Cp[pk(krow, i)];
     W.cv[i] = has_m ? ci : czero<C>();
     W.uv[i] = dot_row<C, BIG>(Cp, i, W.ovi, W.ovb, npu, skip);
   }
-  if (lane == 0 && jump == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth (N < n_cap)
-  __syncwarp();
+  if (ln.sl == 0 && jump == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth (N < n_cap)
+  __syncwarp(ln.gm);
   C ig = czero<C>(), idl = czero<C>(), t = czero<C>(), fv = czero<C>();
   if (has_m) {
     ig = crcp(W.cv[kk]);
@@ -583,26 +610,26 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     // b^T v in full state precision (the scoring used an FP32 sum)
     C bvf = czero<C>();
 #pragma unroll 1
-    for (int a = lane; a < np; a += 32) bvf = cfma(W.ovb[a], W.v[W.ovi[a]], bvf);
-    bvf = csum(bvf);
+    for (int a = ln.sl; a < np; a += L) bvf = cfma(W.ovb[a], W.v[W.ovi[a]], bvf);
+    bvf = csum(bvf, ln);
     C bk = czero<C>(), wk = czero<C>();
     if (jump == 2) {
       // u' = w - c w_k / gamma on the system without PE k
       wk = W.uv[kk];
       const C wkg = cneg(cmul(wk, ig));
 #pragma unroll 1
-      for (int i = lane; i < N; i += 32) W.uv[i] = (i == kk) ? czero<C>() : cfma(W.cv[i], wkg, W.uv[i]);
+      for (int i = ln.sl; i < N; i += L) W.uv[i] = (i == kk) ? czero<C>() : cfma(W.cv[i], wkg, W.uv[i]);
 #pragma unroll 1
-      for (int a = lane; a < np; a += 32)
+      for (int a = ln.sl; a < np; a += L)
         if (W.ovi[a] == kk) bk = W.ovb[a];
-      bk = csum(bk);
-      __syncwarp();
+      bk = csum(bk, ln);
+      __syncwarp(ln.gm);
     }
     C bu = czero<C>();
 #pragma unroll 1
-    for (int a = lane; a < np; a += 32)
+    for (int a = ln.sl; a < np; a += L)
       if (W.ovi[a] != skip) bu = cfma(W.ovb[a], W.uv[W.ovi[a]], bu);
-    bu = csum(bu);
+    bu = csum(bu, ln);
     idl = crcp(csub(cadd(rr, mv.aa), bu));
     // t = (b~^T v_- - mu b~^T u' - h_new) / delta with v_- = v after removing PE k and h_new the
     // new PE's a^T y on the residual without PE k
@@ -612,17 +639,17 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   }
   if (jump == 0 && N + 1 > cap && Cp != Cg) {  // the tile is full: move C^-1 to the global slot
 #pragma unroll 1
-    for (int e = lane; e < tri(N); e += 32) Cg[e] = Cp[e];
+    for (int e = ln.sl; e < tri(N); e += L) Cg[e] = Cp[e];
     Cp = Cg;
     cap = M.n_cap;
-    __syncwarp();
+    __syncwarp(ln.gm);
   }
   // C^-1 in place over the packed triangle, all lanes on consecutive entries. A pass reads an
   // entry only where it writes it, or in the last row for a death (which it does not write).
   const C nig = cneg(ig);
   const int kmap = jump == 1 ? kk : -1;  // the slot the last PE moves into
 #pragma unroll 1
-  for (int e = lane; e < tri(Nout); e += 32) {  // rows 0 .. Nout-1
+  for (int e = ln.sl; e < tri(Nout); e += L) {  // rows 0 .. Nout-1
     int i, j;
     untri(e, i, j);
     const int mi = (i == kmap) ? last : i, mj = (j == kmap) ? last : j;
@@ -634,7 +661,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   // v' = v_m - c_m fv + (t - mu) u', v'_s = -t
   const C tm = csub(t, mu), nfv = cneg(fv);
 #pragma unroll 1
-  for (int i = lane; i < Nout; i += 32) {
+  for (int i = ln.sl; i < Nout; i += L) {
     const int mi = (i == kmap) ? last : i;
     const C val = cfma(tm, W.uv[i], cfma(W.cv[mi], nfv, W.v[mi]));
     W.v[i] = (i == s) ? cneg(t) : val;
@@ -644,32 +671,34 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   if (has_m) {
     const Sup sm = pe_sup(M, n, mv.jm);
 #pragma unroll 1
-    for (int i = sm.ilo + lane; i < sm.ihi; i += 32) W.y[sm.w0 + i] += muT * Vs[sm.ph + i * R];
+    for (int i = sm.ilo + ln.sl; i < sm.ihi; i += L) W.y[sm.w0 + i] += muT * Vs[sm.ph + i * R];
     wds += 2 * (sm.ihi - sm.ilo) + N;
-    __syncwarp();
+    __syncwarp(ln.gm);
   }
   if (has_p) {
     const Sup sp = mv.sp;
 #pragma unroll 1
-    for (int i = sp.ilo + lane; i < sp.ihi; i += 32) W.y[sp.w0 + i] -= muT * Vs[sp.ph + i * R];
+    for (int i = sp.ilo + ln.sl; i < sp.ihi; i += L) W.y[sp.w0 + i] -= muT * Vs[sp.ph + i * R];
     wds += 2 * (sp.ihi - sp.ilo);
   }
-  if (lane == 0) {
+  if (ln.sl == 0) {
     if (jump == 0) W.list[N] = mv.jp;
     else if (jump == 1) W.list[kk] = W.list[last];
     else W.list[kk] = mv.jp;
   }
-  __syncwarp();
+  __syncwarp(ln.gm);
   return AcceptOut<C>{Cp, cap, Nout, wds};
 }
 
-template <typename T, bool BIG>
+template <typename T, bool BIG, int L>
 __global__ void __launch_bounds__(kPeMaxThreads, 4)
     pe_kernel(const __grid_constant__ DevModel M, const __grid_constant__ BatchView B, const __grid_constant__ PeSlots G) {
   using C = typename PeTab<T>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool fp32 = sizeof(T) == 4;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const Lanes<L> ln = pe_lanes<L>();
+  constexpr int kGroups = 32 / L;  // chains per warp
+  const int cw = (threadIdx.x >> 5) * kGroups + ln.g, nchains = (blockDim.x >> 5) * kGroups;
   const int n_alloc = B.n_max, n_cap = M.n_cap, Ns = G.Ns;
   // block tables: the SER and log(i), i = 1 .. n_cap + 1
   T* Vs = reinterpret_cast<T*>(smem_raw);
@@ -678,11 +707,12 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
   for (int i = threadIdx.x; i < n_cap + 2; i += blockDim.x)
     lgN[i] = i > 0 ? (fp32 ? (T)logf((float)i) : (T)log((double)i)) : (T)0;
   __syncthreads();
-  PeWarp<T> W = pe_carve<T>(smem_raw + pe_block_bytes<T>(M.Lt, n_cap) +
-                                (size_t)warp * pe_warp_bytes<T>(n_cap, n_alloc, M.win_extra, Ns),
-                            n_cap, n_alloc, M.win_extra, Ns);
+  PeChain<T> W = pe_carve<T, L>(smem_raw + pe_block_bytes<T>(M.Lt, n_cap) +
+                                    (size_t)cw * pe_chain_bytes<T, L>(n_cap, n_alloc, M.win_extra, Ns),
+                                n_cap, n_alloc, M.win_extra, Ns);
   PeStats& S = *W.st;
-  const size_t slot = (size_t)blockIdx.x * nwarps + warp;
+  const size_t slot = (size_t)blockIdx.x * nchains + cw;
+  int* const hist = G.hist + slot * (size_t)(n_cap + 1);
   C* const Cg = G.C ? reinterpret_cast<C*>(G.C) + slot * G.c_stride : nullptr;
   double* const ws = G.ws ? G.ws + slot * G.ws_stride : nullptr;
   const C* __restrict__ tc = PeTab<T>::tc(M);
@@ -692,8 +722,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
 
   for (;;) {
     int ci = 0;
-    if (lane == 0) ci = atomicAdd(G.counter, 1);
-    ci = __shfl_sync(kFull, ci, 0);
+    if (ln.sl == 0) ci = atomicAdd(G.counter, 1);
+    ci = __shfl_sync(ln.gm, ci, 0, L);
     if (ci >= B.n_waveforms) break;
     const int wi = B.order ? B.order[ci] : ci;
     // ------------------------------------------------------------- chain set-up
@@ -715,7 +745,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
                          burn_in < 0 || (fp32 && ws == nullptr) || k0_hi - k0_lo + 1 > M.win_extra ||
                          (Cg == nullptr && Ns < n_cap);
     if (invalid) {
-      if (lane == 0) {
+      if (ln.sl == 0) {
         fsmp_summary o;
         o.mean_N = o.var_N = o.mean_t0 = o.var_t0 = o.mean_Q = o.var_Q = o.logL = o.logdet = NAN;
         o.drift_max = 0.0; o.alg_bytes = 0.0; o.lambda_hat = NAN;
@@ -724,7 +754,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         o.status = FSMP_ST_INVALID;
         *out = o;
       }
-      __syncwarp();
+      __syncwarp(ln.gm);
       continue;
     }
     int k0;
@@ -739,22 +769,22 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       }
     }
     // log(Phi_T(t0) g) on the t0 grid (-inf where Phi_T = 0), from the FP64 tables
-    for (int k = lane; k <= k0_hi - k0_lo; k += 32) {
+    for (int k = ln.sl; k <= k0_hi - k0_lo; k += L) {
       const int kq = k0_lo + k;
       const double tot = pe_cphi<double>(M, T_hi - 1 - kq) - pe_cphi<double>(M, T_lo - 1 - kq);
       W.lPhi[k] = tot > 0.0 ? (fp32 ? (T)logf((float)(tot * M.g)) : (T)log(tot * M.g)) : (T)-INFINITY;
     }
 #pragma unroll 1
-    for (int k = lane; k <= n_cap; k += 32) W.hist[k] = 0;
+    for (int k = ln.sl; k <= n_cap; k += L) hist[k] = 0;
     // empty z: y = w
     double wsq = 0.0;
-    for (int x = lane; x < n; x += 32) {
+    for (int x = ln.sl; x < n; x += L) {
       const float wx = w[x];
       W.y[x] = (T)wx;
       wsq += (double)wx * (double)wx;
     }
-    wsq = wsum(wsq);
-    if (lane == 0) {
+    wsq = wsum(wsq, ln);
+    if (ln.sl == 0) {
       S.sN = S.sN2 = S.sK = S.sK2 = 0;
       S.sQ = S.sQ2 = 0.0; S.q_cur = 0.0; S.q_from = 0;
       S.logdet = n * M.log_se2;
@@ -764,19 +794,19 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       for (int k = 0; k < 3; ++k) { S.acc[k] = 0; S.prop[k] = 0; }
       S.acc_t0 = S.prop_t0 = S.n_refresh = S.status = S.n_acc_refresh = S.refresh_fail = 0;
     }
-    __syncwarp();
+    __syncwarp(ln.gm);
     const T log_lambda0 = fp32 ? (T)logf((float)lambda0) : (T)log(lambda0);
     C* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1 (packed), room for cap PEs
     int cap = Ns > 0 ? Ns : n_cap;
     int N = 0;
 
     for (int step = 0; step < n_steps; ++step) {
-      // ---- random draws of the next kPeRB steps: lane l takes step step + l
-      if ((step & (kPeRB - 1)) == 0) {
+      // ---- random draws of the next L steps: lane l takes step step + l
+      if ((step & (L - 1)) == 0) {
         PeRand<T> rd;
 #pragma unroll 1
         for (int blk = 0; blk < 2; ++blk) {
-          uint64_t c[4] = {(uint64_t)(step + lane), (uint64_t)blk, 0, 0};
+          uint64_t c[4] = {(uint64_t)(step + ln.sl), (uint64_t)blk, 0, 0};
           philox4x64_10(c, seed, wf_id);
           if (fp32) {
             const float a = u01_float(c[0]), b = u01_float(c[1]), d = u01_float(c[2]), e = u01_float(c[3]);
@@ -803,10 +833,10 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
             }
           }
         }
-        W.rnd[lane] = rd;
-        __syncwarp();
+        W.rnd[ln.sl] = rd;
+        __syncwarp(ln.gm);
       }
-      const PeRand<T> rd = W.rnd[step & (kPeRB - 1)];
+      const PeRand<T> rd = W.rnd[step & (L - 1)];
       // ---- Gibbs part 1: MH on t0 (Sec. 2.4), uniform prior on its grid range
       T la0 = (T)NAN;
       const T lu0 = rd.lu0;
@@ -822,11 +852,11 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         } else {
           T part = (T)0;
 #pragma unroll 1
-          for (int k = lane; k < N; k += 32) {
+          for (int k = ln.sl; k < N; k += L) {
             const int j = W.list[k];
             part += pe_logphi<T>(M, j - k0p) - pe_logphi<T>(M, j - k0);
           }
-          la0 = wsum(part);
+          la0 = wsum(part, ln);
         }
         if (lu0 < la0) { k0 = k0p; t0f |= 2; }
       }
@@ -841,7 +871,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           st_a |= FSMP_ST_CAPACITY;
         } else if (lphi_t0 > (T)-INFINITY) {
           const T base = pe_cphi<T>(M, T_lo - 1 - k0), tot = pe_cphi<T>(M, T_hi - 1 - k0) - base;
-          jp = pe_birth_search<T>(M, T_lo, T_hi, k0, base, rd.u4 * tot, lane);
+          jp = pe_birth_search<T, L>(M, T_lo, T_hi, k0, base, rd.u4 * tot, ln);
           valid = jp >= T_lo;
           la_prior = log_lambda0 + lphi_t0 - lgN[N + 1] + (N == 0 ? logJ : (T)0);
         }
@@ -881,36 +911,36 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           // PEs overlapping a_+, with b_q = a_q^T a_+
           int np = 0;
 #pragma unroll 1
-          for (int base = 0; base < N; base += 32) {
-            const int qi = base + lane;
+          for (int base = 0; base < N; base += L) {
+            const int qi = base + ln.sl;
             C bq = czero<C>();
             if (qi < N) {
               const int o = jp - W.list[qi];
               if (o > -M.Lt && o < M.Lt) bq = xcorr<C>(M, tc, sp, o);
             }
             const bool ov = cnz(bq);
-            const unsigned m = __ballot_sync(kFull, ov);
+            const unsigned m = gballot(ov, ln);
             if (ov) {
-              const int pos = np + __popc(m & ((1u << lane) - 1u));
+              const int pos = np + __popc(m & ((1u << ln.sl) - 1u));
               W.ovi[pos] = qi;
               W.ovb[pos] = bq;
             }
             np += __popc(m);
           }
-          __syncwarp();
+          __syncwarp(ln.gm);
           mv.np = np;
           mv.aa = xcorr<C>(M, tc, sp, 0);
-          // rows of C^-1 b on the overlap set: lane a holds (C^-1 b)_{ovi[a]}, so that b^T C^-1 b
-          // and b^T v reduce over np lanes and (C^-1 b)_k is one of them for an update
+          // rows of C^-1 b on the overlap set: lane a holds (C^-1 b)_{ovi[a]} (a < L), so that
+          // b^T C^-1 b and b^T v reduce over the group and (C^-1 b)_k is one of them for an update
           T ayp = (T)0;
 #pragma unroll 1
-          for (int i = sp.ilo + lane; i < sp.ihi; i += 32) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
+          for (int i = sp.ilo + ln.sl; i < sp.ihi; i += L) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
           C qp = czero<C>(), ck = czero<C>();
           T bvp = (T)0;
           int kpos = -1;
 #pragma unroll 1
-          for (int a0 = 0; a0 < np; a0 += 32) {
-            const int a = a0 + lane;
+          for (int a0 = 0; a0 < np; a0 += L) {
+            const int a = a0 + ln.sl;
             if (a < np) {
               const C rq = dot_row<C, BIG>(Cp, W.ovi[a], W.ovi, W.ovb, np, -1);
               const C ba = W.ovb[a];
@@ -919,20 +949,20 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
               if (jump == 2 && W.ovi[a] == kk) { ck = rq; kpos = a; }
             }
           }
-          mv.quad = np <= 32 ? csum_first(qp, np) : csum(qp);
-          const T bvT = wsum(bvp);  // b^T v at the scoring precision (the accept recomputes it)
-          const T ayT = wsum(ayp);
+          mv.quad = np <= L ? csum_first(qp, np, ln) : csum(qp, ln);
+          const T bvT = wsum(bvp, ln);  // b^T v at the scoring precision (the accept recomputes it)
+          const T ayT = wsum(ayp, ln);
           mv.ay = cfromf(ayT);
           if (jump == 2) {
             // (C^-1 b)_k: from the lane that holds PE k's row, else (no overlap with the old
             // position) a separate dot product
-            const unsigned hk = __ballot_sync(kFull, kpos >= 0);
+            const unsigned hk = gballot(kpos >= 0, ln);
             if (hk) {
-              ck = cshfl(ck, __ffs(hk) - 1);
+              ck = cshfl<L>(ck, __ffs(hk) - 1, ln.gm);
             } else {
               C c2 = czero<C>();
-              for (int a = lane; a < np; a += 32) c2 = cfma(Cp[pk(kk, W.ovi[a])], W.ovb[a], c2);
-              ck = csum(c2);
+              for (int a = ln.sl; a < np; a += L) c2 = cfma(Cp[pk(kk, W.ovi[a])], W.ovb[a], c2);
+              ck = csum(c2, ln);
             }
           }
           mpp = (T)cnum(csub(mv.aa, mv.quad)) * ise2T;
@@ -978,16 +1008,16 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       // ---- accepted move: C^-1, v, y and the PE list
       if (apply) {
         {
-          const AcceptOut<C> ao = pe_accept<T, BIG>(M, W, Vs, Cp, cap, Cg, mv, n, N, lane);
+          const AcceptOut<C> ao = pe_accept<T, BIG, L>(M, W, Vs, Cp, cap, Cg, mv, n, N, ln);
           Cp = ao.Cp;
           cap = ao.cap;
           N = ao.N;
           words += ao.words;
         }
         C qs = czero<C>();
-        for (int i = lane; i < N; i += 32) qs = cadd(qs, W.v[i]);
-        qs = csum(qs);
-        if (lane == 0) {
+        for (int i = ln.sl; i < N; i += L) qs = cadd(qs, W.v[i]);
+        qs = csum(qs, ln);
+        if (ln.sl == 0) {
           close_hold(S, step, burn_in);
           S.q_cur = N * M.mu_q + c64(qs);
           S.q_from = step;
@@ -995,13 +1025,13 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           S.logL += (double)dnu;
           S.n_acc_refresh++;
         }
-        __syncwarp();
+        __syncwarp(ln.gm);
         if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, lane);
+          const RefreshOut ro = pe_refresh<T, BIG, L>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, ln);
           C qr = czero<C>();
-          for (int i = lane; i < N; i += 32) qr = cadd(qr, W.v[i]);
-          qr = csum(qr);
-          if (lane == 0) {
+          for (int i = ln.sl; i < N; i += L) qr = cadd(qr, W.v[i]);
+          qr = csum(qr, ln);
+          if (ln.sl == 0) {
             S.n_acc_refresh = 0;
             if (ro.ok) {
               S.logdet = ro.logdet; S.logL = ro.logL;
@@ -1014,12 +1044,12 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
               S.refresh_fail++;
             }
           }
-          __syncwarp();
+          __syncwarp(ln.gm);
         }
       }
 
-      // ---- bookkeeping of the decided step (lane 0)
-      if (lane == 0) {
+      // ---- bookkeeping of the decided step (the group's first lane)
+      if (ln.sl == 0) {
         S.prop[jump]++;
         if (t0f & 1) { S.prop_t0++; if (t0f & 2) S.acc_t0++; }
         if (apply) S.acc[jump]++;
@@ -1028,7 +1058,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         if (step >= burn_in) {
           const long long Nn = N, kq = k0;
           S.sN += Nn; S.sN2 += Nn * Nn; S.sK += kq; S.sK2 += kq * kq;
-          W.hist[N] += 1;
+          atomicAdd(hist + N, 1);  // no value returned: the lane does not wait on it
         }
         if (trace) {
           fsmp_trace tr;
@@ -1038,14 +1068,14 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           trace[step] = tr;
         }
       }
-      __syncwarp();
+      __syncwarp(ln.gm);
     }
 
     // ------------------------------------------------------------- chain end
     if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
       // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      const RefreshOut ro = pe_refresh<T, BIG>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, lane);
-      if (lane == 0) {
+      const RefreshOut ro = pe_refresh<T, BIG, L>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, ln);
+      if (ln.sl == 0) {
         if (ro.ok) {
           S.logdet = ro.logdet; S.logL = ro.logL;
           S.drift_max = fmax(S.drift_max, ro.drift);
@@ -1056,8 +1086,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
       }
     }
-    const double lam_hat = warp_lambda_mle(W.hist, n_cap, lambda0, lane);
-    if (lane == 0) {
+    const double lam_hat = group_lambda_mle<L>(hist, n_cap, lambda0, ln.sl, ln.gm);
+    if (ln.sl == 0) {
       close_hold(S, n_steps, burn_in);
       fsmp_summary o;
       o.lambda_hat = lam_hat;
@@ -1075,7 +1105,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       o.status = S.status; o.n_samples = ns; o.n_refresh = S.n_refresh; o.reserved = 0;
       *out = o;
     }
-    __syncwarp();
+    __syncwarp(ln.gm);
   }
 }
 
@@ -1090,10 +1120,16 @@ __global__ void split_ff_kernel(const double* a, float* out, size_t n) {
 
 }  // namespace
 
-size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int Ns) {
+size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int Ns) {
+  const int chains = warps * (32 / lanes);
+  const bool l16 = lanes == 16;
   if (M.precision == FSMP_FP64)
-    return pe_block_bytes<double>(M.Lt, M.n_cap) + (size_t)warps * pe_warp_bytes<double>(M.n_cap, n_alloc, M.win_extra, Ns);
-  return pe_block_bytes<float>(M.Lt, M.n_cap) + (size_t)warps * pe_warp_bytes<float>(M.n_cap, n_alloc, M.win_extra, Ns);
+    return pe_block_bytes<double>(M.Lt, M.n_cap) +
+           (size_t)chains * (l16 ? pe_chain_bytes<double, 16>(M.n_cap, n_alloc, M.win_extra, Ns)
+                                 : pe_chain_bytes<double, 32>(M.n_cap, n_alloc, M.win_extra, Ns));
+  return pe_block_bytes<float>(M.Lt, M.n_cap) +
+         (size_t)chains * (l16 ? pe_chain_bytes<float, 16>(M.n_cap, n_alloc, M.win_extra, Ns)
+                               : pe_chain_bytes<float, 32>(M.n_cap, n_alloc, M.win_extra, Ns));
 }
 
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc) { return pe_ws_doubles(n_cap, n_alloc); }
@@ -1111,49 +1147,60 @@ cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t 
 // registers otherwise.
 bool pe_big(int n_cap) { return n_cap > 192; }
 
-cudaError_t pe_kernel_attributes(int precision, int max_smem) {
-  cudaError_t e;
+// Lanes per chain the kernel is built for: 32, and 16 where chains are small (not BIG).
+bool pe_lanes_ok(int lanes, int n_cap) { return lanes == 32 || (lanes == 16 && !pe_big(n_cap)); }
+
+namespace {
+// The kernel instance for (precision, BIG, lanes); f receives its address.
+template <typename F> cudaError_t with_pe_kernel(int precision, bool big, int lanes, F f) {
   if (precision == FSMP_FP64) {
-    e = cudaFuncSetAttribute(pe_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(pe_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    return e;
+    if (big) return f(pe_kernel<double, true, 32>);
+    return lanes == 16 ? f(pe_kernel<double, false, 16>) : f(pe_kernel<double, false, 32>);
   }
-  e = cudaFuncSetAttribute(pe_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pe_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  return e;
+  if (big) return f(pe_kernel<float, true, 32>);
+  return lanes == 16 ? f(pe_kernel<float, false, 16>) : f(pe_kernel<float, false, 32>);
+}
+}  // namespace
+
+cudaError_t pe_kernel_attributes(int precision, int max_smem) {
+  for (int big = 0; big < 2; ++big)
+    for (int lanes : {32, 16}) {
+      if (big && lanes == 16) continue;
+      const cudaError_t e = with_pe_kernel(precision, big != 0, lanes, [&](auto k) {
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+      });
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
-int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big) {
+int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int lanes) {
   int n = 0;
-  cudaError_t e;
-  if (precision == FSMP_FP64)
-    e = big ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<double, true>, threads, smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<double, false>, threads, smem);
-  else
-    e = big ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<float, true>, threads, smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pe_kernel<float, false>, threads, smem);
+  const cudaError_t e = with_pe_kernel(precision, big, lanes, [&](auto k) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
+  });
   return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int ctas, int Ns, size_t smem, void* cinv,
-                      size_t c_stride, double* ws, size_t ws_stride, int* counter, cudaStream_t st) {
+cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
+                      void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
+                      cudaStream_t st) {
   PeSlots G;
   G.C = cinv;
   G.c_stride = c_stride;
   G.ws = ws;
   G.ws_stride = ws_stride;
+  G.hist = hist;
   G.counter = counter;
   G.Ns = Ns;
+  if (hist == nullptr || !pe_lanes_ok(lanes, M.n_cap)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const bool big = pe_big(M.n_cap);
-  if (M.precision == FSMP_FP64) {
-    if (big) pe_kernel<double, true><<<ctas, warps * 32, smem, st>>>(M, B, G);
-    else pe_kernel<double, false><<<ctas, warps * 32, smem, st>>>(M, B, G);
-  } else {
-    if (big) pe_kernel<float, true><<<ctas, warps * 32, smem, st>>>(M, B, G);
-    else pe_kernel<float, false><<<ctas, warps * 32, smem, st>>>(M, B, G);
-  }
+  e = with_pe_kernel(M.precision, pe_big(M.n_cap), lanes, [&](auto k) {
+    k<<<ctas, warps * 32, smem, st>>>(M, B, G);
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

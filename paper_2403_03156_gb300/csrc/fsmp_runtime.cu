@@ -96,17 +96,19 @@ struct fsmp_ctx {
   int gscratch_ctas = 0;
   LaunchShape shape_smem{256, 0, 0}, shape_gmem{256, 0, 0};
   // PE-space kernel: SER cross-correlation tables and one scratch set per launch stream (the
-  // serving streams, then one for fsmp_run_device), each with slots for every resident warp
+  // serving streams, then one for fsmp_run_device), each with slots for every resident chain
   double* tc64 = nullptr;
   float* tc32 = nullptr;
   float* tcff = nullptr;
   struct PeSet {
     void* cinv = nullptr;    // C^-1 slots
     double* ws = nullptr;    // FP64 refresh workspace slots
+    int* hist = nullptr;     // N histogram slots
     int* counter = nullptr;  // chain counter of the launch
   };
   std::vector<PeSet> pe_sets;
-  int pe_slots = 0, pe_warps = 4, pe_tile = 0;
+  int pe_slots = 0, pe_warps = 4, pe_tile = 0, pe_lanes = 32;
+  bool pe_lanes_free = false;  // pe_lanes left to fsmp_autotune
   size_t pe_c_stride = 0, pe_ws_stride = 0, pe_bytes = 0;
   std::atomic<long long> n_launches{0};  // chain-kernel launches
   std::mutex tune_mu;                    // serialises fsmp_autotune calls
@@ -182,6 +184,8 @@ int validate_params(const fsmp_params* p) {
   if (p->kernel < 0 || p->kernel > 4) return FSMP_ERR_INVALID;
   if (p->pe_tile < 0 || p->pe_tile > 128) return FSMP_ERR_INVALID;
   if (p->pe_ctas_per_sm < 0 || p->pe_ctas_per_sm > 64) return FSMP_ERR_INVALID;
+  if (p->pe_lanes != 0 && p->pe_lanes != 16 && p->pe_lanes != 32) return FSMP_ERR_INVALID;
+  if (p->kernel == FSMP_KERNEL_PE && p->pe_lanes == 16 && !pe_lanes_ok(16, p->n_cap)) return FSMP_ERR_INVALID;
   if (p->threads_per_chain != 0 && (p->threads_per_chain < 32 || p->threads_per_chain > 512 ||
                                     p->threads_per_chain % 32))
     return FSMP_ERR_INVALID;
@@ -195,7 +199,7 @@ void free_ctx(fsmp_ctx* c) {
   cudaFree(c->scan); cudaFree(c->Lt_dev); cudaFree(c->gscratch);
   cudaFree(c->phi32); cudaFree(c->logphi32); cudaFree(c->cphi32); cudaFree(c->rscratch);
   cudaFree(c->tc64); cudaFree(c->tc32); cudaFree(c->tcff);
-  for (auto& ps : c->pe_sets) { cudaFree(ps.cinv); cudaFree(ps.ws); cudaFree(ps.counter); }
+  for (auto& ps : c->pe_sets) { cudaFree(ps.cinv); cudaFree(ps.ws); cudaFree(ps.hist); cudaFree(ps.counter); }
   for (auto s : c->streams) cudaStreamDestroy(s);
   if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
   delete c;
@@ -212,12 +216,13 @@ void CUDART_CB pack_done_cb(void* arg) {
 }
 
 // ---- device batch from arrays already on the device
-// Launch shape of the PE-space kernel for windows up to n_alloc: warps (chains) per CTA, the
-// shared tile of C^-1, and resident CTAs per SM from the hardware's occupancy rule.
+// Launch shape of the PE-space kernel for windows up to n_alloc: warps per CTA, lanes per chain,
+// the shared tile of C^-1, and resident CTAs per SM from the hardware's occupancy rule.
+int pe_chains_per_cta(const fsmp_ctx* c) { return c->pe_warps * (32 / c->pe_lanes); }
 int pe_shape(fsmp_ctx* c, int n_alloc, int* ctas, size_t* smem) {
-  *smem = pe_smem_bytes(c->M, n_alloc, c->pe_warps, c->pe_tile);
+  *smem = pe_smem_bytes(c->M, n_alloc, c->pe_warps, c->pe_lanes, c->pe_tile);
   if (*smem > (size_t)c->prop.sharedMemPerBlockOptin) return FSMP_ERR_INVALID;
-  int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem, pe_big(c->p.n_cap));
+  int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem, pe_big(c->p.n_cap), c->pe_lanes);
   if (per_sm < 1) return FSMP_ERR_INVALID;
   if (c->p.pe_ctas_per_sm > 0) per_sm = std::min(per_sm, c->p.pe_ctas_per_sm);
   *ctas = per_sm * c->prop.multiProcessorCount;
@@ -230,11 +235,12 @@ int run_pe(fsmp_ctx* c, BatchView B, int set, cudaStream_t st) {
   int ctas = 0;
   size_t smem = 0;
   if (pe_shape(c, B.n_max, &ctas, &smem) != FSMP_OK) FAIL(FSMP_ERR_INVALID, "window too long for the PE-space kernel");
-  ctas = std::min(ctas, c->pe_slots / c->pe_warps);
-  ctas = std::min(ctas, (B.n_waveforms + c->pe_warps - 1) / c->pe_warps);
+  const int cpc = pe_chains_per_cta(c);
+  ctas = std::min(ctas, c->pe_slots / cpc);
+  ctas = std::min(ctas, (B.n_waveforms + cpc - 1) / cpc);
   const fsmp_ctx::PeSet& ps = c->pe_sets[set];
-  cudaError_t e = launch_pe(c->M, B, c->pe_warps, ctas, c->pe_tile, smem, ps.cinv, c->pe_c_stride, ps.ws,
-                            c->pe_ws_stride, ps.counter, st);
+  cudaError_t e = launch_pe(c->M, B, c->pe_warps, c->pe_lanes, ctas, c->pe_tile, smem, ps.cinv, c->pe_c_stride,
+                            ps.ws, c->pe_ws_stride, ps.hist, ps.counter, st);
   c->n_launches++;
   if (e != cudaSuccess) { set_error("launch_pe", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
   return FSMP_OK;
@@ -736,19 +742,28 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     if (cudaMalloc(&c->rscratch, c->rscratch_stride * (size_t)slots) != cudaSuccess)
       FAIL(FSMP_ERR_NOMEM, "refresh workspace allocation failed");
   }
-  // PE-space kernel: per-warp slots of C^-1 (when the shared tile can overflow) and of the FP64
-  // refresh workspace (FP32 mode), one set per launch stream
+  // PE-space kernel: per-chain slots of C^-1 (when the shared tile can overflow), of the FP64
+  // refresh workspace (FP32 mode) and of the N histogram, one set per launch stream; enough
+  // slots for every shape the context may launch (both lane counts when the tuner picks it)
   if (p.kernel == FSMP_KERNEL_PE) {
     c->pe_warps = p.threads_per_chain > 0 ? std::min(4, p.threads_per_chain / 32) : 4;
     const size_t esz = 8;  // C^-1 is FP64 in both modes
     c->pe_tile = p.pe_tile > 0 ? std::min(p.pe_tile, p.n_cap) : std::min(p.n_cap, 32);
+    c->pe_lanes = p.pe_lanes > 0 ? p.pe_lanes : 32;
+    c->pe_lanes_free = p.pe_lanes == 0 && pe_lanes_ok(16, p.n_cap);
     CK(pe_kernel_attributes(p.precision, max_smem));
     int slots = 0;
-    for (int nn : {std::min(64, p.n_max), p.n_max}) {
-      int ctas = 0;
-      size_t sm = 0;
-      if (pe_shape(c.get(), nn, &ctas, &sm) == FSMP_OK) slots = std::max(slots, ctas * c->pe_warps);
+    const int lanes0 = c->pe_lanes;
+    for (int lanes : {32, 16}) {
+      if (lanes != lanes0 && !c->pe_lanes_free) continue;
+      c->pe_lanes = lanes;
+      for (int nn : {std::min(64, p.n_max), p.n_max}) {
+        int ctas = 0;
+        size_t sm = 0;
+        if (pe_shape(c.get(), nn, &ctas, &sm) == FSMP_OK) slots = std::max(slots, ctas * pe_chains_per_cta(c.get()));
+      }
     }
+    c->pe_lanes = lanes0;
     if (slots < 1) FAIL(FSMP_ERR_INVALID, "n_max too large for the PE-space kernel");
     c->pe_slots = slots;
     c->pe_c_stride = c->pe_tile < p.n_cap ? pe_c_entries(p.n_cap) : 0;
@@ -756,10 +771,12 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     for (int i = 0; i <= p.n_streams; ++i) {
       fsmp_ctx::PeSet ps;
       const size_t cb = c->pe_c_stride * esz * (size_t)slots, wb = c->pe_ws_stride * 8 * (size_t)slots;
+      const size_t hb = pe_hist_ints(p.n_cap) * sizeof(int) * (size_t)slots;
       if (cb && cudaMalloc(&ps.cinv, cb) != cudaSuccess) FAIL(FSMP_ERR_NOMEM, "PE-space C^-1 slots");
       if (wb && cudaMalloc((void**)&ps.ws, wb) != cudaSuccess) FAIL(FSMP_ERR_NOMEM, "PE-space refresh workspace");
+      if (cudaMalloc((void**)&ps.hist, hb) != cudaSuccess) FAIL(FSMP_ERR_NOMEM, "PE-space N histograms");
       CK(cudaMalloc((void**)&ps.counter, sizeof(int)));
-      c->pe_bytes += cb + wb + sizeof(int);
+      c->pe_bytes += cb + wb + hb + sizeof(int);
       c->pe_sets.push_back(ps);
     }
   }
@@ -915,9 +932,9 @@ int fsmp_autotune(fsmp_ctx* c, const fsmp_device_batch* b, int sample, int trial
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const int set = (int)c->streams.size();
-  const int tile0 = c->pe_tile, warps0 = c->pe_warps, ctas0 = c->p.pe_ctas_per_sm;
-  auto trial = [&](int tile, int warps, int ctas, double* rate) -> int {
-    c->pe_tile = tile; c->pe_warps = warps; c->p.pe_ctas_per_sm = ctas;
+  const int tile0 = c->pe_tile, warps0 = c->pe_warps, ctas0 = c->p.pe_ctas_per_sm, lanes0 = c->pe_lanes;
+  auto trial = [&](int lanes, int tile, int warps, int ctas, double* rate) -> int {
+    c->pe_lanes = lanes; c->pe_tile = tile; c->pe_warps = warps; c->p.pe_ctas_per_sm = ctas;
     int cc = 0;
     size_t sm = 0;
     if (pe_shape(c, B.n_max, &cc, &sm) != FSMP_OK) { *rate = -1.0; return FSMP_OK; }
@@ -943,26 +960,36 @@ int fsmp_autotune(fsmp_ctx* c, const fsmp_device_batch* b, int sample, int trial
   std::sort(tiles.begin(), tiles.end());
   tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
   double r0 = 0.0, best = -1.0;
-  int bt = tile0, bw = warps0, bc = ctas0, n_tried = 0;
-  int rc = trial(tile0, warps0, ctas0, &r0);
+  int bl = lanes0, bt = tile0, bw = warps0, bc = ctas0, n_tried = 0;
+  int rc = trial(lanes0, tile0, warps0, ctas0, &r0);
   if (rc == FSMP_OK) {
     best = r0; ++n_tried;
-    // coordinate search: tile, then chains per CTA, then resident CTAs per SM
+    // coordinate search: lanes per chain (when the context leaves it free), tile, warps per
+    // CTA, then resident CTAs per SM
+    if (c->pe_lanes_free) {
+      for (int l : {32, 16}) {
+        double r;
+        if (l == lanes0) continue;
+        if ((rc = trial(l, bt, bw, bc, &r)) != FSMP_OK) break;
+        ++n_tried;
+        if (r > best) { best = r; bl = l; }
+      }
+    }
     for (int t : tiles) {
       double r;
-      if ((rc = trial(t, bw, bc, &r)) != FSMP_OK) break;
+      if (rc != FSMP_OK || (rc = trial(bl, t, bw, bc, &r)) != FSMP_OK) break;
       ++n_tried;
       if (r > best) { best = r; bt = t; }
     }
     for (int w : {1, 2, 4}) {
       double r;
-      if (rc != FSMP_OK || (rc = trial(bt, w, bc, &r)) != FSMP_OK) break;
+      if (rc != FSMP_OK || (rc = trial(bl, bt, w, bc, &r)) != FSMP_OK) break;
       ++n_tried;
       if (r > best) { best = r; bw = w; }
     }
     for (int k : {1, 2, 3}) {
       double r;
-      if (rc != FSMP_OK || (rc = trial(bt, bw, k, &r)) != FSMP_OK) break;
+      if (rc != FSMP_OK || (rc = trial(bl, bt, bw, k, &r)) != FSMP_OK) break;
       ++n_tried;
       if (r > best) { best = r; bc = k; }
     }
@@ -971,12 +998,13 @@ int fsmp_autotune(fsmp_ctx* c, const fsmp_device_batch* b, int sample, int trial
   cudaEventDestroy(e1);
   cudaFree(scratch);
   if (rc != FSMP_OK) {
-    c->pe_tile = tile0; c->pe_warps = warps0; c->p.pe_ctas_per_sm = ctas0;
+    c->pe_lanes = lanes0; c->pe_tile = tile0; c->pe_warps = warps0; c->p.pe_ctas_per_sm = ctas0;
     return rc;
   }
-  c->pe_tile = bt; c->pe_warps = bw; c->p.pe_ctas_per_sm = bc;
+  c->pe_lanes = bl; c->pe_tile = bt; c->pe_warps = bw; c->p.pe_ctas_per_sm = bc;
   if (out) {
-    out->pe_tile = bt; out->chains_per_cta = bw; out->ctas_per_sm = bc; out->n_tried = n_tried;
+    out->pe_tile = bt; out->chains_per_cta = bw * (32 / bl); out->ctas_per_sm = bc; out->n_tried = n_tried;
+    out->lanes_per_chain = bl;
     out->best_steps_per_s = best; out->default_steps_per_s = r0;
   }
   return FSMP_OK;
@@ -1009,11 +1037,11 @@ int fsmp_get_info(fsmp_ctx* c, fsmp_info* o) {
   o->R = c->M.R;
   o->L_V = c->M.L_V;
   o->n_smem_max = c->n_smem_max;
-  if (c->p.kernel == FSMP_KERNEL_PE) {  // a warp per chain, pe_warps chains per CTA
+  if (c->p.kernel == FSMP_KERNEL_PE) {  // pe_lanes lanes per chain, pe_warps warps per CTA
     int ctas = 0;
     size_t sm = 0;
     if (pe_shape(c, c->p.n_max, &ctas, &sm) == FSMP_OK) {
-      o->threads_per_chain = 32;
+      o->threads_per_chain = c->pe_lanes;
       o->ctas_per_sm = ctas / c->prop.multiProcessorCount;
     }
   } else {

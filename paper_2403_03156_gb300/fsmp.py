@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
                 ("refresh_every", _c_int), ("drift_tol", _c_double), ("kernel", _c_int),
                 ("threads_per_chain", _c_int), ("device_mem_budget", ctypes.c_size_t),
                 ("device", _c_int), ("max_queued", _c_int), ("n_streams", _c_int),
-                ("pe_tile", _c_int), ("pe_ctas_per_sm", _c_int)]
+                ("pe_tile", _c_int), ("pe_ctas_per_sm", _c_int), ("pe_lanes", _c_int)]
 
 
 class Batch(ctypes.Structure):
@@ -71,7 +71,8 @@ class DeviceBatch(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("pe_tile", _c_int), ("chains_per_cta", _c_int), ("ctas_per_sm", _c_int), ("n_tried", _c_int),
-                ("best_steps_per_s", _c_double), ("default_steps_per_s", _c_double)]
+                ("best_steps_per_s", _c_double), ("default_steps_per_s", _c_double),
+                ("lanes_per_chain", _c_int)]
 
 
 class Info(ctypes.Structure):
@@ -153,7 +154,7 @@ _PARAM_DEFAULTS = dict(dt_sample_ns=1.0, grid_ns=0.25, ser_kind=0, ser_sigma=1.5
                        jump_J=0.25, n_cap=32, n_max=1024, precision=FP64, refresh_every=64,
                        drift_tol=0.0, kernel=KERNEL_AUTO, threads_per_chain=0,
                        device_mem_budget=0, device=0, max_queued=0, n_streams=0, pe_tile=0,
-                       pe_ctas_per_sm=0)
+                       pe_ctas_per_sm=0, pe_lanes=0)
 
 
 def make_params(d: dict | None = None, **kw) -> Params:

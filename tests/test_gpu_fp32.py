@@ -43,7 +43,8 @@ def _params(wl, **kw):
     return dict(wl["params"], n_max=max(64, n_max), precision=fsmp.FP32_REFRESH, **kw)
 
 
-KERNELS = [pytest.param(fsmp.KERNEL_SMEM, id="sigma"), pytest.param(fsmp.KERNEL_PE, id="pe")]
+KERNELS = [pytest.param((fsmp.KERNEL_SMEM, 32), id="sigma"), pytest.param((fsmp.KERNEL_PE, 32), id="pe"),
+           pytest.param((fsmp.KERNEL_PE, 16), id="pe16")]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -54,7 +55,7 @@ def test_fp32_tracks_oracle_step_by_step(lib, orc, refresh_every, kernel):
     incremental FP32 drift between refreshes stays small."""
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=96, n_steps=600, seed=3)
     b = wl["batch"]
-    with fsmp.Context(_params(wl, refresh_every=refresh_every, kernel=kernel)) as ctx:
+    with fsmp.Context(_params(wl, refresh_every=refresh_every, kernel=kernel[0], pe_lanes=kernel[1])) as ctx:
         s_gpu, t_gpu = ctx.run(b, record_trace=True)
     s_orc, t_orc = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16, trace=True)
     pref = _lockstep_prefix(t_gpu, t_orc)
@@ -90,7 +91,7 @@ def test_fp32_summaries_match_oracle_statistically(lib, orc, kernel):
     errors (and each summary's differences are centred)."""
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=384, n_steps=2000, seed=11, burn_in=400)
     b = wl["batch"]
-    with fsmp.Context(_params(wl, refresh_every=64, kernel=kernel)) as ctx:
+    with fsmp.Context(_params(wl, refresh_every=64, kernel=kernel[0], pe_lanes=kernel[1])) as ctx:
         s_gpu, _ = ctx.run(b)
     s_orc, _ = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16)
     for f in ("mean_N", "mean_Q", "mean_t0", "lambda_hat"):

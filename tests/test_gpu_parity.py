@@ -53,13 +53,16 @@ def _oracle_trace(orc, params, batch, threads=16):
     return s, t
 
 
-@pytest.mark.parametrize("kernel", [fsmp.KERNEL_SMEM, fsmp.KERNEL_GLOBAL, fsmp.KERNEL_PE])
-def test_lockstep_fp64_config1(lib, orc, kernel):
+@pytest.mark.parametrize("kernel,lanes", [pytest.param(fsmp.KERNEL_SMEM, 32, id="sigma-smem"),
+                                          pytest.param(fsmp.KERNEL_GLOBAL, 32, id="sigma-global"),
+                                          pytest.param(fsmp.KERNEL_PE, 32, id="pe"),
+                                          pytest.param(fsmp.KERNEL_PE, 16, id="pe16")])
+def test_lockstep_fp64_config1(lib, orc, kernel, lanes):
     """Config 1 (256 x 128 samples, lambda 2, 1000 steps): every log acceptance ratio to 1e-9
-    relative, identical decisions and summaries."""
+    relative, identical decisions and summaries (PE kernel: a warp or a half warp per chain)."""
     wl = workloads.make_workload("plain_fp64_256x128")
     b = wl["batch"]
-    with fsmp.Context(C1, n_max=128, precision=fsmp.FP64, kernel=kernel) as ctx:
+    with fsmp.Context(C1, n_max=128, precision=fsmp.FP64, kernel=kernel, pe_lanes=lanes) as ctx:
         s_gpu, t_gpu = ctx.run(b, record_trace=True)
     s_orc, t_orc = _oracle_trace(orc, C1, b)
     gpu_util.compare_traces(t_gpu, t_orc)
