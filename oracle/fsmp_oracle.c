@@ -39,6 +39,14 @@
  *      overwrites slot k; the PE removed or moved is slot floor(u4 * N).
  *   R8 Charge summary: E[Q | z, w] = N mu_q + sigma_q^2 u^T Sigma^-1 y with u = sum_k a_k,
  *      the Gaussian posterior mean of the marginalised charges of Eq. (mgauss).
+ *   R9 MCP model (n_mix > 1): a PE is (t_k, e_k). U and Sigma carry mu_{e_k} and
+ *      sigma_{e_k}^2 per PE, Lambda = diag(-sigma_{e-}^2, sigma_{e+}^2) and
+ *      lambda = (-mu_{e-}, mu_{e+}) (Appendix A.2). e+ ~ G (Sec. 2.4) is drawn for every
+ *      birth and update from a ninth uniform u8 (Philox counter (step, 2, 0, 0), first
+ *      output): the smallest e with G(0) + ... + G(e) > u8. The acceptances are Eq. (mcp)
+ *      with the prior of Eq. (mcp-pzmu); an update with zero time shift and e+ = e- is the
+ *      accepted no-op of R5, with e+ != e- it is a move. The charge summary of R8 becomes
+ *      sum_k (mu_{e_k} + sigma_{e_k}^2 a_k^T Sigma^-1 y).
  */
 #include "fsmp_oracle.h"
 
@@ -92,6 +100,14 @@ void orc_step_uniforms(uint64_t seed, uint64_t wf_index, uint64_t step, double u
   orc_philox4x64_10(c0, key, o0);
   orc_philox4x64_10(c1, key, o1);
   for (int i = 0; i < 4; ++i) { u[i] = orc_u01(o0[i]); u[4 + i] = orc_u01(o1[i]); }
+}
+
+double orc_step_uniform_e(uint64_t seed, uint64_t wf_index, uint64_t step) {
+  uint64_t key[2] = {seed, wf_index};
+  uint64_t c2[4] = {step, 2, 0, 0};
+  uint64_t o2[4];
+  orc_philox4x64_10(c2, key, o2);
+  return orc_u01(o2[0]);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -256,6 +272,32 @@ typedef struct {
   const double* V; /* peak-normalised SER table, Lt entries */
 } model;
 
+/* Charge model of a PE of component e (reading R9): N(mix_mu[e], mix_sigma[e]^2) of
+ * Eq. (mcp-multi-norm), or the dynode N(mu_q, sigma_q^2) when n_mix = 0. */
+static void charge_comp(const orc_params* p, int e, double* mu, double* s2) {
+  if (p->n_mix > 0) {
+    *mu = p->mix_mu[e];
+    *s2 = p->mix_sigma[e] * p->mix_sigma[e];
+  } else {
+    *mu = p->mu_q;
+    *s2 = p->sigma_q * p->sigma_q;
+  }
+}
+
+/* e+ ~ G (Sec. 2.4): the smallest e whose cumulative probability exceeds u, else (rounding)
+ * the last component with G > 0. 0 for the dynode model. */
+static int draw_comp(const orc_params* p, double u) {
+  if (p->n_mix <= 1) return 0;
+  double cum = 0.0;
+  int last = 0;
+  for (int e = 0; e < p->n_mix; ++e) {
+    if (p->mix_G[e] > 0.0) last = e;
+    cum += p->mix_G[e];
+    if (cum > u) return e;
+  }
+  return last;
+}
+
 /* a[w] = V(w*dt - t_j) on the grid (reading R1): V[w*R - j] inside the table, else 0. */
 static void pe_vector(const model* M, int n, int j, double* a) {
   for (int w = 0; w < n; ++w) {
@@ -265,10 +307,10 @@ static void pe_vector(const model* M, int n, int j, double* a) {
 }
 
 /* log p(w|z) = -n/2 log 2pi - 1/2 log|Sigma| - 1/2 (w-U)^T Sigma^-1 (w-U), with
- * U_w = mu_q sum_k V(t_w - t_k) and Sigma = sigma_q^2 sum_k a_k a_k^T + sigma_eps^2 I
- * (Appendix A.1). Optionally returns Sigma^-1 (w - U) in sinv_y. Returns NaN if Sigma is
- * not positive definite. */
-static double logp_def(const model* M, const float* wv, int n, const int32_t* j, int N,
+ * U_w = sum_k mu_{e_k} V(t_w - t_k) and Sigma = sum_k sigma_{e_k}^2 a_k a_k^T + sigma_eps^2 I
+ * (Appendix A.1; per-PE components of Appendix A.2, e == NULL: all 0). Optionally returns
+ * Sigma^-1 (w - U) in sinv_y. Returns NaN if Sigma is not positive definite. */
+static double logp_def(const model* M, const float* wv, int n, const int32_t* j, const int32_t* e, int N,
                        double* logdet_out, double* quad_out, double* sinv_y) {
   const orc_params* p = M->p;
   double* S = (double*)calloc((size_t)n * n, sizeof(double));
@@ -279,10 +321,12 @@ static double logp_def(const model* M, const float* wv, int n, const int32_t* j,
   double out = NAN;
   if (!S || !U || !a || !r || !x) goto done;
   for (int k = 0; k < N; ++k) {
+    double mu, s2;
+    charge_comp(p, e ? e[k] : 0, &mu, &s2);
     pe_vector(M, n, j[k], a);
     for (int w = 0; w < n; ++w) {
-      U[w] += p->mu_q * a[w];
-      for (int v = 0; v < n; ++v) S[w * n + v] += p->sigma_q * p->sigma_q * a[w] * a[v];
+      U[w] += mu * a[w];
+      for (int v = 0; v < n; ++v) S[w * n + v] += s2 * a[w] * a[v];
     }
   }
   for (int w = 0; w < n; ++w) S[w * n + w] += p->sigma_noise * p->sigma_noise;
@@ -314,6 +358,7 @@ typedef struct {
   double *am, *ap, *cm, *cp;
   double B[2][2];
   double lam[2];
+  double Linv[2];
 } inc_state;
 
 static int inc_init(inc_state* st, const orc_params* p, const float* wv, int n) {
@@ -341,9 +386,10 @@ static void inc_free(inc_state* st) {
 /* Delta nu of the jump with single-PE vectors a_- = am, a_+ = ap (either may be all zero,
  * Eq. (11)): c = Sigma^-1 a, B = (Lambda^-1 + a^T c)^-1, Upsilon = c^T y + Lambda^-1 lambda,
  * Delta nu = 1/2 (Upsilon^T B Upsilon - lambda^T Lambda^-1 lambda + log|B Lambda^-1|)
- * (Eqs. (12), (16)-(18)), Lambda = sigma_q^2 diag(-1, 1), lambda = mu_q (-1, 1)^T
- * (Eq. (DeltaU)). Returns 0, or -1 if |B Lambda^-1| is not positive. */
-static int inc_delta_nu(inc_state* st, const orc_params* p, double* dnu) {
+ * (Eqs. (12), (16)-(18)), Lambda = diag(-sigma_{e-}^2, sigma_{e+}^2), lambda =
+ * (-mu_{e-}, mu_{e+})^T (Eq. (DeltaU); Appendix A.2 for the components em, ep; the dynode
+ * model has sigma_q, mu_q for both). Returns 0, or -1 if |B Lambda^-1| is not positive. */
+static int inc_delta_nu(inc_state* st, const orc_params* p, int em, int ep, double* dnu) {
   int n = st->n;
   /* c = Sigma^-1 a; terms with a[v] == 0 contribute nothing and are skipped */
   for (int x = 0; x < n; ++x) { st->cm[x] = 0.0; st->cp[x] = 0.0; }
@@ -353,10 +399,14 @@ static int inc_delta_nu(inc_state* st, const orc_params* p, double* dnu) {
     if (st->ap[v] != 0.0)
       for (int x = 0; x < n; ++x) st->cp[x] += st->Sinv[x * n + v] * st->ap[v];
   }
-  double sq2 = p->sigma_q * p->sigma_q;
-  double Linv[2] = {-1.0 / sq2, 1.0 / sq2}; /* Lambda^-1 (diagonal) */
-  st->lam[0] = -p->mu_q;
-  st->lam[1] = p->mu_q;
+  double mu_m, s2_m, mu_p, s2_p;
+  charge_comp(p, em, &mu_m, &s2_m);
+  charge_comp(p, ep, &mu_p, &s2_p);
+  st->Linv[0] = -1.0 / s2_m; /* Lambda^-1 (diagonal) */
+  st->Linv[1] = 1.0 / s2_p;
+  const double* Linv = st->Linv;
+  st->lam[0] = -mu_m;
+  st->lam[1] = mu_p;
   /* a^T c = a^T Sigma^-1 a is symmetric because Sigma^-1 is: its off-diagonal is computed
    * once (a_-^T c_+) and used for both entries, so B below is exactly symmetric. */
   double atc[2][2] = {{0, 0}, {0, 0}};
@@ -403,9 +453,9 @@ static void inc_accept(inc_state* st, const orc_params* p) {
     }
   }
   for (int x = 0; x < n; ++x) st->y[x] -= st->am[x] * st->lam[0] + st->ap[x] * st->lam[1];
-  double sq2 = p->sigma_q * p->sigma_q;
+  (void)p;
   double detB = st->B[0][0] * st->B[1][1] - st->B[0][1] * st->B[1][0];
-  double detBL = detB * (-1.0 / sq2) * (1.0 / sq2);
+  double detBL = detB * st->Linv[0] * st->Linv[1];
   st->logdet += -log(detBL);
 }
 
@@ -424,6 +474,7 @@ typedef struct {
   const uint8_t* forced;
   double* occ;
   int occ_width;
+  double* occ_e;
 } chain_in;
 
 typedef struct {
@@ -453,9 +504,12 @@ static double tab_Phi_T(const chain_in* c, chain_tabs* t, int k0) {
   return *slot;
 }
 
+/* log G(e) of the MCP model (reading R9); 0 for the dynode model. */
+static double log_G(const orc_params* p, int e) { return p->n_mix > 1 ? log(p->mix_G[e]) : 0.0; }
+
 static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int32_t* list_out,
                      int32_t* N_out, int32_t* k0_out, double* sinv_out, double* y_out,
-                     double* logdet_out) {
+                     double* logdet_out, int32_t* e_out) {
   const orc_params* p = c->p;
   const model* M = c->M;
   const int n = c->n;
@@ -472,13 +526,18 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
   tb.logphi = (double*)malloc(sizeof(double) * (nd > 0 ? nd : 1));
   tb.Phi_T = (double*)malloc(sizeof(double) * (c->k0_hi - c->k0_lo + 1));
   int32_t* list = (int32_t*)calloc((size_t)p->n_cap + 1, sizeof(int32_t));
+  int32_t* list_e = (int32_t*)calloc((size_t)p->n_cap + 1, sizeof(int32_t)); /* components */
+  int32_t* zprop_e = (int32_t*)calloc((size_t)p->n_cap + 1, sizeof(int32_t));
   double* av = (double*)malloc(sizeof(double) * n);
   double* uvec = (double*)malloc(sizeof(double) * n);
   double* svec = (double*)malloc(sizeof(double) * n);
   int32_t* zprop = (int32_t*)malloc(sizeof(int32_t) * (p->n_cap + 1));
   inc_state st;
   memset(&st, 0, sizeof(st));
-  if (!tb.phi || !tb.logphi || !tb.Phi_T || !list || !av || !uvec || !svec || !zprop) { rc = ORC_ERR_NOMEM; goto done; }
+  if (!tb.phi || !tb.logphi || !tb.Phi_T || !list || !list_e || !zprop_e || !av || !uvec || !svec || !zprop) {
+    rc = ORC_ERR_NOMEM;
+    goto done;
+  }
   for (int d = tb.d_min; d <= tb.d_max; ++d) {
     double ph = orc_phi(p, d * g);
     tb.phi[d - tb.d_min] = ph;
@@ -494,7 +553,7 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
   /* initial state (reading of Sec. 2.3 without the deconvolution): z empty */
   double logp_cur = 0.0;
   if (c->mode == ORC_MODE_DEFINITION && !p->prior_only)
-    logp_cur = logp_def(M, c->w, n, list, 0, NULL, NULL, NULL);
+    logp_cur = logp_def(M, c->w, n, list, list_e, 0, NULL, NULL, NULL);
 
   double sN = 0, sN2 = 0, st0 = 0, st02 = 0, sQ = 0, sQ2 = 0;
   double* hist = (double*)calloc((size_t)p->n_cap + 1, sizeof(double));
@@ -509,6 +568,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     tr.la0 = NAN; tr.lu0 = NAN; tr.la = NAN; tr.lu = NAN; tr.dnu = NAN;
     tr.flags = 0;
     uint8_t forced = c->forced ? c->forced[step] : 0;
+    /* component of a born or updated PE, e+ ~ G (reading R9) */
+    const int ep = p->n_mix > 1 ? draw_comp(p, orc_step_uniform_e(c->seed, c->wf_index, (uint64_t)step)) : 0;
 
     /* ---- Gibbs part 1: MH on t0 given z (Sec. 2.4, reading R2) ---- */
     if (p->sample_t0) {
@@ -574,7 +635,9 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
         }
         if (jp < 0) jp = jlast;
         memcpy(zprop, list, sizeof(int32_t) * N);
+        memcpy(zprop_e, list_e, sizeof(int32_t) * N);
         zprop[N] = jp;
+        zprop_e[N] = ep;
         Nprop = N + 1;
         valid = 1;
       }
@@ -583,21 +646,25 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       if (k >= N) k = N - 1;
       if (jump == ORC_JUMP_DEATH) {
         memcpy(zprop, list, sizeof(int32_t) * N);
+        memcpy(zprop_e, list_e, sizeof(int32_t) * N);
         zprop[k] = list[N - 1];
+        zprop_e[k] = list_e[N - 1];
         Nprop = N - 1;
         valid = 1;
       } else {
         double z2 = sqrt(-2.0 * log(u[5])) * cos(ORC_TWO_PI * u[6]);
         long D = (long)rint(z2 * inv_g);
         jp = list[k] + (int)D;
-        if (D == 0) {
-          noop = 1; /* reading R5: an accepted no-op */
+        if (D == 0 && ep == list_e[k]) {
+          noop = 1; /* readings R5, R9: an accepted no-op */
           la = 0.0;
         } else if (jp < c->T_lo || jp >= c->T_hi || tab_logphi(&tb, jp - k0) == -INFINITY) {
           la = -INFINITY;
         } else {
           memcpy(zprop, list, sizeof(int32_t) * N);
+          memcpy(zprop_e, list_e, sizeof(int32_t) * N);
           zprop[k] = jp;
+          zprop_e[k] = ep;
           Nprop = N;
           valid = 1;
         }
@@ -610,24 +677,33 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       if (p->prior_only) {
         dnu = 0.0;
       } else if (c->mode == ORC_MODE_DEFINITION) {
-        logp_new = logp_def(M, c->w, n, zprop, Nprop, NULL, NULL, NULL);
+        logp_new = logp_def(M, c->w, n, zprop, zprop_e, Nprop, NULL, NULL, NULL);
         dnu = logp_new - logp_cur; /* Eq. (delta-nu) */
         if (!isfinite(dnu)) { ok = 0; out->status |= ORC_ST_NONFINITE; }
       } else {
         if (jump == ORC_JUMP_BIRTH) { for (int w = 0; w < n; ++w) st.am[w] = 0.0; pe_vector(M, n, jp, st.ap); }
         else if (jump == ORC_JUMP_DEATH) { pe_vector(M, n, list[k], st.am); for (int w = 0; w < n; ++w) st.ap[w] = 0.0; }
         else { pe_vector(M, n, list[k], st.am); pe_vector(M, n, jp, st.ap); }
-        if (inc_delta_nu(&st, p, &dnu) != 0) { ok = 0; out->status |= ORC_ST_BADDET; }
+        /* components of a_- and a_+; the absent one of a birth or death does not enter */
+        const int e_minus = jump == ORC_JUMP_BIRTH ? ep : list_e[k];
+        const int e_plus = jump == ORC_JUMP_DEATH ? e_minus : ep;
+        if (inc_delta_nu(&st, p, e_minus, e_plus, &dnu) != 0) { ok = 0; out->status |= ORC_ST_BADDET; }
         else if (!isfinite(dnu)) { ok = 0; out->status |= ORC_ST_NONFINITE; }
       }
       if (ok) {
         double Phi = tab_Phi_T(c, &tb, k0);
+        /* Eq. (mcp): the prior of Eq. (mcp-pzmu) carries G(e) per PE and the proposal draws
+         * e+ ~ G, so a birth gains G(e+) / G(e+), a death G(e-) / G(e-) and an update
+         * G(e+) G(e-) / (G(e-) G(e+)); the terms are kept as the paper writes them */
         if (jump == ORC_JUMP_BIRTH)
-          la = dnu + log(c->lambda0) + log(Phi) - log((double)(N + 1)) + (N == 0 ? logJ : 0.0);
+          la = dnu + log(c->lambda0) + log(Phi) - log((double)(N + 1)) + (N == 0 ? logJ : 0.0) + log_G(p, ep) -
+               log_G(p, ep);
         else if (jump == ORC_JUMP_DEATH)
-          la = dnu - log(c->lambda0) - log(Phi) + log((double)N) - (N == 1 ? logJ : 0.0);
+          la = dnu - log(c->lambda0) - log(Phi) + log((double)N) - (N == 1 ? logJ : 0.0) - log_G(p, list_e[k]) +
+               log_G(p, list_e[k]);
         else
-          la = dnu + tab_logphi(&tb, jp - k0) - tab_logphi(&tb, list[k] - k0);
+          la = dnu + tab_logphi(&tb, jp - k0) - tab_logphi(&tb, list[k] - k0) + log_G(p, ep) - log_G(p, list_e[k]) +
+               log_G(p, list_e[k]) - log_G(p, ep);
       } else {
         la = -INFINITY;
       }
@@ -648,9 +724,9 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
         out->acc[jump]++;
         if (c->mode == ORC_MODE_INCREMENTAL && !p->prior_only) inc_accept(&st, p);
         if (c->mode == ORC_MODE_DEFINITION) logp_cur = logp_new;
-        if (jump == ORC_JUMP_BIRTH) { list[N] = jp; N++; }
-        else if (jump == ORC_JUMP_DEATH) { list[k] = list[N - 1]; N--; }
-        else list[k] = jp;
+        if (jump == ORC_JUMP_BIRTH) { list[N] = jp; list_e[N] = ep; N++; }
+        else if (jump == ORC_JUMP_DEATH) { list[k] = list[N - 1]; list_e[k] = list_e[N - 1]; N--; }
+        else { list[k] = jp; list_e[k] = ep; }
         q_valid = 0;
       }
     }
@@ -662,7 +738,12 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     if (step >= c->burn_in) {
       if (!q_valid) {
         if (p->prior_only) {
-          q_cur = N * p->mu_q;
+          q_cur = 0.0;
+          for (int kk = 0; kk < N; ++kk) {
+            double mu, s2;
+            charge_comp(p, list_e[kk], &mu, &s2);
+            q_cur += mu;
+          }
         } else {
           if (c->mode == ORC_MODE_INCREMENTAL) {
             for (int x = 0; x < n; ++x) {
@@ -671,16 +752,18 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
               svec[x] = s;
             }
           } else {
-            logp_def(M, c->w, n, list, N, NULL, NULL, svec);
+            logp_def(M, c->w, n, list, list_e, N, NULL, NULL, svec);
           }
-          for (int x = 0; x < n; ++x) uvec[x] = 0.0;
+          /* sum_k (mu_{e_k} + sigma_{e_k}^2 a_k^T Sigma^-1 y) (readings R8, R9) */
+          q_cur = 0.0;
           for (int kk = 0; kk < N; ++kk) {
+            double mu, s2;
+            charge_comp(p, list_e[kk], &mu, &s2);
             pe_vector(M, n, list[kk], av);
-            for (int x = 0; x < n; ++x) uvec[x] += av[x];
+            double as = 0.0;
+            for (int x = 0; x < n; ++x) as += av[x] * svec[x];
+            q_cur += mu + s2 * as;
           }
-          double us = 0.0;
-          for (int x = 0; x < n; ++x) us += uvec[x] * svec[x];
-          q_cur = N * p->mu_q + p->sigma_q * p->sigma_q * us;
         }
         q_valid = 1;
       }
@@ -694,6 +777,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
           int col = list[kk] - c->T_lo;
           if (col >= 0 && col < c->occ_width) c->occ[col] += 1.0;
         }
+      if (c->occ_e)
+        for (int kk = 0; kk < N; ++kk) c->occ_e[list_e[kk]] += 1.0;
     }
   }
 
@@ -710,6 +795,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     out->lambda_hat = ns > 0 ? orc_lambda_mle(hist, p->n_cap, c->lambda0) : NAN;
     if (c->occ && ns > 0)
       for (int col = 0; col < c->occ_width; ++col) c->occ[col] *= inv;
+    if (c->occ_e && ns > 0)
+      for (int e = 0; e < (p->n_mix > 1 ? p->n_mix : 1); ++e) c->occ_e[e] *= inv;
     if (p->prior_only) {
       out->logL = NAN; out->logdet = NAN;
     } else if (c->mode == ORC_MODE_INCREMENTAL) {
@@ -723,10 +810,11 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       out->logL = -0.5 * n * ORC_LOG_2PI - 0.5 * st.logdet - 0.5 * quad;
     } else {
       double ld = 0.0;
-      out->logL = logp_def(M, c->w, n, list, N, &ld, NULL, NULL);
+      out->logL = logp_def(M, c->w, n, list, list_e, N, &ld, NULL, NULL);
       out->logdet = ld;
     }
     if (list_out) memcpy(list_out, list, sizeof(int32_t) * N);
+    if (e_out) memcpy(e_out, list_e, sizeof(int32_t) * N);
     if (N_out) *N_out = N;
     if (k0_out) *k0_out = k0;
     if (c->mode == ORC_MODE_INCREMENTAL && !p->prior_only) {
@@ -737,7 +825,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     free(hist);
   }
 done:
-  free(tb.phi); free(tb.logphi); free(tb.Phi_T); free(list); free(av); free(uvec); free(svec); free(zprop);
+  free(tb.phi); free(tb.logphi); free(tb.Phi_T); free(list); free(list_e); free(zprop_e);
+  free(av); free(uvec); free(svec); free(zprop);
   if (st.Sinv) inc_free(&st);
   return rc;
 }
@@ -750,6 +839,15 @@ static int check_params(const orc_params* p) {
   if (!(p->sigma_noise > 0) || !(p->sigma_q > 0) || !(p->jump_J > 0) || !(p->jump_J <= 0.5)) return ORC_ERR_INVALID;
   if (p->n_cap < 1 || !(p->phi_support_ns > 0)) return ORC_ERR_INVALID;
   if (!(p->t0_hi >= p->t0_lo)) return ORC_ERR_INVALID;
+  if (p->n_mix < 0 || p->n_mix > ORC_MAX_MIX) return ORC_ERR_INVALID;
+  if (p->n_mix > 0) {
+    double sum = 0.0;
+    for (int e = 0; e < p->n_mix; ++e) {
+      if (!(p->mix_G[e] >= 0.0) || !(p->mix_sigma[e] > 0.0) || !isfinite(p->mix_mu[e])) return ORC_ERR_INVALID;
+      sum += p->mix_G[e];
+    }
+    if (!(fabs(sum - 1.0) <= 1e-9)) return ORC_ERR_INVALID; /* G is a distribution (Appendix A.2) */
+  }
   return 0;
 }
 
@@ -788,6 +886,7 @@ static int make_chain_in(const orc_params* p, const model* M, const orc_batch* b
   c->forced = b->forced ? b->forced + (size_t)i * b->n_steps : NULL;
   c->occ = b->occ ? b->occ + (size_t)i * b->occ_width : NULL;
   c->occ_width = b->occ_width;
+  c->occ_e = b->occ_e ? b->occ_e + (size_t)i * (p->n_mix > 1 ? p->n_mix : 1) : NULL;
   return 0;
 }
 
@@ -809,7 +908,7 @@ static void* worker(void* arg) {
     int rc = make_chain_in(a->p, a->M, a->b, i, a->mode, &c);
     if (rc == 0)
       rc = run_chain(&c, &a->out[i], a->trace ? a->trace + (size_t)i * a->b->n_steps : NULL,
-                     NULL, NULL, NULL, NULL, NULL, NULL);
+                     NULL, NULL, NULL, NULL, NULL, NULL, NULL);
     if (rc != 0) a->rc = rc;
   }
   return NULL;
@@ -922,66 +1021,85 @@ int orc_run_batch(const orc_params* p, const orc_batch* b, int mode, int n_threa
 
 int orc_run_chain_state(const orc_params* p, const orc_batch* b, int mode,
                         orc_summary* out, orc_trace* trace, int32_t* list_out, int32_t* N_out,
-                        int32_t* k0_out, double* sinv_out, double* y_out, double* logdet_out) {
+                        int32_t* k0_out, double* sinv_out, double* y_out, double* logdet_out,
+                        int32_t* e_out) {
   model M;
   double* V = NULL;
   int rc = build_model(p, &M, &V);
   if (rc) return rc;
   chain_in c;
   rc = make_chain_in(p, &M, b, 0, mode, &c);
-  if (rc == 0) rc = run_chain(&c, out, trace, list_out, N_out, k0_out, sinv_out, y_out, logdet_out);
+  if (rc == 0) rc = run_chain(&c, out, trace, list_out, N_out, k0_out, sinv_out, y_out, logdet_out, e_out);
   free(V);
   return rc;
 }
 
-double orc_logp_definition(const orc_params* p, const float* w, int n, const int32_t* j, int N,
-                           double* logdet_out, double* quad_out) {
+double orc_logp_definition_e(const orc_params* p, const float* w, int n, const int32_t* j, const int32_t* e,
+                             int N, double* logdet_out, double* quad_out) {
   model M;
   double* V = NULL;
   if (build_model(p, &M, &V) != 0) return NAN;
-  double r = logp_def(&M, w, n, j, N, logdet_out, quad_out, NULL);
+  double r = logp_def(&M, w, n, j, e, N, logdet_out, quad_out, NULL);
   free(V);
   return r;
 }
 
-int orc_delta_nu(const orc_params* p, const float* w, int n, const int32_t* j, int N,
-                 int kind, int k, int jp, int mode, double* dnu_out) {
+double orc_logp_definition(const orc_params* p, const float* w, int n, const int32_t* j, int N,
+                           double* logdet_out, double* quad_out) {
+  return orc_logp_definition_e(p, w, n, j, NULL, N, logdet_out, quad_out);
+}
+
+int orc_delta_nu_e(const orc_params* p, const float* w, int n, const int32_t* j, const int32_t* e, int N,
+                   int kind, int k, int jp, int ep, int mode, double* dnu_out) {
   model M;
   double* V = NULL;
   int rc = build_model(p, &M, &V);
   if (rc) return rc;
   if ((kind != 0 && (k < 0 || k >= N)) || N < 0) { free(V); return ORC_ERR_INVALID; }
+  int32_t* e0 = (int32_t*)calloc((size_t)N + 1, sizeof(int32_t));
+  if (!e0) { free(V); return ORC_ERR_NOMEM; }
+  if (e) memcpy(e0, e, sizeof(int32_t) * N);
   if (mode == ORC_MODE_DEFINITION) {
     int32_t* z2 = (int32_t*)malloc(sizeof(int32_t) * (N + 1));
+    int32_t* e2 = (int32_t*)malloc(sizeof(int32_t) * (N + 1));
     memcpy(z2, j, sizeof(int32_t) * N);
+    memcpy(e2, e0, sizeof(int32_t) * N);
     int N2 = N;
-    if (kind == 0) { z2[N] = jp; N2 = N + 1; }
-    else if (kind == 1) { z2[k] = j[N - 1]; N2 = N - 1; }
-    else z2[k] = jp;
-    double l0 = logp_def(&M, w, n, j, N, NULL, NULL, NULL);
-    double l1 = logp_def(&M, w, n, z2, N2, NULL, NULL, NULL);
+    if (kind == 0) { z2[N] = jp; e2[N] = ep; N2 = N + 1; }
+    else if (kind == 1) { z2[k] = j[N - 1]; e2[k] = e0[N - 1]; N2 = N - 1; }
+    else { z2[k] = jp; e2[k] = ep; }
+    double l0 = logp_def(&M, w, n, j, e0, N, NULL, NULL, NULL);
+    double l1 = logp_def(&M, w, n, z2, e2, N2, NULL, NULL, NULL);
     free(z2);
+    free(e2);
     *dnu_out = l1 - l0;
   } else {
     inc_state st;
     memset(&st, 0, sizeof(st));
-    if (inc_init(&st, p, w, n) != 0) { inc_free(&st); free(V); return ORC_ERR_NOMEM; }
+    if (inc_init(&st, p, w, n) != 0) { inc_free(&st); free(e0); free(V); return ORC_ERR_NOMEM; }
     double d;
     /* Sigma^-1(z) built from the empty state by successive births (Eq. (12), a_- = 0) */
     for (int i = 0; i < N; ++i) {
       for (int x = 0; x < n; ++x) st.am[x] = 0.0;
       pe_vector(&M, n, j[i], st.ap);
-      if (inc_delta_nu(&st, p, &d) != 0) { inc_free(&st); free(V); return ORC_ERR_INVALID; }
+      if (inc_delta_nu(&st, p, e0[i], e0[i], &d) != 0) { inc_free(&st); free(e0); free(V); return ORC_ERR_INVALID; }
       inc_accept(&st, p);
     }
+    int em = ep, epp = ep;
     if (kind == 0) { for (int x = 0; x < n; ++x) st.am[x] = 0.0; pe_vector(&M, n, jp, st.ap); }
-    else if (kind == 1) { pe_vector(&M, n, j[k], st.am); for (int x = 0; x < n; ++x) st.ap[x] = 0.0; }
-    else { pe_vector(&M, n, j[k], st.am); pe_vector(&M, n, jp, st.ap); }
-    rc = inc_delta_nu(&st, p, &d);
+    else if (kind == 1) { pe_vector(&M, n, j[k], st.am); for (int x = 0; x < n; ++x) st.ap[x] = 0.0; em = epp = e0[k]; }
+    else { pe_vector(&M, n, j[k], st.am); pe_vector(&M, n, jp, st.ap); em = e0[k]; }
+    rc = inc_delta_nu(&st, p, em, epp, &d);
     inc_free(&st);
-    if (rc) { free(V); return ORC_ERR_INVALID; }
+    if (rc) { free(e0); free(V); return ORC_ERR_INVALID; }
     *dnu_out = d;
   }
+  free(e0);
   free(V);
   return 0;
+}
+
+int orc_delta_nu(const orc_params* p, const float* w, int n, const int32_t* j, int N,
+                 int kind, int k, int jp, int mode, double* dnu_out) {
+  return orc_delta_nu_e(p, w, n, j, NULL, N, kind, k, jp, 0, mode, dnu_out);
 }

@@ -18,6 +18,8 @@
  *   SER and phi               Sec. 3 (SER formula; LS two-exponential phi)
  *   marginal likelihood       Appendix A.1, Eq. (mgauss) and the log-density below it
  *   rank-2 jump, Woodbury     Appendix A.1, Eqs. (11), (12), (14), (DeltaU), (16)-(18)
+ *   MCP charge model          Eq. (mcp-multi-norm) (Sec. 2.1), Eq. (mcp) (Sec. 2.4),
+ *                             Eq. (mcp-pzmu) and the redefined U, Sigma, Lambda (Appendix A.2)
  *
  * Readings where the paper is silent (grid, t0 prior, tie rules, RNG layout) are the
  * ones listed in the repository's design notes; each is restated where it is used.
@@ -32,6 +34,8 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+#define ORC_MAX_MIX 8
 
 typedef struct {
   double dt_sample_ns;     /* sample period (1 ns in the paper, Sec. 2.3 / Sec. 3)          */
@@ -50,6 +54,11 @@ typedef struct {
   double jump_J;           /* J of Sec. 2.4 (1/4)                                            */
   int    n_cap;            /* PE capacity: a birth at N == n_cap is rejected                  */
   int    prior_only;       /* test switch: Delta nu := 0 (samples the prior restricted to T) */
+  /* MCP charge model (Eq. (mcp-multi-norm)): n_mix Gaussian components, PE of component e has
+   * charge N(mix_mu[e], mix_sigma[e]^2) with probability mix_G[e]; n_mix = 0 is the dynode
+   * model N(mu_q, sigma_q^2) above */
+  int    n_mix;
+  double mix_G[ORC_MAX_MIX], mix_mu[ORC_MAX_MIX], mix_sigma[ORC_MAX_MIX];
 } orc_params;
 
 /* One record per chain step. la0 / la are log acceptance ratios (-inf = forced reject,
@@ -91,6 +100,8 @@ typedef struct {
   double* occ;             /* optional [n_waveforms * occ_width]: time-averaged PE count at grid
                               index T_lo + c (c < occ_width) after burn-in (a PE-time histogram) */
   int occ_width;
+  double* occ_e;           /* optional [n_waveforms * max(n_mix, 1)]: time-averaged number of PEs
+                              of each MCP component after burn-in */
 } orc_batch;
 
 /* Philox4x64-10 block function. */
@@ -99,6 +110,9 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 void orc_philox_blocks(const uint64_t key[2], const uint64_t* ctrs, int n, uint64_t* out);
 /* The 8 uniforms of one chain step (two Philox blocks), in (0,1). */
 void orc_step_uniforms(uint64_t seed, uint64_t wf_index, uint64_t step, double u[8]);
+/* The uniform that draws the MCP component of a born or updated PE (n_mix > 1): the first
+ * output of a third block, counter (step, 2, 0, 0). */
+double orc_step_uniform_e(uint64_t seed, uint64_t wf_index, uint64_t step);
 
 /* SER V_PE(t) (Sec. 3 formula, not normalised) and phi(t). */
 double orc_ser_raw(const orc_params* p, double t_ns);
@@ -110,23 +124,31 @@ int orc_ser_table(const orc_params* p, double* out, int max_len, double* peak_ou
 /* log p(w | z) by building Sigma(z), U(z) and a Cholesky factorisation (Appendix A.1). */
 double orc_logp_definition(const orc_params* p, const float* w, int n, const int32_t* j, int N,
                            double* logdet_out, double* quad_out);
+/* The same for z = {(t_k, e_k)} of the MCP model (Appendix A.2); e may be NULL (all 0). */
+double orc_logp_definition_e(const orc_params* p, const float* w, int n, const int32_t* j, const int32_t* e,
+                             int N, double* logdet_out, double* quad_out);
 
 /* Delta nu of one proposal from state z (j[0..N)), with either a Cholesky of both
  * states (mode 0) or eqs. (11)-(18) applied to Sigma^-1(z) built by successive births
  * (mode 1). kind: 0 birth of jp, 1 death of slot k, 2 update slot k -> jp. */
 int orc_delta_nu(const orc_params* p, const float* w, int n, const int32_t* j, int N,
                  int kind, int k, int jp, int mode, double* dnu_out);
+/* The same with PE components e[0..N) (NULL: all 0) and the component ep of the new PE. */
+int orc_delta_nu_e(const orc_params* p, const float* w, int n, const int32_t* j, const int32_t* e, int N,
+                   int kind, int k, int jp, int ep, int mode, double* dnu_out);
 
 /* Run the chains of a batch; n_threads <= 0 uses one thread. trace: [n_waveforms*n_steps]
  * or NULL. Returns 0 or a negative error. */
 int orc_run_batch(const orc_params* p, const orc_batch* b, int mode, int n_threads,
                   orc_summary* out, orc_trace* trace);
 
-/* Run one chain (waveform 0 of b) and export its final state: PE list (n_cap entries),
- * N, k0, Sigma^-1 (n*n, incremental mode only), y (n), log|Sigma|. */
+/* Run one chain (waveform 0 of b) and export its final state: PE list (n_cap entries) and
+ * their components (n_cap entries, may be NULL), N, k0, Sigma^-1 (n*n, incremental mode
+ * only), y (n), log|Sigma|. */
 int orc_run_chain_state(const orc_params* p, const orc_batch* b, int mode,
                         orc_summary* out, orc_trace* trace, int32_t* list_out, int32_t* N_out,
-                        int32_t* k0_out, double* sinv_out, double* y_out, double* logdet_out);
+                        int32_t* k0_out, double* sinv_out, double* y_out, double* logdet_out,
+                        int32_t* e_out);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ MODE_INCREMENTAL = 1
 
 F_T0_PROPOSED, F_T0_ACCEPTED, F_ACCEPTED, F_NOOP, F_T0_DISAGREE, F_DISAGREE = 1, 2, 4, 8, 16, 32
 ST_CAPACITY, ST_BADDET, ST_NONFINITE, ST_DISAGREE = 1, 2, 16, 32
+MAX_MIX = 8
 
 TRACE_DTYPE = np.dtype([("la0", "<f8"), ("lu0", "<f8"), ("la", "<f8"), ("lu", "<f8"),
                         ("dnu", "<f8"), ("N", "<i4"), ("k0", "<i4"), ("jump", "<i4"),
@@ -51,7 +52,9 @@ class OrcParams(ctypes.Structure):
                 ("sigma_q", ctypes.c_double), ("sigma_noise", ctypes.c_double),
                 ("t0_lo", ctypes.c_double), ("t0_hi", ctypes.c_double),
                 ("sample_t0", ctypes.c_int), ("jump_J", ctypes.c_double),
-                ("n_cap", ctypes.c_int), ("prior_only", ctypes.c_int)]
+                ("n_cap", ctypes.c_int), ("prior_only", ctypes.c_int),
+                ("n_mix", ctypes.c_int), ("mix_G", ctypes.c_double * MAX_MIX),
+                ("mix_mu", ctypes.c_double * MAX_MIX), ("mix_sigma", ctypes.c_double * MAX_MIX)]
 
 
 class OrcBatch(ctypes.Structure):
@@ -62,7 +65,7 @@ class OrcBatch(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("index_base", ctypes.c_uint64),
                 ("wf_ids", ctypes.c_void_p), ("n_steps", ctypes.c_int), ("burn_in", ctypes.c_int),
                 ("forced", ctypes.c_void_p), ("occ", ctypes.c_void_p),
-                ("occ_width", ctypes.c_int)]
+                ("occ_width", ctypes.c_int), ("occ_e", ctypes.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -87,6 +90,8 @@ def lib():
                                         ctypes.c_int, ctypes.c_void_p]
         L.orc_step_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_double)]
+        L.orc_step_uniform_e.restype = ctypes.c_double
+        L.orc_step_uniform_e.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         L.orc_ser_raw.restype = ctypes.c_double
         L.orc_ser_raw.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_double]
         L.orc_phi.restype = ctypes.c_double
@@ -99,6 +104,16 @@ def lib():
                                           ctypes.c_void_p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
+        L.orc_logp_definition_e.restype = ctypes.c_double
+        L.orc_logp_definition_e.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
+        L.orc_delta_nu_e.restype = ctypes.c_int
+        L.orc_delta_nu_e.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]
         L.orc_delta_nu.restype = ctypes.c_int
         L.orc_delta_nu.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_int,
                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -112,7 +127,8 @@ def lib():
         L.orc_run_chain_state.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcBatch),
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -121,19 +137,31 @@ _PARAM_DEFAULTS = dict(dt_sample_ns=1.0, grid_ns=0.25, ser_kind=0, ser_sigma=1.5
                        ser_under_frac=0.0, ser_under_sigma=1.0, ser_under_tau=16.0, ser_eps=1e-4,
                        phi_kind=0, phi_p1=1.5, phi_p2=20.0, phi_support_ns=4096.0, mu_q=1.0,
                        sigma_q=0.3, sigma_noise=0.06, t0_lo=30.0, t0_hi=40.0, sample_t0=1,
-                       jump_J=0.25, n_cap=32, prior_only=0)
+                       jump_J=0.25, n_cap=32, prior_only=0, n_mix=0)
+_MIX_KEYS = ("mix_G", "mix_mu", "mix_sigma")
 
 
 def make_params(d: dict | None = None, **kw) -> OrcParams:
-    """Oracle parameter struct from a dict of model parameters (extra keys are ignored)."""
+    """Oracle parameter struct from a dict of model parameters (extra keys are ignored).
+    The MCP mixture is given as lists ``mix_G``, ``mix_mu``, ``mix_sigma`` (n_mix = their
+    length unless given)."""
     vals = dict(_PARAM_DEFAULTS)
+    mix = {}
     for src in (d or {}, kw):
         for k, v in src.items():
             if k in vals:
                 vals[k] = v
+            elif k in _MIX_KEYS and v is not None:
+                mix[k] = [float(x) for x in v]
+    if mix and not vals["n_mix"]:
+        vals["n_mix"] = len(mix["mix_G"])
     p = OrcParams()
     for k, v in vals.items():
         setattr(p, k, v)
+    for k, v in mix.items():
+        arr = getattr(p, k)
+        for i, x in enumerate(v[:MAX_MIX]):
+            arr[i] = x
     return p
 
 
@@ -164,6 +192,11 @@ def step_uniforms(seed, wf_index, step):
     return np.array(list(u))
 
 
+def step_uniform_e(seed, wf_index, step):
+    """The ninth uniform of a step: it draws the MCP component of a new PE."""
+    return lib().orc_step_uniform_e(int(seed), int(wf_index), int(step))
+
+
 def ser_raw(params, t):
     p = make_params(params)
     return lib().orc_ser_raw(ctypes.byref(p), float(t))
@@ -186,13 +219,19 @@ def ser_table(params):
     return out, peak.value
 
 
-def logp_definition(params, w, j):
+def logp_definition(params, w, j, e=None):
+    """log p(w|z), log|Sigma|, quadratic form; e: the PEs' MCP components (None: all 0)."""
     p = make_params(params)
     w = np.ascontiguousarray(w, np.float32)
     j = np.ascontiguousarray(j, np.int32)
     ld, q = ctypes.c_double(), ctypes.c_double()
-    r = lib().orc_logp_definition(ctypes.byref(p), w.ctypes.data, len(w), j.ctypes.data, len(j),
-                                  ctypes.byref(ld), ctypes.byref(q))
+    if e is None:
+        r = lib().orc_logp_definition(ctypes.byref(p), w.ctypes.data, len(w), j.ctypes.data, len(j),
+                                      ctypes.byref(ld), ctypes.byref(q))
+    else:
+        e = np.ascontiguousarray(e, np.int32)
+        r = lib().orc_logp_definition_e(ctypes.byref(p), w.ctypes.data, len(w), j.ctypes.data,
+                                        e.ctypes.data, len(j), ctypes.byref(ld), ctypes.byref(q))
     return r, ld.value, q.value
 
 
@@ -202,16 +241,20 @@ def lambda_mle(hist, lambda0):
     return lib().orc_lambda_mle(h.ctypes.data, len(h) - 1, float(lambda0))
 
 
-def delta_nu(params, w, j, kind, k=0, jp=0, mode=MODE_INCREMENTAL):
-    """Delta nu of one proposal (kind 0 birth of jp, 1 death of slot k, 2 update k -> jp)."""
+def delta_nu(params, w, j, kind, k=0, jp=0, mode=MODE_INCREMENTAL, e=None, ep=0):
+    """Delta nu of one proposal (kind 0 birth of jp, 1 death of slot k, 2 update k -> jp);
+    e: the PEs' MCP components (None: all 0), ep: the component of the new PE."""
     p = make_params(params)
     w = np.ascontiguousarray(w, np.float32)
     N = len(j)
     jj = np.zeros(max(N, 1), np.int32)
     jj[:N] = np.asarray(j, np.int32)
+    ee = np.zeros(max(N, 1), np.int32)
+    if e is not None:
+        ee[:N] = np.asarray(e, np.int32)
     out = ctypes.c_double()
-    rc = lib().orc_delta_nu(ctypes.byref(p), w.ctypes.data, len(w), jj.ctypes.data, N,
-                            int(kind), int(k), int(jp), int(mode), ctypes.byref(out))
+    rc = lib().orc_delta_nu_e(ctypes.byref(p), w.ctypes.data, len(w), jj.ctypes.data, ee.ctypes.data, N,
+                              int(kind), int(k), int(jp), int(ep), int(mode), ctypes.byref(out))
     if rc != 0:
         raise ValueError("orc_delta_nu failed: %d" % rc)
     return out.value
@@ -254,13 +297,19 @@ class _BatchKeep:
             self.occ = np.zeros((b.n_waveforms, int(batch["occ_width"])), np.float64)
             b.occ = self.occ.ctypes.data
             b.occ_width = int(batch["occ_width"])
+        self.occ_e = None
+        if batch.get("occ_e"):
+            self.occ_e = np.zeros((b.n_waveforms, int(batch["occ_e"])), np.float64)
+            b.occ_e = self.occ_e.ctypes.data
         self.b = b
 
 
 def run_batch(params, batch, mode=MODE_INCREMENTAL, n_threads=1, trace=False):
     """Run every chain of ``batch`` (a dict of arrays, see ``orc_batch``).
 
-    Returns (summaries, trace) with ``trace`` of shape (n_waveforms, n_steps) or None.
+    Returns (summaries, trace) with ``trace`` of shape (n_waveforms, n_steps) or None, then
+    the PE-time histogram if ``batch["occ_width"]`` is set, then the per-component PE counts
+    if ``batch["occ_e"]`` (the number of components) is set.
     """
     p = make_params(params)
     keep = _BatchKeep(batch)
@@ -271,6 +320,8 @@ def run_batch(params, batch, mode=MODE_INCREMENTAL, n_threads=1, trace=False):
                              out.ctypes.data, None if tr is None else tr.ctypes.data)
     if rc != 0:
         raise ValueError("orc_run_batch failed: %d" % rc)
+    if keep.occ_e is not None:
+        return out, tr, keep.occ, keep.occ_e
     if keep.occ is not None:
         return out, tr, keep.occ
     return out, tr
@@ -284,6 +335,7 @@ def run_chain_state(params, batch, mode=MODE_INCREMENTAL):
     out = np.zeros(1, SUMMARY_DTYPE)
     tr = np.zeros(keep.b.n_steps, TRACE_DTYPE)
     lst = np.zeros(int(p.n_cap) + 1, np.int32)
+    lst_e = np.zeros(int(p.n_cap) + 1, np.int32)
     N = np.zeros(1, np.int32)
     k0 = np.zeros(1, np.int32)
     sinv = np.zeros((n, n), np.float64)
@@ -291,8 +343,9 @@ def run_chain_state(params, batch, mode=MODE_INCREMENTAL):
     ld = np.zeros(1, np.float64)
     rc = lib().orc_run_chain_state(ctypes.byref(p), ctypes.byref(keep.b), int(mode),
                                    out.ctypes.data, tr.ctypes.data, lst.ctypes.data, N.ctypes.data,
-                                   k0.ctypes.data, sinv.ctypes.data, y.ctypes.data, ld.ctypes.data)
+                                   k0.ctypes.data, sinv.ctypes.data, y.ctypes.data, ld.ctypes.data,
+                                   lst_e.ctypes.data)
     if rc != 0:
         raise ValueError("orc_run_chain_state failed: %d" % rc)
-    return dict(summary=out[0], trace=tr, z=lst[:N[0]].copy(), N=int(N[0]), k0=int(k0[0]),
-                sinv=sinv, y=y, logdet=float(ld[0]))
+    return dict(summary=out[0], trace=tr, z=lst[:N[0]].copy(), e=lst_e[:N[0]].copy(), N=int(N[0]),
+                k0=int(k0[0]), sinv=sinv, y=y, logdet=float(ld[0]))

@@ -1,7 +1,8 @@
 """Independent restatement of the FSMP model with library routines, used only to pin the
 CPU oracle: the SER and phi from scipy's ``exponnorm`` (the ex-Gaussian), the Gaussian
 marginal likelihood of Appendix A.1 from ``scipy.stats.multivariate_normal``, and the
-grid prior of a PE multiset written out term by term."""
+grid prior of a PE multiset written out term by term (with the MCP components of
+Eq. (mcp-pzmu) when the parameters carry a mixture)."""
 from __future__ import annotations
 
 import itertools
@@ -54,40 +55,60 @@ def pe_matrix(V, R, n, js):
     return np.where(ok, V[np.clip(m, 0, len(V) - 1)], 0.0)
 
 
-def loglik(params, V, R, w, js):
+def charge(params, e):
+    """(mu, sigma^2) of a PE of MCP component e (the dynode mu_q, sigma_q without a mixture)."""
+    if params.get("n_mix", 0) or params.get("mix_G"):
+        return params["mix_mu"][e], params["mix_sigma"][e] ** 2
+    return params["mu_q"], params["sigma_q"] ** 2
+
+
+def loglik(params, V, R, w, js, es=None):
     n = len(w)
     A = pe_matrix(V, R, n, js) if len(js) else np.zeros((0, n))
-    U = params["mu_q"] * A.sum(0)
-    S = params["sigma_q"] ** 2 * A.T @ A + params["sigma_noise"] ** 2 * np.eye(n)
+    es = np.zeros(len(js), int) if es is None else np.asarray(es)
+    mus = np.array([charge(params, int(e))[0] for e in es])
+    s2s = np.array([charge(params, int(e))[1] for e in es])
+    U = (mus[:, None] * A).sum(0) if len(js) else np.zeros(n)
+    S = A.T @ (s2s[:, None] * A) + params["sigma_noise"] ** 2 * np.eye(n)
     return stats.multivariate_normal.logpdf(np.asarray(w, np.float64), mean=U, cov=S), U, S
 
 
 def enumerate_posterior(params, w, T_lo, T_hi, k0_values, lambda0, n_cap, t_origin=0.0):
     """Exact posterior over (t0 on its grid, PE multiset on [T_lo, T_hi)) with at most n_cap
-    PEs: mass = p(t0) prod_j (lambda0 phi_j g)^m_j / m_j! p(w | multiset)."""
+    PEs: mass = p(t0) prod_j (lambda0 phi_j g)^m_j / m_j! p(w | multiset). With an MCP
+    mixture the multiset is over (grid point, component) pairs and each PE's factor carries
+    G(e) (Eq. (mcp-pzmu)); ``comp`` is then the expected number of PEs per component."""
     V, R = ser_table(params)
     g = params["grid_ns"]
     js = np.arange(T_lo, T_hi)
     nT = len(js)
-    logmass, Ns, occs, t0s = [], [], [], []
+    G = list(params["mix_G"]) if params.get("mix_G") else [1.0]
+    nE = len(G)
+    types = [(i, e) for i in range(nT) for e in range(nE)]
+    logmass, Ns, occs, comps, t0s = [], [], [], [], []
     for k in range(n_cap + 1):
-        for S in itertools.combinations_with_replacement(range(nT), k):
-            ll, _, _ = loglik(params, V, R, w, js[list(S)])
+        for S in itertools.combinations_with_replacement(range(len(types)), k):
+            pes = [types[x] for x in S]
+            ll, _, _ = loglik(params, V, R, w, js[[i for i, _ in pes]], [e for _, e in pes])
             cnt = Counter(S)
             occ = np.zeros(nT)
-            for i, m in cnt.items():
-                occ[i] = m
+            comp = np.zeros(nE)
+            for x, m in cnt.items():
+                occ[types[x][0]] += m
+                comp[types[x][1]] += m
             for k0 in k0_values:
                 ph = phi(params, (js - k0) * g)
                 lp = 0.0
-                for i, m in cnt.items():
-                    if ph[i] <= 0:
+                for x, m in cnt.items():
+                    i, e = types[x]
+                    if ph[i] <= 0 or G[e] <= 0:
                         lp = -np.inf
                         break
-                    lp += m * math.log(lambda0 * ph[i] * g) - math.lgamma(m + 1)
+                    lp += m * math.log(lambda0 * ph[i] * g * G[e]) - math.lgamma(m + 1)
                 logmass.append(ll + lp)
                 Ns.append(k)
                 occs.append(occ)
+                comps.append(comp)
                 t0s.append(t_origin + k0 * g)
     logmass = np.array(logmass)
     p = np.exp(logmass - logmass.max())
@@ -95,4 +116,4 @@ def enumerate_posterior(params, w, T_lo, T_hi, k0_values, lambda0, n_cap, t_orig
     Ns = np.array(Ns)
     return dict(pN=np.array([p[Ns == k].sum() for k in range(n_cap + 1)]),
                 occ=(p[:, None] * np.array(occs)).sum(0), t0=float((p * np.array(t0s)).sum()),
-                EN=float((p * Ns).sum()))
+                EN=float((p * Ns).sum()), comp=(p[:, None] * np.array(comps)).sum(0))
