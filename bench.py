@@ -398,7 +398,7 @@ def run_ours(args):
     kdom = int(np.argmax(mean_dur))
     alg_bytes = float(summ[kdom]["alg_bytes"].sum())
     achieved = alg_bytes / (mean_dur[kdom] * 1e-3) / 1e9
-    kernel_src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_pe.cu" if pe else "fsmp_chain.cu")
+    kernel_src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_pe_kernel.cuh" if pe else "fsmp_chain.cu")
     tr = load_traffic(kernel_src, "pe_kernel" if pe else "chain_kernel")
     allsum = np.concatenate(summ)
     acc = allsum["acc"].sum(0)

@@ -70,6 +70,8 @@ extern "C" {
 
 typedef struct fsmp_ctx fsmp_ctx;
 
+#define FSMP_MAX_MIX 8          /* components of the MCP charge mixture                      */
+
 /* Model and engine parameters, copied at fsmp_create. Model terms follow the paper:
  *  - SER (Sec. 3): ser_kind 0 is the ex-Gaussian shifted by 4 sigma,
  *    V(t) = (1/2tau) exp((s^2 - 2(t-4s)tau)/2tau^2) erfc((s^2 - (t-4s)tau)/(sqrt2 s tau)),
@@ -82,6 +84,11 @@ typedef struct fsmp_ctx fsmp_ctx;
  *    (tau1 = phi_p1, tau2 = phi_p2). phi := 0 for |t| > phi_support_ns.
  *  - charges N(mu_q, sigma_q^2) marginalised (Sec. 2.1, Appendix A.1); white noise
  *    sigma_noise (Sec. 1).
+ *  - MCP charge model (Eq. (mcp-multi-norm), Sec. 2.1; Eq. (mcp), Sec. 2.4; Appendix A.2):
+ *    n_mix > 0 Gaussian components, a PE of component e has charge N(mix_mu[e],
+ *    mix_sigma[e]^2) with prior probability mix_G[e] (the G(e) must sum to 1); a PE is then
+ *    (t, e), e+ ~ G is drawn for every birth and update, and mu_q, sigma_q are unused.
+ *    n_mix = 0 is the dynode model. Only FSMP_KERNEL_PE (and AUTO) runs a mixture.
  *  - t0 prior uniform on [t0_lo, t0_hi] (Eq. (t0prior)); sample_t0 = 0 holds t0 fixed.
  *  - jump probabilities J, J, 1 - 2J (Sec. 2.4); n_cap = PE capacity per chain. */
 typedef struct {
@@ -114,6 +121,8 @@ typedef struct {
                               warp; n_cap <= 192 only); 0: 32 until fsmp_autotune picks one.
                               The lane count sets the order of the chain's sums, so results
                               for another count agree up to rounding, not bit for bit       */
+  int n_mix;               /* MCP charge mixture: number of components (0: dynode model)     */
+  double mix_G[FSMP_MAX_MIX], mix_mu[FSMP_MAX_MIX], mix_sigma[FSMP_MAX_MIX];
 } fsmp_params;
 
 /* One waveform's posterior summaries (after burn_in steps). t0 is in absolute ns.
@@ -277,9 +286,9 @@ int fsmp_autotune(fsmp_ctx* ctx, const fsmp_device_batch* batch, int sample, int
  * all device scratch it needs (the model tables and the per-CTA FP64 refresh workspaces of
  * the FP32 chain kernel) in one static 64 MiB device array that every GPU loading this code
  * holds until the process exits. The caller passes inputs and outputs as in fsmp_run_device.
- *  - Only precision FSMP_FP32_REFRESH, windows of at most 256 samples, n_cap <= 64,
- *    phi_support_ns / grid_ns <= 32768 and SER scans of at most 16384 grid points; larger
- *    sizes return FSMP_ERR_INVALID (see fsmp_last_error()).
+ *  - Only precision FSMP_FP32_REFRESH, the dynode charge model (n_mix = 0), windows of at
+ *    most 256 samples, n_cap <= 64, phi_support_ns / grid_ns <= 32768 and SER scans of at
+ *    most 16384 grid points; anything else returns FSMP_ERR_INVALID (see fsmp_last_error()).
  *  - The first call on a device sets up that device (it resolves the array's address and the
  *    kernel's shared-memory limit), and the first call with a new set of model parameters
  *    rebuilds the tables and synchronises `stream` once: make such a call before any stream

@@ -25,6 +25,14 @@ struct DevModel {
   double mu_q, sigma_q, sq2, se2, inv_se2;
   double log_se2, log_r;       // log sigma_eps^2 and log(sigma_eps^2 / sigma_q^2)
   float mu_hi, mu_lo, r_hi, r_lo;  // mu_q and sigma_eps^2 / sigma_q^2 as float pairs (hi + lo)
+  // Charge components of the PE-space kernel: one (mu_q, sigma_q) for the dynode model, else
+  // the MCP mixture (Eq. (mcp-multi-norm)). For component e: mean cm_mu, variance cm_q,
+  // its inverse cm_iq, cm_r = sigma_eps^2 / cm_q and its log, cumulative probability
+  // G(0) + .. + G(e), and the float pairs of cm_mu and cm_r.
+  int n_comp, cm_last;        // components; the last one with G > 0
+  double cm_mu[FSMP_MAX_MIX], cm_q[FSMP_MAX_MIX], cm_iq[FSMP_MAX_MIX], cm_r[FSMP_MAX_MIX], cm_lr[FSMP_MAX_MIX];
+  double cm_cum[FSMP_MAX_MIX];
+  float cm_mu_hi[FSMP_MAX_MIX], cm_mu_lo[FSMP_MAX_MIX], cm_r_hi[FSMP_MAX_MIX], cm_r_lo[FSMP_MAX_MIX];
   double t0_lo, t0_hi;
   int sample_t0;
   double J, log_J;
@@ -104,26 +112,54 @@ FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x
 #ifdef __CUDACC__
 // lambda_FSMP of a chain (Eq. (reduce-mu0)): the maximiser of
 //   l(lambda) = -lambda + log sum_N h[N] (lambda / lambda0)^N
-// over its N-sample counts h[0 .. n_max], by Newton steps on
-//   l'(lambda) = -1 + E_w[N] / lambda,  l''(lambda) = (Var_w[N] - E_w[N]) / lambda^2,
-// w_N ∝ h[N] (lambda / lambda0)^N, from the sample mean (fixed-point steps lambda <- E_w[N]
-// where l'' >= 0); the boundary lambda = 0 when l(0) is not smaller. A group of L consecutive
-// lanes (mask gm, sl the lane within it) calls it and every lane gets the result; NAN if h is
-// empty.
+// over its N-sample counts h[0 .. n_max]. l can have several local maxima (a chain that visits
+// clusters of N far apart), all inside (0, top] with top the largest N sampled, since a
+// stationary point satisfies lambda = E_w[N] with w_N ∝ h[N] (lambda / lambda0)^N. So:
+// (1) scan l on 8 L points of (0, top] in FP32 (lanes over points) and take the best;
+// (2) Newton steps in FP64 on l'(lambda) = -1 + E_w[N] / lambda, l''(lambda) =
+//     (Var_w[N] - E_w[N]) / lambda^2, kept within two scan cells of the best point
+//     (bisection where a step would leave it, fixed-point steps lambda <- E_w[N] where
+//     l'' >= 0); (3) the boundary lambda = 0 when l(0) is not smaller. A group of L
+// consecutive lanes (mask gm, sl the lane within it) calls it and every lane gets the result;
+// NAN if h is empty.
 template <int L>
 __device__ inline double group_lambda_mle(const int* h, int n_max, double lambda0, int sl, unsigned gm) {
-  double c = 0.0, cn = 0.0;
-  int top = -1;
+  int top = -1, bot = n_max + 1;
   for (int k = sl; k <= n_max; k += L)
-    if (h[k] > 0) { c += h[k]; cn += (double)k * h[k]; top = k; }
+    if (h[k] > 0) { top = k; bot = min(bot, k); }
   for (int o = L / 2; o > 0; o >>= 1) {
-    c += __shfl_xor_sync(gm, c, o, L);
-    cn += __shfl_xor_sync(gm, cn, o, L);
     top = max(top, __shfl_xor_sync(gm, top, o, L));
+    bot = min(bot, __shfl_xor_sync(gm, bot, o, L));
   }
   if (top < 0) return NAN;
   if (top == 0) return 0.0;
-  double lam = cn / c, ll = -INFINITY;
+  // (1) coarse scan, log2 units: l / ln 2 = -lambda / ln 2 + log2 sum_N h[N] 2^(N log2(lambda / lambda0))
+  constexpr int G = 8 * L;
+  const float lr0 = log2f((float)lambda0);
+  float best = -INFINITY;
+  int bi = 0;
+  for (int g = sl; g < G; g += L) {
+    const float lam = (float)top * (float)(g + 1) / (float)G;
+    const float s2 = log2f(lam) - lr0;
+    float mx = -INFINITY;
+    for (int k = bot; k <= top; ++k)
+      if (h[k] > 0) mx = fmaxf(mx, log2f((float)h[k]) + (float)k * s2);
+    float acc = 0.0f;
+    for (int k = bot; k <= top; ++k)
+      if (h[k] > 0) acc += exp2f(log2f((float)h[k]) + (float)k * s2 - mx);
+    const float l = -lam * 1.44269504f + mx + log2f(acc);
+    if (l > best) { best = l; bi = g; }
+  }
+  for (int o = L / 2; o > 0; o >>= 1) {  // argmax, the smaller index on ties
+    const float ob = __shfl_xor_sync(gm, best, o, L);
+    const int oi = __shfl_xor_sync(gm, bi, o, L);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  // (2) Newton in FP64 inside [lambda_(b-2), lambda_(b+2)] (two scan cells of slack for the
+  // FP32 rounding of the scan)
+  const double cell = (double)top / G;
+  double lo = fmax(cell * (bi - 1), 1e-300), hi = cell * (bi + 3);
+  double lam = cell * (bi + 1), ll = -INFINITY;
   for (int it = 0; it < 200; ++it) {
     const double s = log(lam / lambda0);
     double mx = -INFINITY;
@@ -144,8 +180,10 @@ __device__ inline double group_lambda_mle(const int* h, int n_max, double lambda
     const double E = s1 / sw, Vr = s2 / sw - E * E;
     ll = -lam + mx + log(sw);
     const double g = -1.0 + E / lam, H = (Vr - E) / (lam * lam);
+    if (g == 0.0) break;                   // a stationary point
+    if (g > 0.0) lo = lam; else hi = lam;  // the maximum lies on the side l' points to
     double nl = H < 0.0 ? lam - g / H : E;
-    if (!(nl > 0.0)) nl = 0.5 * lam;
+    if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
     const bool done = fabs(nl - lam) <= 1e-14 * lam;
     lam = nl;
     if (done) break;
@@ -183,17 +221,25 @@ cudaError_t chain_kernel_attributes(int precision, bool sigma_in_smem, int max_s
 // Resident CTAs per SM of the chain kernel for this block size and dynamic shared memory.
 int chain_kernel_occupancy(int precision, bool sigma_in_smem, int threads, size_t smem);
 cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, double* fp32_tflops);
-// PE-space kernel (fsmp_pe.cu): a chain on `lanes` (32 or 16) lanes, warps per CTA. Shared memory
+// PE-space kernel (fsmp_pe.cu, fsmp_pe_mix.cu, fsmp_pe_kernel.cuh): a chain on `lanes` (32 or 16)
+// lanes, warps per CTA. Shared memory
 // per CTA with windows up to n_alloc and a shared tile of C^-1 for Ns PEs per chain; FP64
 // workspace doubles per chain slot (FP32 mode); entries of a global C^-1 slot; ints of an N
 // histogram slot.
 size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int Ns);
 size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
 size_t pe_c_entries(int n_cap);  // entries of a global C^-1 slot (packed triangle)
+size_t pe_c_entry_bytes(int precision);  // bytes of one C^-1 entry (a pair of FP64 or FP32 values)
 inline size_t pe_hist_ints(int n_cap) { return (size_t)n_cap + 1; }
 cudaError_t pe_kernel_attributes(int precision, int max_smem);
 cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st);
-int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int lanes);
+int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int lanes, bool mix);
+// The MCP-mixture instances (fsmp_pe_mix.cu); launch_pe dispatches to them when M.n_comp > 1.
+cudaError_t pe_mix_attributes(int precision, int max_smem);
+int pe_mix_occupancy(int precision, int threads, size_t smem, int lanes);
+cudaError_t pe_mix_launch(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
+                          void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
+                          cudaStream_t st);
 bool pe_big(int n_cap);
 bool pe_lanes_ok(int lanes, int n_cap);
 // Slots (C^-1, workspace, histogram) are indexed by resident chain: CTA x warps x (32 / lanes).

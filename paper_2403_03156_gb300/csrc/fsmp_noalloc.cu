@@ -105,6 +105,7 @@ extern "C" int fsmp_run_device_noalloc(const fsmp_params* p, const fsmp_device_b
       (p->phi_kind != 0 && p->phi_kind != 1) || !(p->phi_p1 > 0) || !(p->phi_p2 > 0) || !(p->phi_support_ns > 0) ||
       !(p->sigma_q > 0) || !(p->sigma_noise > 0) || !(p->t0_hi >= p->t0_lo) || !(p->jump_J > 0) || !(p->jump_J <= 0.5))
     return fail(FSMP_ERR_INVALID, "invalid model parameters");
+  if (p->n_mix != 0) return fail(FSMP_ERR_INVALID, "the MCP charge mixture runs only in the PE-space kernel");
   if (p->n_cap < 1 || p->n_cap > kNoallocMaxCap) return fail(FSMP_ERR_INVALID, "n_cap exceeds the static-scratch limit of 64");
   const int n_max = b->n_max_hint > 0 ? b->n_max_hint : p->n_max;
   if (n_max < 1 || n_max > kNoallocMaxWindow) return fail(FSMP_ERR_INVALID, "window length exceeds the static-scratch limit of 256 samples");

@@ -1,1124 +1,8 @@
-// fsmp_pe.cu -- the FSMP chain in PE space, one warp per chain (arXiv 2403.03156, Sec. 2.4 and
-// Appendix A.1, with the Woodbury identity applied to the whole of A).
-//
-// Sigma(z) = sigma_eps^2 I + sigma_q^2 A A^T with A = [a_1 .. a_N] (n x N). With
-// r = sigma_eps^2 / sigma_q^2 and the N x N capacitance matrix C = r I + A^T A,
-//   Sigma^-1 = (I - A C^-1 A^T) / sigma_eps^2,   log|Sigma| = n log sigma_eps^2 + log|C| - N log r.
-// A chain keeps C^-1, v = C^-1 A^T y and the residual y = w - mu_q sum_k a_k. For a move with the
-// columns a_- = a_k (a PE of z) and a_+ (a new position), and b = A^T a_+,
-//   a_+^T Sigma^-1 a_+ = (|a_+|^2 - b^T C^-1 b) / sigma_eps^2,   a_+^T Sigma^-1 y = (a_+^T y - b^T v) / sigma_eps^2,
-//   1 - sigma_q^2 a_k^T Sigma^-1 a_k = r C^-1_kk,                a_k^T Sigma^-1 y = v_k / sigma_q^2,
-//   a_k^T Sigma^-1 a_+ = (C^-1 b)_k / sigma_q^2,
-// the 2x2 quantities of Eqs. (16)-(18). Only the p PEs whose support overlaps a_+ have b != 0, so a
-// proposal reads p^2 + O(p) entries of C^-1 and no n-vector beyond a_+'s support. An accepted move
-// updates C^-1 by bordering (birth), a Schur-complement downdate (death) or both in one pass
-// (update): O(N^2) instead of the O(n^2) of Sigma^-1. The charge summary is
-// E[Q | z, w] = N mu_q + sum_k v_k. Inner products a_i^T a_j over the window come from the SER
-// cross-correlation prefix table.
-//
-// Layout: a chain runs on a group of L consecutive lanes (L = 32: a warp; L = 16: two chains per
-// warp, for chains with few PEs, where most of a step is work that every lane repeats); a CTA
-// holds several independent chains and a group takes chains from a launch-wide counter. C^-1 sits
-// in a per-chain shared-memory tile (the packed triangle of Ns PEs) while N <= Ns and moves to the
-// chain's global slot (n_cap PEs) when a birth would exceed the tile. The counts of N after
-// burn-in (for lambda_FSMP) sit in a global slot per chain.
-//
-// Precision. For PEs close in time C is nearly singular (eigenvalues down to r) and C^-1 holds
-// entries near 1/r that cancel in b^T C^-1 b; stored in FP32 they cost about 1e-2 in log alpha per
-// step. C^-1, v and b therefore carry about 48 significant bits: FP64 in FP64 mode, and in FP32
-// mode float-float pairs (hi + lo, Dekker's exact product and Knuth's TwoSum) that run on the FP32
-// pipe -- an FP64 instruction costs this part as much as 64 FP32 ones. In FP32 mode the residual y,
-// the SER and phi tables, the random draws and the 2x2 algebra are FP32, and C^-1, v, y, log|Sigma|
-// and the log-likelihood are rebuilt from z in FP64 (Gauss-Jordan inversion of C, which is
-// symmetric positive definite) every refresh_every accepted moves and at the end. Per step the
-// random draws, proposal rules and acceptance tests are those of the Sigma^-1 kernel.
-#include <math.h>
-
-#include "fsmp_internal.h"
+// fsmp_pe.cu -- host side of the PE-space chain kernel (arXiv 2403.03156, Sec. 2.4 and Appendix
+// A.1) and its dynode-model instances; the kernel itself is in fsmp_pe_kernel.cuh.
+#include "fsmp_pe_kernel.cuh"
 
 namespace fsmp {
-namespace {
-
-constexpr int kPeMaxThreads = 128;  // warps per CTA: at most 4
-
-// The lanes of one chain: L consecutive lanes of a warp. Exchanges and reductions stay inside the
-// group; gm is its lane mask. A step draws the random numbers of the next L steps (one per lane).
-template <int L> struct Lanes {
-  int sl;       // lane within the group
-  int g;        // group within the warp
-  unsigned gm;  // lane mask of the group
-};
-template <int L> __device__ __forceinline__ Lanes<L> pe_lanes() {
-  static_assert(L == 32 || L == 16, "a chain runs on 32 or 16 lanes");
-  const int lane = threadIdx.x & 31;
-  Lanes<L> r;
-  r.sl = lane & (L - 1);
-  r.g = lane / L;
-  r.gm = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (r.g * L));
-  return r;
-}
-// the group's lanes with p set, as bits 0 .. L-1
-template <int L> __device__ __forceinline__ unsigned gballot(bool p, const Lanes<L> ln) {
-  const unsigned b = __ballot_sync(ln.gm, p);
-  if constexpr (L == 32) return b;
-  else return (b >> (ln.g * L)) & ((1u << L) - 1u);
-}
-
-// ---------------------------------------------------------------- float-float arithmetic
-// A value hi + lo with |lo| <= ulp(hi) / 2. TwoSum (Knuth) and the FMA-based exact product
-// (Dekker) give the rounding error of one FP32 operation exactly; the pair operations below are
-// the usual "sloppy" double-float forms (relative error about 2^-44).
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff ff_quick(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-  const float s = __fadd_rn(x.hi, y.hi);
-  const float bb = __fsub_rn(s, x.hi);
-  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
-  return ff_quick(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return ff_quick(p, e);
-}
-__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
-
-// The state arithmetic for both modes: C = double (FP64 mode) or ff (FP32 mode).
-__device__ __forceinline__ double cadd(double a, double b) { return a + b; }
-__device__ __forceinline__ double csub(double a, double b) { return a - b; }
-__device__ __forceinline__ double cmul(double a, double b) { return a * b; }
-__device__ __forceinline__ double cfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ double cneg(double a) { return -a; }
-__device__ __forceinline__ double crcp(double a) { return 1.0 / a; }
-__device__ __forceinline__ double cnum(double a) { return a; }   // to the scoring precision
-__device__ __forceinline__ double c64(double a) { return a; }    // to FP64
-__device__ __forceinline__ bool cnz(double a) { return a != 0.0; }
-template <int L> __device__ __forceinline__ double cshfl_xor(double a, int o, unsigned gm) {
-  return __shfl_xor_sync(gm, a, o, L);
-}
-template <int L> __device__ __forceinline__ double cshfl(double a, int src, unsigned gm) {
-  return __shfl_sync(gm, a, src, L);
-}
-__device__ __forceinline__ double cfromf(double a) { return a; }
-template <typename C> __device__ __forceinline__ C czero();
-template <> __device__ __forceinline__ double czero<double>() { return 0.0; }
-
-__device__ __forceinline__ ff cadd(ff a, ff b) { return ff_add(a, b); }
-__device__ __forceinline__ ff csub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
-__device__ __forceinline__ ff cmul(ff a, ff b) { return ff_mul(a, b); }
-__device__ __forceinline__ ff cfma(ff a, ff b, ff c) { return ff_add(ff_mul(a, b), c); }
-__device__ __forceinline__ ff cneg(ff a) { return ff_neg(a); }
-__device__ __forceinline__ ff crcp(ff a) {  // one Newton step on the FP32 reciprocal
-  const float r = __frcp_rn(a.hi);
-  const ff e = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul(a, ff{r, 0.0f})));
-  return ff_add(ff{r, 0.0f}, ff_mul(e, ff{r, 0.0f}));
-}
-__device__ __forceinline__ float cnum(ff a) { return __fadd_rn(a.hi, a.lo); }
-__device__ __forceinline__ double c64(ff a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ bool cnz(ff a) { return a.hi != 0.0f; }
-template <int L> __device__ __forceinline__ ff cshfl_xor(ff a, int o, unsigned gm) {
-  return ff{__shfl_xor_sync(gm, a.hi, o, L), __shfl_xor_sync(gm, a.lo, o, L)};
-}
-template <int L> __device__ __forceinline__ ff cshfl(ff a, int src, unsigned gm) {
-  return ff{__shfl_sync(gm, a.hi, src, L), __shfl_sync(gm, a.lo, src, L)};
-}
-__device__ __forceinline__ ff cfromf(float a) { return ff{a, 0.0f}; }
-template <> __device__ __forceinline__ ff czero<ff>() { return ff{0.0f, 0.0f}; }
-// FP64 -> state value (refresh only)
-template <typename C> __device__ __forceinline__ C cfrom64(double a);
-template <> __device__ __forceinline__ double cfrom64<double>(double a) { return a; }
-template <> __device__ __forceinline__ ff cfrom64<ff>(double a) {
-  const float h = (float)a;
-  return ff{h, (float)(a - (double)h)};
-}
-// mu_q and r = sigma_eps^2 / sigma_q^2 as state values (split into pairs on the host)
-template <typename C> __device__ __forceinline__ C c_mu(const DevModel& M);
-template <> __device__ __forceinline__ double c_mu<double>(const DevModel& M) { return M.mu_q; }
-template <> __device__ __forceinline__ ff c_mu<ff>(const DevModel& M) { return ff{M.mu_hi, M.mu_lo}; }
-template <typename C> __device__ __forceinline__ C c_r(const DevModel& M);
-template <> __device__ __forceinline__ double c_r<double>(const DevModel& M) { return M.se2 / M.sq2; }
-template <> __device__ __forceinline__ ff c_r<ff>(const DevModel& M) { return ff{M.r_hi, M.r_lo}; }
-
-// group sums of state values: over all lanes, or over lanes [0, m) (zero beyond m)
-template <int L, typename C> __device__ __forceinline__ C csum(C v, const Lanes<L> ln) {
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v = cadd(v, cshfl_xor<L>(v, o, ln.gm));
-  return v;
-}
-template <int L, typename C> __device__ __forceinline__ C csum_first(C v, int m, const Lanes<L> ln) {
-  for (int o = L / 2; o > 0; o >>= 1)
-    if (o < m) v = cadd(v, cshfl_xor<L>(v, o, ln.gm));
-  return cshfl<L>(v, 0, ln.gm);
-}
-
-// C^-1 is symmetric and stored as its lower triangle, row by row: entry (i, j), j <= i, at
-// tri(i) + j. The storage has no row stride, so a chain's C^-1 moves from the shared tile to
-// its global slot by a plain copy.
-__host__ __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
-__device__ __forceinline__ int pk(int i, int j) { return i >= j ? tri(i) + j : tri(j) + i; }
-// (i, j) of packed position e (j <= i); the FP32 square root is exact enough below 2^22
-__device__ __forceinline__ void untri(int e, int& i, int& j) {
-  i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  if (tri(i + 1) <= e) ++i;
-  if (tri(i) > e) --i;
-  j = e - tri(i);
-}
-
-// sum_a C^-1[q][idx[a]] b[a] over a < m (skipping idx[a] == skip); BIG: four independent
-// partial sums so that the gathers of consecutive terms overlap
-template <typename C, bool BIG>
-__device__ __forceinline__ C dot_row(const C* __restrict__ Cp, int q, const int* __restrict__ idx,
-                                     const C* __restrict__ b, int m, int skip) {
-  C s0 = czero<C>();
-  int a = 0;
-  if constexpr (BIG) {
-    C s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
-#pragma unroll 1
-    for (; a + 3 < m; a += 4) {
-      const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
-      const C r0 = Cp[pk(q, i0)], r1 = Cp[pk(q, i1)], r2 = Cp[pk(q, i2)], r3 = Cp[pk(q, i3)];
-      if (i0 != skip) s0 = cfma(r0, b[a], s0);
-      if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
-      if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
-      if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
-    }
-    s0 = cadd(cadd(s0, s1), cadd(s2, s3));
-  }
-#pragma unroll 1
-  for (; a < m; ++a)
-    if (idx[a] != skip) s0 = cfma(Cp[pk(q, idx[a])], b[a], s0);
-  return s0;
-}
-
-template <int L, typename T> __device__ __forceinline__ T wsum(T v, const Lanes<L> ln) {
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(ln.gm, v, o, L);
-  return v;
-}
-template <int L, typename T> __device__ __forceinline__ T wmax(T v, const Lanes<L> ln) {
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(ln.gm, v, o, L));
-  return v;
-}
-
-// ---------------------------------------------------------------- model tables
-template <typename T> struct PeTab;
-template <> struct PeTab<double> {
-  using C = double;
-  __device__ static const double* V(const DevModel& M) { return M.V64; }
-  __device__ static const double* logphi(const DevModel& M) { return M.logphi; }
-  __device__ static const double* cphi(const DevModel& M) { return M.cphi; }
-  __device__ static const double* tc(const DevModel& M) { return M.tc64; }
-};
-template <> struct PeTab<float> {
-  using C = ff;
-  __device__ static const float* V(const DevModel& M) { return M.V32; }
-  __device__ static const float* logphi(const DevModel& M) { return M.logphi32; }
-  __device__ static const float* cphi(const DevModel& M) { return M.cphi32; }
-  __device__ static const ff* tc(const DevModel& M) { return reinterpret_cast<const ff*>(M.tcff); }
-};
-
-template <typename T> __device__ __forceinline__ T pe_logphi(const DevModel& M, int d) {
-  return (d < -M.D || d > M.D) ? (T)-INFINITY : __ldg(PeTab<T>::logphi(M) + (d + M.D));
-}
-template <typename T> __device__ __forceinline__ T pe_cphi(const DevModel& M, int d) {
-  if (d < -M.D) return (T)0;
-  if (d > M.D) return __ldg(PeTab<T>::cphi(M) + 2 * M.D);
-  return __ldg(PeTab<T>::cphi(M) + (d + M.D));
-}
-
-// Support of the PE at grid index j in a window of n samples: its first sample w0 = ceil(j / R),
-// the phase ph = w0 R - j of that sample, and the range [ilo, ihi) of its support samples
-// (sample w0 + i, SER index ph + i R) that lie in the window.
-struct Sup {
-  int w0, ph, ilo, ihi;
-};
-__device__ __forceinline__ Sup pe_sup(const DevModel& M, int n, int j) {
-  Sup s;
-  s.w0 = (int)floorf((float)(j + M.R - 1) / (float)M.R);  // exact for |j| < 2^22
-  s.ph = s.w0 * M.R - j;
-  const int mph = (M.Lt - s.ph + M.R - 1) / M.R;
-  s.ilo = max(0, -s.w0);
-  s.ihi = min(mph, n - s.w0);
-  if (s.ihi <= s.ilo) s.ilo = s.ihi = 0;  // no sample of the window: an all-zero column
-  return s;
-}
-
-// a_x^T a_q over the window, for x with support s and q = x - o (|o| < Lt), from the prefix table.
-template <typename C> __device__ __forceinline__ C xcorr(const DevModel& M, const C* __restrict__ tc, const Sup& s, int o) {
-  const int O = 2 * M.Lt - 1;
-  const C* base = tc + (size_t)s.ph * M.tcM * O + (o + M.Lt - 1);
-  C v = base[(size_t)s.ihi * O];
-  if (s.ilo > 0) v = csub(v, base[(size_t)s.ilo * O]);
-  return v;
-}
-
-// Smallest j in [T_lo, T_hi) with cphi(j - k0) - base > target (L-ary group search; cphi is
-// non-decreasing, so the answer does not depend on L); if rounding leaves none, the last j of T
-// with phi > 0.
-template <typename T, int L>
-__device__ int pe_birth_search(const DevModel& M, int T_lo, int T_hi, int k0, T base, T target, const Lanes<L> ln) {
-  int lo = T_lo, hi = T_hi - 1;
-  if ((pe_cphi<T>(M, hi - k0) - base) > target) {
-    while (lo < hi) {
-      const int len = hi - lo + 1;
-      const int step = (len + L - 1) / L;
-      const int p = min(hi, lo + (ln.sl + 1) * step - 1);
-      const bool pred = (pe_cphi<T>(M, p - k0) - base) > target;
-      const unsigned b = gballot(pred, ln);
-      const int f = __ffs(b) - 1;
-      const int new_lo = lo + f * step;
-      hi = min(hi, lo + (f + 1) * step - 1);
-      lo = new_lo;
-    }
-    return lo;
-  }
-  int last = -1;
-  for (int top = T_hi - 1; top >= T_lo; top -= L) {
-    const int j = top - ln.sl;
-    const bool ok = j >= T_lo && pe_logphi<T>(M, j - k0) > (T)-INFINITY;
-    const unsigned b = gballot(ok, ln);
-    if (b) { last = top - (__ffs(b) - 1); break; }
-  }
-  return last;
-}
-
-template <typename T> struct PeRand {
-  T z1, lu0, u3, u4, z2, lu;  // t0 shift normal, log u2, jump type, PE choice, shift normal, log u7
-};
-
-// FP32 value of the uniform ((x >> 11) + 0.5) 2^-53: the odd 54-bit integer 2 (x >> 11) + 1
-// rounded to FP32, times 2^-54 (exact), i.e. the FP64 uniform rounded to FP32 without FP64 work.
-__device__ __forceinline__ float u01_float(uint64_t x) {
-  return __ull2float_rn(((x >> 11) << 1) | 1ull) * 0x1.0p-54f;
-}
-
-// Per-chain statistics (shared memory, written by the group's first lane).
-struct PeStats {
-  long long sN, sN2, sK, sK2;
-  double sQ, sQ2, q_cur, logdet, logL, drift_max, wsq;
-  unsigned long long alg_words;
-  int acc[3], prop[3], acc_t0, prop_t0, n_refresh, status, q_from, n_acc_refresh, refresh_fail, pad;
-};
-
-__host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-// Per-chain shared memory. C is the state type (8 bytes in both modes).
-template <typename T> struct PeChain {
-  using C = typename PeTab<T>::C;
-  PeStats* st;
-  PeRand<T>* rnd;  // draws of the next L steps [L]
-  int* list;   // PE grid indices [n_cap]
-  int* ovi;    // PEs overlapping the proposed one [n_cap]
-  C* ovb;      // their inner products with it [n_cap]
-  C* v;        // C^-1 A^T y [n_cap]
-  C* cv;       // row k of C^-1 / C^-1 b [n_cap]
-  C* uv;       // second work vector [n_cap]
-  T* y;        // residual [n_alloc]
-  T* lPhi;     // log(Phi_T(t0) g) on the chain's t0 grid [win_extra]
-  C* Cs;       // C^-1 tile: packed triangle of Ns PEs
-};
-template <typename T, int L> __host__ __device__ inline size_t pe_chain_bytes(int n_cap, int n_alloc, int win_extra, int Ns) {
-  return a16(sizeof(PeStats)) + a16(sizeof(PeRand<T>) * L) + 2 * a16(sizeof(int) * n_cap) +
-         4 * a16(8 * (size_t)n_cap) + a16(sizeof(T) * n_alloc) + a16(sizeof(T) * win_extra) +
-         a16(8 * (size_t)tri(Ns));
-}
-template <typename T> __host__ __device__ inline size_t pe_block_bytes(int Lt, int n_cap) {
-  return a16(sizeof(T) * Lt) + a16(sizeof(T) * (n_cap + 2));
-}
-template <typename T, int L> __device__ PeChain<T> pe_carve(unsigned char* p, int n_cap, int n_alloc, int win_extra, int Ns) {
-  using C = typename PeTab<T>::C;
-  PeChain<T> W;
-  size_t o = 0;
-  W.st = reinterpret_cast<PeStats*>(p + o); o += a16(sizeof(PeStats));
-  W.rnd = reinterpret_cast<PeRand<T>*>(p + o); o += a16(sizeof(PeRand<T>) * L);
-  W.list = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
-  W.ovi = reinterpret_cast<int*>(p + o); o += a16(sizeof(int) * n_cap);
-  W.ovb = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
-  W.v = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
-  W.cv = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
-  W.uv = reinterpret_cast<C*>(p + o); o += a16(8 * (size_t)n_cap);
-  W.y = reinterpret_cast<T*>(p + o); o += a16(sizeof(T) * n_alloc);
-  W.lPhi = reinterpret_cast<T*>(p + o); o += a16(sizeof(T) * win_extra);
-  W.Cs = reinterpret_cast<C*>(p + o);
-  return W;
-}
-
-// Global per-chain slots (one per resident chain of the launch).
-struct PeSlots {
-  void* C;             // C^-1 slots (8-byte entries): the packed triangle of n_cap PEs
-  size_t c_stride;     // entries per slot
-  double* ws;          // FP64 refresh workspace slots (FP32 mode)
-  size_t ws_stride;    // doubles per slot
-  int* hist;           // N histogram slots, n_cap + 1 counts each
-  int* counter;        // next chain of the launch (zeroed before the launch)
-  int Ns;              // shared-memory tile of C^-1 (0: always global)
-};
-
-// FP64 refresh workspace of one chain: C (n_cap x n_cap) and four vectors of max(n_cap, n_alloc).
-__host__ __device__ inline int pe_lvec(int n_cap, int n_alloc) { return n_cap > n_alloc ? n_cap : n_alloc; }
-__host__ __device__ inline size_t pe_ws_doubles(int n_cap, int n_alloc) {
-  return (size_t)n_cap * n_cap + 4 * (size_t)pe_lvec(n_cap, n_alloc);
-}
-
-// Charge hold: the state's charge summary q_cur holds from step q_from on; close it at step s.
-__device__ __forceinline__ void close_hold(PeStats& S, int s, int burn_in) {
-  const int from = max(S.q_from, burn_in);
-  if (s > from) {
-    const double c = (double)(s - from);
-    S.sQ += S.q_cur * c;
-    S.sQ2 += S.q_cur * S.q_cur * c;
-  }
-}
-
-struct RefreshOut {
-  int ok;
-  double logdet, logL, drift;
-};
-
-// FP64 rebuild of C^-1, v, y, log|Sigma| and the log-likelihood from the PE list (FP32 mode).
-// ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
-// value (no address of the caller's locals escapes, so they stay in registers).
-template <typename T, bool BIG, int L>
-__device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T> W, typename PeTab<T>::C* Cp,
-                                              double* ws, int n_cap, int lvec, const float* w, double wsq, int n,
-                                              int N, const Lanes<L> ln) {
-  using C = typename PeTab<T>::C;
-  RefreshOut out{0, 0.0, 0.0, 0.0};
-  const int ws_ld = N > 0 ? N : 1;
-  double* A = ws;                               // C, then C^-1 (row-major N x N)
-  double* h = A + (size_t)n_cap * n_cap;        // A^T y
-  double* rowk = h + lvec;                      // staged pivot row
-  double* colk = rowk + lvec;                   // staged pivot column
-  const double* V = M.V64;
-  const double mu = M.mu_q, r = M.se2 / M.sq2;
-  // C = r I + A^T A (full, row-major)
-#pragma unroll 1
-  for (int i = 0; i < N; ++i) {
-    const int ji = W.list[i];
-    const Sup si = pe_sup(M, n, ji);
-#pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      const int o = ji - W.list[j];
-      double c = (o > -M.Lt && o < M.Lt) ? xcorr<double>(M, M.tc64, si, o) : 0.0;
-      if (j == i) c += r;
-      A[(size_t)i * ws_ld + j] = c;
-    }
-  }
-  __syncwarp(ln.gm);
-  // With y = w - mu A 1: h = A^T y = A^T w - mu (A^T A) 1, and
-  // y^T y = w^T w - 2 mu 1^T A^T w + mu^2 1^T A^T A 1 -- no FP64 copy of y is needed.
-  double awt = 0.0, rst = 0.0;
-#pragma unroll 1
-  for (int k = ln.sl; k < N; k += L) {
-    const Sup s = pe_sup(M, n, W.list[k]);
-    double a0 = 0.0, a1 = 0.0;
-    int i = s.ilo;
-#pragma unroll 1
-    for (; i + 1 < s.ihi; i += 2) {
-      a0 = fma(V[s.ph + i * M.R], (double)w[s.w0 + i], a0);
-      a1 = fma(V[s.ph + (i + 1) * M.R], (double)w[s.w0 + i + 1], a1);
-    }
-    if (i < s.ihi) a0 = fma(V[s.ph + i * M.R], (double)w[s.w0 + i], a0);
-    double rs = -r;
-#pragma unroll 1
-    for (int j = 0; j < N; ++j) rs += A[(size_t)k * ws_ld + j];
-    const double aw = a0 + a1;
-    h[k] = aw - mu * rs;
-    awt += aw;
-    rst += rs;
-  }
-  awt = wsum(awt, ln);
-  rst = wsum(rst, ln);
-  const double yy = wsq - 2.0 * mu * awt + mu * mu * rst;
-  // the FP32 residual, each sample summed in FP64 over the PEs that cover it
-#pragma unroll 1
-  for (int x = ln.sl; x < n; x += L) {
-    double yv = (double)w[x];
-#pragma unroll 1
-    for (int k = 0; k < N; ++k) {
-      const int idx = x * M.R - W.list[k];
-      if (idx >= 0 && idx < M.Lt) yv = fma(-mu, V[idx], yv);
-    }
-    W.y[x] = (T)yv;
-  }
-  __syncwarp(ln.gm);
-  // Gauss-Jordan inversion in place with diagonal pivots (C is SPD: the pivots are the
-  // LDL^T pivots, all positive); log|C| = sum log pivot, kept as mantissa x 2^exponent
-  double pm = 1.0;
-  int pe = 0;
-#pragma unroll 1
-  for (int k = 0; k < N; ++k) {
-#pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      rowk[j] = A[(size_t)k * ws_ld + j];
-      colk[j] = A[(size_t)j * ws_ld + k];
-    }
-    __syncwarp(ln.gm);
-    const double piv = rowk[k];
-    if (!(piv > 0.0) || !isfinite(piv)) return out;
-    const double ip = 1.0 / piv;
-    int ex;
-    pm *= frexp(piv, &ex);
-    pe += ex;
-    pm = frexp(pm, &ex);
-    pe += ex;
-#pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) colk[j] *= ip;  // the row multipliers
-    __syncwarp(ln.gm);
-    // rows i != k: A_ij -= f_i A_kj (A_ik = -f_i); row k: A_kj / pivot. Lanes over columns
-    // (BIG: four rows per iteration so that their loads overlap).
-#pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      const double rkj = rowk[j];
-      int i = 0;
-      if constexpr (BIG) {
-#pragma unroll 1
-        for (; i + 3 < N; i += 4) {
-          double x[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) x[r] = A[(size_t)(i + r) * ws_ld + j];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int ir = i + r;
-            const double f = colk[ir];
-            A[(size_t)ir * ws_ld + j] = (ir == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x[r]));
-          }
-        }
-      }
-#pragma unroll 1
-      for (; i < N; ++i) {
-        const double f = colk[i];
-        const double x = A[(size_t)i * ws_ld + j];
-        A[(size_t)i * ws_ld + j] = (i == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x));
-      }
-    }
-    __syncwarp(ln.gm);
-  }
-  const double logdetC = log(pm) + (double)pe * 0.6931471805599453;
-  // v = C^-1 h (C^-1 symmetric: lanes over columns)
-#pragma unroll 1
-  for (int i = ln.sl; i < N; i += L) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int j = 0;
-#pragma unroll 1
-    for (; BIG && j + 3 < N; j += 4) {
-      s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
-      s1 = fma(A[(size_t)(j + 1) * ws_ld + i], h[j + 1], s1);
-      s2 = fma(A[(size_t)(j + 2) * ws_ld + i], h[j + 2], s2);
-      s3 = fma(A[(size_t)(j + 3) * ws_ld + i], h[j + 3], s3);
-    }
-#pragma unroll 1
-    for (; j < N; ++j) s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
-    rowk[i] = (s0 + s1) + (s2 + s3);
-  }
-  __syncwarp(ln.gm);
-  double hv = 0.0;
-#pragma unroll 1
-  for (int i = ln.sl; i < N; i += L) hv += h[i] * rowk[i];
-  hv = wsum(hv, ln);
-  // drift of the incremental state, then the refreshed state (packed lower triangle)
-  double dmax = 0.0, amax = 0.0;
-#pragma unroll 1
-  for (int e = ln.sl; e < tri(N); e += L) {
-    int i, j;
-    untri(e, i, j);
-    const double nv = A[(size_t)i * ws_ld + j];
-    dmax = fmax(dmax, fabs(nv - c64(Cp[e])));
-    amax = fmax(amax, fabs(nv));
-    Cp[e] = cfrom64<C>(nv);
-  }
-  double vd = 0.0, va = 0.0;
-#pragma unroll 1
-  for (int i = ln.sl; i < N; i += L) {
-    vd = fmax(vd, fabs(rowk[i] - c64(W.v[i])));
-    va = fmax(va, fabs(rowk[i]));
-    W.v[i] = cfrom64<C>(rowk[i]);
-  }
-  dmax = wmax(dmax, ln); amax = wmax(amax, ln); vd = wmax(vd, ln); va = wmax(va, ln);
-  __syncwarp(ln.gm);
-  out.ok = 1;
-  out.drift = fmax(amax > 0.0 ? dmax / amax : 0.0, va > 0.0 ? vd / fmax(va, 1.0) : 0.0);
-  out.logdet = n * M.log_se2 + logdetC - N * M.log_r;
-  out.logL = -0.5 * (n * kLog2Pi + out.logdet + (yy - hv) / M.se2);
-  return out;
-}
-
-// Scalars of an accepted move, from the proposal and its scoring.
-template <typename C> struct PeMove {
-  int jump, kk, jp, jm, np;
-  C aa, quad, bv, vk, ay;
-  Sup sp;
-};
-
-template <typename C> struct AcceptOut {
-  C* Cp;
-  int cap, N;
-  unsigned long long words;
-};
-
-// Apply an accepted move to C^-1, v, y and the PE list (out of line: it runs on a minority of
-// steps and keeps the per-step code compact). Returns the new N, and the new C^-1 storage when
-// it moves from the shared tile (capacity cap PEs) to the global slot (n_cap PEs).
-template <typename T, bool BIG, int L>
-__device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel& M, const PeChain<T> W, const T* Vs,
-                                                                  typename PeTab<T>::C* Cp, int cap,
-                                                                  typename PeTab<T>::C* Cg,
-                                                                  const PeMove<typename PeTab<T>::C> mv, int n, int N,
-                                                                  const Lanes<L> ln) {
-  // One form for the three moves. With c = row k of C^-1 (death, update), gamma = c_k, and
-  // u' = C_-^-1 b~ (birth, update: C_- is C without PE k for an update, C itself for a birth;
-  // b~ is b without its k entry), delta = r + |a_+|^2 - b~^T u':
-  //   C'_ij = C_{m(i) m(j)} - c_m(i) c_m(j) / gamma + u'_i u'_j / delta   (i, j != s),
-  //   C'_is = -u'_i / delta,  C'_ss = 1 / delta,
-  // where s is the slot of the new PE (N for a birth, k for an update; none for a death) and
-  // m moves the last PE into slot k for a death (identity otherwise). v changes the same way.
-  using C = typename PeTab<T>::C;
-  const C mu = c_mu<C>(M), rr = c_r<C>(M);
-  const T muT = (T)M.mu_q;
-  const int R = M.R, np = mv.np, kk = mv.kk, jump = mv.jump;
-  const bool has_m = jump != 0, has_p = jump != 1;
-  const int skip = jump == 2 ? kk : -1;
-  const int Nout = N + (jump == 0 ? 1 : (jump == 1 ? -1 : 0));
-  const int s = jump == 0 ? N : (jump == 2 ? kk : -1);
-  const int last = N - 1;
-  // vectors: c (cv; zero for a birth) and C^-1 b~ (uv; zero for a death). The passes below
-  // always apply both terms, so that they have no branches on the move type.
-  const int krow = has_m ? kk : 0;
-  const int npu = has_p ? np : 0;
-#pragma unroll 1
-  for (int i = ln.sl; i < N; i += L) {
-    const C ci = Cp[pk(krow, i)];
-    W.cv[i] = has_m ? ci : czero<C>();
-    W.uv[i] = dot_row<C, BIG>(Cp, i, W.ovi, W.ovb, npu, skip);
-  }
-  if (ln.sl == 0 && jump == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth (N < n_cap)
-  __syncwarp(ln.gm);
-  C ig = czero<C>(), idl = czero<C>(), t = czero<C>(), fv = czero<C>();
-  if (has_m) {
-    ig = crcp(W.cv[kk]);
-    fv = cmul(cadd(mv.vk, mu), ig);
-  }
-  if (has_p) {
-    // b^T v in full state precision (the scoring used an FP32 sum)
-    C bvf = czero<C>();
-#pragma unroll 1
-    for (int a = ln.sl; a < np; a += L) bvf = cfma(W.ovb[a], W.v[W.ovi[a]], bvf);
-    bvf = csum(bvf, ln);
-    C bk = czero<C>(), wk = czero<C>();
-    if (jump == 2) {
-      // u' = w - c w_k / gamma on the system without PE k
-      wk = W.uv[kk];
-      const C wkg = cneg(cmul(wk, ig));
-#pragma unroll 1
-      for (int i = ln.sl; i < N; i += L) W.uv[i] = (i == kk) ? czero<C>() : cfma(W.cv[i], wkg, W.uv[i]);
-#pragma unroll 1
-      for (int a = ln.sl; a < np; a += L)
-        if (W.ovi[a] == kk) bk = W.ovb[a];
-      bk = csum(bk, ln);
-      __syncwarp(ln.gm);
-    }
-    C bu = czero<C>();
-#pragma unroll 1
-    for (int a = ln.sl; a < np; a += L)
-      if (W.ovi[a] != skip) bu = cfma(W.ovb[a], W.uv[W.ovi[a]], bu);
-    bu = csum(bu, ln);
-    idl = crcp(csub(cadd(rr, mv.aa), bu));
-    // t = (b~^T v_- - mu b~^T u' - h_new) / delta with v_- = v after removing PE k and h_new the
-    // new PE's a^T y on the residual without PE k
-    const C bvm = jump == 2 ? csub(csub(bvf, cmul(bk, mv.vk)), cmul(wk, fv)) : bvf;
-    const C hnew = csub(cadd(mv.ay, cmul(mu, bk)), cmul(mu, mv.aa));
-    t = cmul(csub(csub(bvm, cmul(mu, bu)), hnew), idl);
-  }
-  if (jump == 0 && N + 1 > cap && Cp != Cg) {  // the tile is full: move C^-1 to the global slot
-#pragma unroll 1
-    for (int e = ln.sl; e < tri(N); e += L) Cg[e] = Cp[e];
-    Cp = Cg;
-    cap = M.n_cap;
-    __syncwarp(ln.gm);
-  }
-  // C^-1 in place over the packed triangle, all lanes on consecutive entries. A pass reads an
-  // entry only where it writes it, or in the last row for a death (which it does not write).
-  const C nig = cneg(ig);
-  const int kmap = jump == 1 ? kk : -1;  // the slot the last PE moves into
-#pragma unroll 1
-  for (int e = ln.sl; e < tri(Nout); e += L) {  // rows 0 .. Nout-1
-    int i, j;
-    untri(e, i, j);
-    const int mi = (i == kmap) ? last : i, mj = (j == kmap) ? last : j;
-    const C old = Cp[pk(mi, mj)];
-    const C val = cfma(W.uv[i], cmul(W.uv[j], idl), cfma(W.cv[mi], cmul(W.cv[mj], nig), old));
-    const C sv = (i == s && j == s) ? idl : cneg(cmul(W.uv[i == s ? j : i], idl));
-    Cp[e] = (i == s || j == s) ? sv : val;
-  }
-  // v' = v_m - c_m fv + (t - mu) u', v'_s = -t
-  const C tm = csub(t, mu), nfv = cneg(fv);
-#pragma unroll 1
-  for (int i = ln.sl; i < Nout; i += L) {
-    const int mi = (i == kmap) ? last : i;
-    const C val = cfma(tm, W.uv[i], cfma(W.cv[mi], nfv, W.v[mi]));
-    W.v[i] = (i == s) ? cneg(t) : val;
-  }
-  // residual and PE list
-  unsigned long long wds = (unsigned long long)N * np + 2ull * tri(Nout) + 2ull * Nout;
-  if (has_m) {
-    const Sup sm = pe_sup(M, n, mv.jm);
-#pragma unroll 1
-    for (int i = sm.ilo + ln.sl; i < sm.ihi; i += L) W.y[sm.w0 + i] += muT * Vs[sm.ph + i * R];
-    wds += 2 * (sm.ihi - sm.ilo) + N;
-    __syncwarp(ln.gm);
-  }
-  if (has_p) {
-    const Sup sp = mv.sp;
-#pragma unroll 1
-    for (int i = sp.ilo + ln.sl; i < sp.ihi; i += L) W.y[sp.w0 + i] -= muT * Vs[sp.ph + i * R];
-    wds += 2 * (sp.ihi - sp.ilo);
-  }
-  if (ln.sl == 0) {
-    if (jump == 0) W.list[N] = mv.jp;
-    else if (jump == 1) W.list[kk] = W.list[last];
-    else W.list[kk] = mv.jp;
-  }
-  __syncwarp(ln.gm);
-  return AcceptOut<C>{Cp, cap, Nout, wds};
-}
-
-template <typename T, bool BIG, int L>
-__global__ void __launch_bounds__(kPeMaxThreads, 4)
-    pe_kernel(const __grid_constant__ DevModel M, const __grid_constant__ BatchView B, const __grid_constant__ PeSlots G) {
-  using C = typename PeTab<T>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool fp32 = sizeof(T) == 4;
-  const Lanes<L> ln = pe_lanes<L>();
-  constexpr int kGroups = 32 / L;  // chains per warp
-  const int cw = (threadIdx.x >> 5) * kGroups + ln.g, nchains = (blockDim.x >> 5) * kGroups;
-  const int n_alloc = B.n_max, n_cap = M.n_cap, Ns = G.Ns;
-  // block tables: the SER and log(i), i = 1 .. n_cap + 1
-  T* Vs = reinterpret_cast<T*>(smem_raw);
-  T* lgN = reinterpret_cast<T*>(smem_raw + a16(sizeof(T) * M.Lt));
-  for (int m = threadIdx.x; m < M.Lt; m += blockDim.x) Vs[m] = PeTab<T>::V(M)[m];
-  for (int i = threadIdx.x; i < n_cap + 2; i += blockDim.x)
-    lgN[i] = i > 0 ? (fp32 ? (T)logf((float)i) : (T)log((double)i)) : (T)0;
-  __syncthreads();
-  PeChain<T> W = pe_carve<T, L>(smem_raw + pe_block_bytes<T>(M.Lt, n_cap) +
-                                    (size_t)cw * pe_chain_bytes<T, L>(n_cap, n_alloc, M.win_extra, Ns),
-                                n_cap, n_alloc, M.win_extra, Ns);
-  PeStats& S = *W.st;
-  const size_t slot = (size_t)blockIdx.x * nchains + cw;
-  int* const hist = G.hist + slot * (size_t)(n_cap + 1);
-  C* const Cg = G.C ? reinterpret_cast<C*>(G.C) + slot * G.c_stride : nullptr;
-  double* const ws = G.ws ? G.ws + slot * G.ws_stride : nullptr;
-  const C* __restrict__ tc = PeTab<T>::tc(M);
-  const T q = (T)M.sq2, mu = (T)M.mu_q, rrT = (T)(M.se2 / M.sq2), iqT = (T)(1.0 / M.sq2), ise2T = (T)M.inv_se2;
-  const T Jt = (T)M.J, logJ = (T)M.log_J, inv_gT = (T)M.inv_g;
-  const int R = M.R;
-
-  for (;;) {
-    int ci = 0;
-    if (ln.sl == 0) ci = atomicAdd(G.counter, 1);
-    ci = __shfl_sync(ln.gm, ci, 0, L);
-    if (ci >= B.n_waveforms) break;
-    const int wi = B.order ? B.order[ci] : ci;
-    // ------------------------------------------------------------- chain set-up
-    const int o0 = B.offsets[wi], n = B.offsets[wi + 1] - o0;
-    const float* __restrict__ w = B.samples + o0;
-    const double lambda0 = B.lambda0[wi];
-    const double t_origin = B.t_origin ? B.t_origin[wi] : 0.0;
-    const int T_lo = B.T_lo ? B.T_lo[wi] : 0;
-    const int T_hi = B.T_hi ? B.T_hi[wi] : n * R;
-    const int k0_lo = (int)ceil((M.t0_lo - t_origin) / M.g - 1e-9);
-    const int k0_hi = (int)floor((M.t0_hi - t_origin) / M.g + 1e-9);
-    const uint64_t seed = B.seeds ? B.seeds[wi] : B.seed;
-    const uint64_t wf_id = B.wf_ids ? B.wf_ids[wi] : B.index_base + (uint64_t)wi;
-    const int n_steps = B.n_steps_arr ? B.n_steps_arr[wi] : B.n_steps;
-    const int burn_in = B.burn_in_arr ? B.burn_in_arr[wi] : B.burn_in;
-    fsmp_summary* out = B.out + wi;
-    fsmp_trace* trace = B.trace ? B.trace + (B.trace_off ? B.trace_off[wi] : (int64_t)wi * n_steps) : nullptr;
-    const bool invalid = n < 1 || n > n_alloc || T_hi <= T_lo || k0_hi < k0_lo || !(lambda0 > 0.0) || n_steps < 0 ||
-                         burn_in < 0 || (fp32 && ws == nullptr) || k0_hi - k0_lo + 1 > M.win_extra ||
-                         (Cg == nullptr && Ns < n_cap);
-    if (invalid) {
-      if (ln.sl == 0) {
-        fsmp_summary o;
-        o.mean_N = o.var_N = o.mean_t0 = o.var_t0 = o.mean_Q = o.var_Q = o.logL = o.logdet = NAN;
-        o.drift_max = 0.0; o.alg_bytes = 0.0; o.lambda_hat = NAN;
-        for (int k = 0; k < 3; ++k) { o.acc[k] = 0; o.prop[k] = 0; }
-        o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
-        o.status = FSMP_ST_INVALID;
-        *out = o;
-      }
-      __syncwarp(ln.gm);
-      continue;
-    }
-    int k0;
-    {
-      const double t0i = B.t0_init ? B.t0_init[wi] : NAN;
-      if (!isnan(t0i)) {
-        double kq = rint((t0i - t_origin) / M.g);
-        kq = fmin(fmax(kq, (double)k0_lo), (double)k0_hi);
-        k0 = (int)kq;
-      } else {
-        k0 = k0_lo + (k0_hi - k0_lo) / 2;
-      }
-    }
-    // log(Phi_T(t0) g) on the t0 grid (-inf where Phi_T = 0), from the FP64 tables
-    for (int k = ln.sl; k <= k0_hi - k0_lo; k += L) {
-      const int kq = k0_lo + k;
-      const double tot = pe_cphi<double>(M, T_hi - 1 - kq) - pe_cphi<double>(M, T_lo - 1 - kq);
-      W.lPhi[k] = tot > 0.0 ? (fp32 ? (T)logf((float)(tot * M.g)) : (T)log(tot * M.g)) : (T)-INFINITY;
-    }
-#pragma unroll 1
-    for (int k = ln.sl; k <= n_cap; k += L) hist[k] = 0;
-    // empty z: y = w
-    double wsq = 0.0;
-    for (int x = ln.sl; x < n; x += L) {
-      const float wx = w[x];
-      W.y[x] = (T)wx;
-      wsq += (double)wx * (double)wx;
-    }
-    wsq = wsum(wsq, ln);
-    if (ln.sl == 0) {
-      S.sN = S.sN2 = S.sK = S.sK2 = 0;
-      S.sQ = S.sQ2 = 0.0; S.q_cur = 0.0; S.q_from = 0;
-      S.logdet = n * M.log_se2;
-      S.logL = -0.5 * (n * kLog2Pi + S.logdet + wsq * M.inv_se2);
-      S.wsq = wsq;
-      S.drift_max = 0.0; S.alg_words = 0;
-      for (int k = 0; k < 3; ++k) { S.acc[k] = 0; S.prop[k] = 0; }
-      S.acc_t0 = S.prop_t0 = S.n_refresh = S.status = S.n_acc_refresh = S.refresh_fail = 0;
-    }
-    __syncwarp(ln.gm);
-    const T log_lambda0 = fp32 ? (T)logf((float)lambda0) : (T)log(lambda0);
-    C* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1 (packed), room for cap PEs
-    int cap = Ns > 0 ? Ns : n_cap;
-    int N = 0;
-
-    for (int step = 0; step < n_steps; ++step) {
-      // ---- random draws of the next L steps: lane l takes step step + l
-      if ((step & (L - 1)) == 0) {
-        PeRand<T> rd;
-#pragma unroll 1
-        for (int blk = 0; blk < 2; ++blk) {
-          uint64_t c[4] = {(uint64_t)(step + ln.sl), (uint64_t)blk, 0, 0};
-          philox4x64_10(c, seed, wf_id);
-          if (fp32) {
-            const float a = u01_float(c[0]), b = u01_float(c[1]), d = u01_float(c[2]), e = u01_float(c[3]);
-            if (blk == 0) {
-              rd.z1 = (T)(sqrtf(-2.0f * logf(a)) * cosf(6.2831853f * b));
-              rd.lu0 = (T)logf(d);
-              rd.u3 = (T)e;
-            } else {
-              rd.u4 = (T)a;
-              rd.z2 = (T)(sqrtf(-2.0f * logf(b)) * cosf(6.2831853f * d));
-              rd.lu = (T)logf(e);
-            }
-          } else {
-            const double a = u01_from_bits(c[0]), b = u01_from_bits(c[1]), d = u01_from_bits(c[2]),
-                         e = u01_from_bits(c[3]);
-            if (blk == 0) {
-              rd.z1 = (T)(sqrt(-2.0 * log(a)) * cos(kTwoPi * b));
-              rd.lu0 = (T)log(d);
-              rd.u3 = (T)e;
-            } else {
-              rd.u4 = (T)a;
-              rd.z2 = (T)(sqrt(-2.0 * log(b)) * cos(kTwoPi * d));
-              rd.lu = (T)log(e);
-            }
-          }
-        }
-        W.rnd[ln.sl] = rd;
-        __syncwarp(ln.gm);
-      }
-      const PeRand<T> rd = W.rnd[step & (L - 1)];
-      // ---- Gibbs part 1: MH on t0 (Sec. 2.4), uniform prior on its grid range
-      T la0 = (T)NAN;
-      const T lu0 = rd.lu0;
-      int t0f = 0, st_a = 0;
-      if (M.sample_t0) {
-        t0f = 1;
-        const int Dm = fp32 ? __float2int_rn((float)(rd.z1 * inv_gT)) : __double2int_rn((double)(rd.z1 * inv_gT));
-        const int k0p = k0 + Dm;
-        if (Dm == 0) {
-          la0 = (T)0;
-        } else if (k0p < k0_lo || k0p > k0_hi) {
-          la0 = (T)-INFINITY;
-        } else {
-          T part = (T)0;
-#pragma unroll 1
-          for (int k = ln.sl; k < N; k += L) {
-            const int j = W.list[k];
-            part += pe_logphi<T>(M, j - k0p) - pe_logphi<T>(M, j - k0);
-          }
-          la0 = wsum(part, ln);
-        }
-        if (lu0 < la0) { k0 = k0p; t0f |= 2; }
-      }
-      // ---- Gibbs part 2: one RJMCMC jump (Sec. 2.4)
-      const int jump = (N == 0) ? 0 : (rd.u3 < Jt ? 0 : (rd.u3 < (T)2 * Jt ? 1 : 2));
-      int valid = 0, noop = 0, kk = -1, jp = -1, jm = -1;
-      T la_prior = (T)0, la_fixed = (T)-INFINITY;
-      const T lu = rd.lu;
-      const T lphi_t0 = W.lPhi[k0 - k0_lo];
-      if (jump == 0) {
-        if (N >= n_cap) {
-          st_a |= FSMP_ST_CAPACITY;
-        } else if (lphi_t0 > (T)-INFINITY) {
-          const T base = pe_cphi<T>(M, T_lo - 1 - k0), tot = pe_cphi<T>(M, T_hi - 1 - k0) - base;
-          jp = pe_birth_search<T, L>(M, T_lo, T_hi, k0, base, rd.u4 * tot, ln);
-          valid = jp >= T_lo;
-          la_prior = log_lambda0 + lphi_t0 - lgN[N + 1] + (N == 0 ? logJ : (T)0);
-        }
-      } else {
-        kk = fp32 ? __float2int_rd((float)(rd.u4 * (T)N)) : __double2int_rd((double)(rd.u4 * (T)N));
-        if (kk >= N) kk = N - 1;
-        jm = W.list[kk];
-        if (jump == 1) {
-          valid = 1;
-          la_prior = -log_lambda0 - lphi_t0 + lgN[N] - (N == 1 ? logJ : (T)0);
-        } else {
-          const int Dm = fp32 ? __float2int_rn((float)(rd.z2 * inv_gT)) : __double2int_rn((double)(rd.z2 * inv_gT));
-          const int jpl = jm + Dm;
-          if (Dm == 0) {
-            noop = 1;
-            la_fixed = (T)0;
-          } else if (jpl < T_lo || jpl >= T_hi || pe_logphi<T>(M, jpl - k0) == (T)-INFINITY) {
-            la_fixed = (T)-INFINITY;
-          } else {
-            jp = jpl;
-            valid = 1;
-            la_prior = pe_logphi<T>(M, jp - k0) - pe_logphi<T>(M, jm - k0);
-          }
-        }
-      }
-      // ---- scoring: the 2x2 quantities in PE space, then the 2x2 algebra in T
-      PeMove<C> mv;
-      mv.jump = jump; mv.kk = kk; mv.jp = jp; mv.jm = jm; mv.np = 0;
-      mv.aa = mv.quad = mv.bv = mv.vk = mv.ay = czero<C>();
-      mv.sp = Sup{0, 0, 0, 0};
-      T mmm = 0, mmp = 0, mpp = 0, gm = 0, gp = 0, em = 1;
-      unsigned long long words = 0;
-      if (valid) {
-        if (jump != 1) {
-          const Sup sp = pe_sup(M, n, jp);
-          mv.sp = sp;
-          // PEs overlapping a_+, with b_q = a_q^T a_+
-          int np = 0;
-#pragma unroll 1
-          for (int base = 0; base < N; base += L) {
-            const int qi = base + ln.sl;
-            C bq = czero<C>();
-            if (qi < N) {
-              const int o = jp - W.list[qi];
-              if (o > -M.Lt && o < M.Lt) bq = xcorr<C>(M, tc, sp, o);
-            }
-            const bool ov = cnz(bq);
-            const unsigned m = gballot(ov, ln);
-            if (ov) {
-              const int pos = np + __popc(m & ((1u << ln.sl) - 1u));
-              W.ovi[pos] = qi;
-              W.ovb[pos] = bq;
-            }
-            np += __popc(m);
-          }
-          __syncwarp(ln.gm);
-          mv.np = np;
-          mv.aa = xcorr<C>(M, tc, sp, 0);
-          // rows of C^-1 b on the overlap set: lane a holds (C^-1 b)_{ovi[a]} (a < L), so that
-          // b^T C^-1 b and b^T v reduce over the group and (C^-1 b)_k is one of them for an update
-          T ayp = (T)0;
-#pragma unroll 1
-          for (int i = sp.ilo + ln.sl; i < sp.ihi; i += L) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
-          C qp = czero<C>(), ck = czero<C>();
-          T bvp = (T)0;
-          int kpos = -1;
-#pragma unroll 1
-          for (int a0 = 0; a0 < np; a0 += L) {
-            const int a = a0 + ln.sl;
-            if (a < np) {
-              const C rq = dot_row<C, BIG>(Cp, W.ovi[a], W.ovi, W.ovb, np, -1);
-              const C ba = W.ovb[a];
-              qp = cfma(ba, rq, qp);
-              bvp += (T)cnum(ba) * (T)cnum(W.v[W.ovi[a]]);
-              if (jump == 2 && W.ovi[a] == kk) { ck = rq; kpos = a; }
-            }
-          }
-          mv.quad = np <= L ? csum_first(qp, np, ln) : csum(qp, ln);
-          const T bvT = wsum(bvp, ln);  // b^T v at the scoring precision (the accept recomputes it)
-          const T ayT = wsum(ayp, ln);
-          mv.ay = cfromf(ayT);
-          if (jump == 2) {
-            // (C^-1 b)_k: from the lane that holds PE k's row, else (no overlap with the old
-            // position) a separate dot product
-            const unsigned hk = gballot(kpos >= 0, ln);
-            if (hk) {
-              ck = cshfl<L>(ck, __ffs(hk) - 1, ln.gm);
-            } else {
-              C c2 = czero<C>();
-              for (int a = ln.sl; a < np; a += L) c2 = cfma(Cp[pk(kk, W.ovi[a])], W.ovb[a], c2);
-              ck = csum(c2, ln);
-            }
-          }
-          mpp = (T)cnum(csub(mv.aa, mv.quad)) * ise2T;
-          gp = (ayT - bvT) * ise2T;
-          mmp = (T)cnum(ck) * iqT;
-          words += (unsigned long long)(N + 2 * np + 2 * (sp.ihi - sp.ilo) + np * np + np);
-        }
-        if (jump != 0) {
-          mv.vk = W.v[kk];
-          em = rrT * (T)cnum(Cp[tri(kk) + kk]);
-          mmm = ((T)1 - em) * iqT;
-          gm = (T)cnum(mv.vk) * iqT;
-          words += 2;
-        }
-      }
-      T la = la_fixed, dnu = (T)NAN, dT = (T)0;
-      int st_c = 0;
-      if (valid) {
-        // det(I + Lambda M), Lambda = sigma_q^2 diag(-1, 1), with 1 - q m_-- = em
-        const T Dd = em * ((T)1 + q * mpp) + q * q * mmp * mmp;
-        if (!(Dd > (T)0)) {
-          la = (T)-INFINITY;
-          st_c |= FSMP_ST_BADDET;
-        } else {
-          const T iD = (T)1 / Dd;
-          const T B11 = -q * ((T)1 + q * mpp) * iD, B12 = q * q * mmp * iD, B22 = q * em * iD;
-          const T rm = gm - mu * (mmp - mmm), rp = gp - mu * (mpp - mmp);
-          const T dR = (T)-2 * mu * (gp - gm) + mu * mu * (mmm - (T)2 * mmp + mpp) -
-                       (B11 * rm * rm + (T)2 * B12 * rm * rp + B22 * rp * rp);
-          dT = log(Dd);
-          dnu = (T)-0.5 * (dT + dR);
-          if (!isfinite(dnu)) {
-            la = (T)-INFINITY;
-            st_c |= FSMP_ST_NONFINITE;
-          } else {
-            la = dnu + la_prior;
-          }
-        }
-      }
-      const int acc = lu < la;
-      const int apply = acc && valid && isfinite(la);
-
-      // ---- accepted move: C^-1, v, y and the PE list
-      if (apply) {
-        {
-          const AcceptOut<C> ao = pe_accept<T, BIG, L>(M, W, Vs, Cp, cap, Cg, mv, n, N, ln);
-          Cp = ao.Cp;
-          cap = ao.cap;
-          N = ao.N;
-          words += ao.words;
-        }
-        C qs = czero<C>();
-        for (int i = ln.sl; i < N; i += L) qs = cadd(qs, W.v[i]);
-        qs = csum(qs, ln);
-        if (ln.sl == 0) {
-          close_hold(S, step, burn_in);
-          S.q_cur = N * M.mu_q + c64(qs);
-          S.q_from = step;
-          S.logdet += (double)dT;
-          S.logL += (double)dnu;
-          S.n_acc_refresh++;
-        }
-        __syncwarp(ln.gm);
-        if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          const RefreshOut ro = pe_refresh<T, BIG, L>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, ln);
-          C qr = czero<C>();
-          for (int i = ln.sl; i < N; i += L) qr = cadd(qr, W.v[i]);
-          qr = csum(qr, ln);
-          if (ln.sl == 0) {
-            S.n_acc_refresh = 0;
-            if (ro.ok) {
-              S.logdet = ro.logdet; S.logL = ro.logL;
-              S.drift_max = fmax(S.drift_max, ro.drift);
-              if (ro.drift > M.drift_tol) S.status |= FSMP_ST_DRIFT;
-              S.n_refresh++;
-              S.q_cur = N * M.mu_q + c64(qr);
-            } else {
-              S.status |= FSMP_ST_DRIFT;
-              S.refresh_fail++;
-            }
-          }
-          __syncwarp(ln.gm);
-        }
-      }
-
-      // ---- bookkeeping of the decided step (the group's first lane)
-      if (ln.sl == 0) {
-        S.prop[jump]++;
-        if (t0f & 1) { S.prop_t0++; if (t0f & 2) S.acc_t0++; }
-        if (apply) S.acc[jump]++;
-        S.status |= st_a | st_c;
-        S.alg_words += words;
-        if (step >= burn_in) {
-          const long long Nn = N, kq = k0;
-          S.sN += Nn; S.sN2 += Nn * Nn; S.sK += kq; S.sK2 += kq * kq;
-          atomicAdd(hist + N, 1);  // no value returned: the lane does not wait on it
-        }
-        if (trace) {
-          fsmp_trace tr;
-          tr.la0 = (double)la0; tr.lu0 = (double)lu0; tr.la = (double)la; tr.lu = (double)lu;
-          tr.dnu = (double)dnu; tr.N = N; tr.k0 = k0; tr.jump = jump;
-          tr.flags = t0f | (acc ? 4 : 0) | ((acc && noop) ? 8 : 0);
-          trace[step] = tr;
-        }
-      }
-      __syncwarp(ln.gm);
-    }
-
-    // ------------------------------------------------------------- chain end
-    if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
-      // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      const RefreshOut ro = pe_refresh<T, BIG, L>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, ln);
-      if (ln.sl == 0) {
-        if (ro.ok) {
-          S.logdet = ro.logdet; S.logL = ro.logL;
-          S.drift_max = fmax(S.drift_max, ro.drift);
-          if (ro.drift > M.drift_tol) S.status |= FSMP_ST_DRIFT;
-          S.n_refresh++;
-        } else {
-          S.status |= FSMP_ST_DRIFT;
-        }
-      }
-    }
-    const double lam_hat = group_lambda_mle<L>(hist, n_cap, lambda0, ln.sl, ln.gm);
-    if (ln.sl == 0) {
-      close_hold(S, n_steps, burn_in);
-      fsmp_summary o;
-      o.lambda_hat = lam_hat;
-      int ns = n_steps - burn_in;
-      if (ns < 0) ns = 0;
-      const double inv = ns > 0 ? 1.0 / ns : NAN;
-      const double mN = (double)S.sN * inv, mK = (double)S.sK * inv;
-      o.mean_N = mN; o.var_N = (double)S.sN2 * inv - mN * mN;
-      o.mean_t0 = t_origin + M.g * mK; o.var_t0 = M.g * M.g * ((double)S.sK2 * inv - mK * mK);
-      o.mean_Q = S.sQ * inv; o.var_Q = S.sQ2 * inv - o.mean_Q * o.mean_Q;
-      o.logL = S.logL; o.logdet = S.logdet;
-      o.drift_max = S.drift_max; o.alg_bytes = (double)S.alg_words * 8.0;
-      for (int k = 0; k < 3; ++k) { o.acc[k] = S.acc[k]; o.prop[k] = S.prop[k]; }
-      o.acc_t0 = S.acc_t0; o.prop_t0 = S.prop_t0; o.N_final = N; o.k0_final = k0;
-      o.status = S.status; o.n_samples = ns; o.n_refresh = S.n_refresh; o.reserved = 0;
-      *out = o;
-    }
-    __syncwarp(ln.gm);
-  }
-}
-
-// Float-float copy of an FP64 table: hi = fl(x), lo = fl(x - hi).
-__global__ void split_ff_kernel(const double* a, float* out, size_t n) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float h = (float)a[i];
-  out[2 * i] = h;
-  out[2 * i + 1] = (float)(a[i] - (double)h);
-}
-
-}  // namespace
 
 size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int Ns) {
   const int chains = warps * (32 / lanes);
@@ -1136,6 +20,10 @@ size_t pe_ws_slot_doubles(int n_cap, int n_alloc) { return pe_ws_doubles(n_cap, 
 
 size_t pe_c_entries(int n_cap) { return (size_t)tri(n_cap); }
 
+size_t pe_c_entry_bytes(int precision) {
+  return precision == FSMP_FP64 ? sizeof(PeTab<double>::C) : sizeof(PeTab<float>::C);
+}
+
 cudaError_t launch_split_ff(const double* a, float* out, size_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   split_ff_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, out, n);
@@ -1150,58 +38,25 @@ bool pe_big(int n_cap) { return n_cap > 192; }
 // Lanes per chain the kernel is built for: 32, and 16 where chains are small (not BIG).
 bool pe_lanes_ok(int lanes, int n_cap) { return lanes == 32 || (lanes == 16 && !pe_big(n_cap)); }
 
-namespace {
-// The kernel instance for (precision, BIG, lanes); f receives its address.
-template <typename F> cudaError_t with_pe_kernel(int precision, bool big, int lanes, F f) {
-  if (precision == FSMP_FP64) {
-    if (big) return f(pe_kernel<double, true, 32>);
-    return lanes == 16 ? f(pe_kernel<double, false, 16>) : f(pe_kernel<double, false, 32>);
-  }
-  if (big) return f(pe_kernel<float, true, 32>);
-  return lanes == 16 ? f(pe_kernel<float, false, 16>) : f(pe_kernel<float, false, 32>);
-}
-}  // namespace
 
 cudaError_t pe_kernel_attributes(int precision, int max_smem) {
-  for (int big = 0; big < 2; ++big)
-    for (int lanes : {32, 16}) {
-      if (big && lanes == 16) continue;
-      const cudaError_t e = with_pe_kernel(precision, big != 0, lanes, [&](auto k) {
-        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-      });
-      if (e != cudaSuccess) return e;
-    }
-  return cudaSuccess;
+  const cudaError_t e = pe_set_attributes<false>(precision, max_smem);
+  return e != cudaSuccess ? e : pe_mix_attributes(precision, max_smem);
 }
 
-int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int lanes) {
-  int n = 0;
-  const cudaError_t e = with_pe_kernel(precision, big, lanes, [&](auto k) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
-  });
-  return e == cudaSuccess ? n : 0;
+int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int lanes, bool mix) {
+  if (mix) return pe_mix_occupancy(precision, threads, smem, lanes);
+  return pe_occupancy<false>(precision, threads, smem, big, lanes);
 }
 
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
                       void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
                       cudaStream_t st) {
-  PeSlots G;
-  G.C = cinv;
-  G.c_stride = c_stride;
-  G.ws = ws;
-  G.ws_stride = ws_stride;
-  G.hist = hist;
-  G.counter = counter;
-  G.Ns = Ns;
   if (hist == nullptr || !pe_lanes_ok(lanes, M.n_cap)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  e = with_pe_kernel(M.precision, pe_big(M.n_cap), lanes, [&](auto k) {
-    k<<<ctas, warps * 32, smem, st>>>(M, B, G);
-    return cudaSuccess;
-  });
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  if (M.n_comp > 1)
+    return pe_mix_launch(M, B, warps, lanes, ctas, Ns, smem, cinv, c_stride, ws, ws_stride, hist, counter, st);
+  return pe_launch<false>(M, B, warps, lanes, ctas, Ns, smem, cinv, c_stride, ws, ws_stride, hist, counter,
+                          pe_big(M.n_cap), st);
 }
 
 }  // namespace fsmp

@@ -190,6 +190,17 @@ int validate_params(const fsmp_params* p) {
                                     p->threads_per_chain % 32))
     return FSMP_ERR_INVALID;
   if (p->phi_support_ns / p->grid_ns > 4.0e6) return FSMP_ERR_INVALID;
+  if (p->n_mix < 0 || p->n_mix > FSMP_MAX_MIX) return FSMP_ERR_INVALID;
+  if (p->n_mix > 0) {
+    double sum = 0.0;
+    for (int e = 0; e < p->n_mix; ++e) {
+      if (!(p->mix_G[e] >= 0.0) || !(p->mix_sigma[e] > 0.0) || !isfinite(p->mix_mu[e])) return FSMP_ERR_INVALID;
+      sum += p->mix_G[e];
+    }
+    if (!(fabs(sum - 1.0) <= 1e-9)) return FSMP_ERR_INVALID;  // G is a distribution
+    // the Sigma^-1 kernels carry one charge model; the mixture runs in the PE-space kernel
+    if (p->kernel != FSMP_KERNEL_AUTO && p->kernel != FSMP_KERNEL_PE) return FSMP_ERR_INVALID;
+  }
   return FSMP_OK;
 }
 
@@ -222,7 +233,8 @@ int pe_chains_per_cta(const fsmp_ctx* c) { return c->pe_warps * (32 / c->pe_lane
 int pe_shape(fsmp_ctx* c, int n_alloc, int* ctas, size_t* smem) {
   *smem = pe_smem_bytes(c->M, n_alloc, c->pe_warps, c->pe_lanes, c->pe_tile);
   if (*smem > (size_t)c->prop.sharedMemPerBlockOptin) return FSMP_ERR_INVALID;
-  int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem, pe_big(c->p.n_cap), c->pe_lanes);
+  int per_sm = pe_kernel_occupancy(c->p.precision, c->pe_warps * 32, *smem, pe_big(c->p.n_cap), c->pe_lanes,
+                                   c->M.n_comp > 1);
   if (per_sm < 1) return FSMP_ERR_INVALID;
   if (c->p.pe_ctas_per_sm > 0) per_sm = std::min(per_sm, c->p.pe_ctas_per_sm);
   *ctas = per_sm * c->prop.multiProcessorCount;
@@ -669,6 +681,27 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   M.se2 = p.sigma_noise * p.sigma_noise; M.inv_se2 = 1.0 / M.se2;
   M.log_se2 = log(M.se2); M.log_r = log(M.se2 / M.sq2);
   split_pair(M.mu_q, &M.mu_hi, &M.mu_lo); split_pair(M.se2 / M.sq2, &M.r_hi, &M.r_lo);
+  // charge components (the cumulative G is summed left to right, as the draw compares it)
+  M.n_comp = p.n_mix > 0 ? p.n_mix : 1;
+  M.cm_last = 0;
+  {
+    double cum = 0.0;
+    for (int e = 0; e < FSMP_MAX_MIX; ++e) {
+      const bool on = e < M.n_comp;
+      const double mu = p.n_mix > 0 ? p.mix_mu[e] : p.mu_q, sg = p.n_mix > 0 ? p.mix_sigma[e] : p.sigma_q;
+      const double G = p.n_mix > 0 ? p.mix_G[e] : 1.0;
+      M.cm_mu[e] = on ? mu : 0.0;
+      M.cm_q[e] = on ? sg * sg : 1.0;
+      M.cm_iq[e] = 1.0 / M.cm_q[e];
+      M.cm_r[e] = M.se2 / M.cm_q[e];
+      M.cm_lr[e] = log(M.cm_r[e]);
+      if (on) cum += G;
+      M.cm_cum[e] = on ? cum : 2.0;
+      if (on && G > 0.0) M.cm_last = e;
+      split_pair(M.cm_mu[e], &M.cm_mu_hi[e], &M.cm_mu_lo[e]);
+      split_pair(M.cm_r[e], &M.cm_r_hi[e], &M.cm_r_lo[e]);
+    }
+  }
   M.t0_lo = p.t0_lo; M.t0_hi = p.t0_hi; M.sample_t0 = p.sample_t0 ? 1 : 0;
   M.J = p.jump_J; M.log_J = log(p.jump_J);
   M.n_cap = p.n_cap;
@@ -747,7 +780,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   // slots for every shape the context may launch (both lane counts when the tuner picks it)
   if (p.kernel == FSMP_KERNEL_PE) {
     c->pe_warps = p.threads_per_chain > 0 ? std::min(4, p.threads_per_chain / 32) : 4;
-    const size_t esz = 8;  // C^-1 is FP64 in both modes
+    const size_t esz = pe_c_entry_bytes(p.precision);
     c->pe_tile = p.pe_tile > 0 ? std::min(p.pe_tile, p.n_cap) : std::min(p.n_cap, 32);
     c->pe_lanes = p.pe_lanes > 0 ? p.pe_lanes : 32;
     c->pe_lanes_free = p.pe_lanes == 0 && pe_lanes_ok(16, p.n_cap);

@@ -31,6 +31,7 @@ TRACE_DTYPE = np.dtype([("la0", "<f8"), ("lu0", "<f8"), ("la", "<f8"), ("lu", "<
                         ("flags", "<i4")])
 
 _c_double, _c_int, _c_u64, _vp = ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+MAX_MIX = 8  # FSMP_MAX_MIX
 
 
 class Params(ctypes.Structure):
@@ -45,7 +46,9 @@ class Params(ctypes.Structure):
                 ("refresh_every", _c_int), ("drift_tol", _c_double), ("kernel", _c_int),
                 ("threads_per_chain", _c_int), ("device_mem_budget", ctypes.c_size_t),
                 ("device", _c_int), ("max_queued", _c_int), ("n_streams", _c_int),
-                ("pe_tile", _c_int), ("pe_ctas_per_sm", _c_int), ("pe_lanes", _c_int)]
+                ("pe_tile", _c_int), ("pe_ctas_per_sm", _c_int), ("pe_lanes", _c_int),
+                ("n_mix", _c_int), ("mix_G", _c_double * MAX_MIX), ("mix_mu", _c_double * MAX_MIX),
+                ("mix_sigma", _c_double * MAX_MIX)]
 
 
 class Batch(ctypes.Structure):
@@ -154,18 +157,32 @@ _PARAM_DEFAULTS = dict(dt_sample_ns=1.0, grid_ns=0.25, ser_kind=0, ser_sigma=1.5
                        jump_J=0.25, n_cap=32, n_max=1024, precision=FP64, refresh_every=64,
                        drift_tol=0.0, kernel=KERNEL_AUTO, threads_per_chain=0,
                        device_mem_budget=0, device=0, max_queued=0, n_streams=0, pe_tile=0,
-                       pe_ctas_per_sm=0, pe_lanes=0)
+                       pe_ctas_per_sm=0, pe_lanes=0, n_mix=0)
+_MIX_KEYS = ("mix_G", "mix_mu", "mix_sigma")
 
 
 def make_params(d: dict | None = None, **kw) -> Params:
+    """fsmp_params from a dict (unknown keys are ignored). The MCP charge mixture is given as
+    lists ``mix_G``, ``mix_mu``, ``mix_sigma``; n_mix defaults to their length."""
     vals = dict(_PARAM_DEFAULTS)
+    mix = {}
     for src in (d or {}, kw):
         for k, v in src.items():
             if k in vals:
                 vals[k] = v
+            elif k in _MIX_KEYS and v is not None:
+                mix[k] = [float(x) for x in v]
+    if mix and not vals["n_mix"]:
+        vals["n_mix"] = len(mix["mix_G"])
+    if len(mix.get("mix_G", ())) > MAX_MIX:
+        raise ValueError("at most %d mixture components" % MAX_MIX)
     p = Params()
     for k, v in vals.items():
         setattr(p, k, v)
+    for k, v in mix.items():
+        arr = getattr(p, k)
+        for i, x in enumerate(v):
+            arr[i] = x
     return p
 
 

@@ -49,3 +49,35 @@ def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(fsmp, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         fsmp.load()
+
+
+def test_params_and_tune_layout_match_the_header(tmp_path):
+    """sizeof / offsetof of fsmp_params and fsmp_tune from the C compiler against the ctypes
+    mirrors the binding passes across the boundary."""
+    import subprocess
+    from paper_2403_03156_gb300 import fsmp
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "fsmp.h"\nint main(void) {\n'
+                   '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(fsmp_params), offsetof(fsmp_params, pe_lanes),\n'
+                   '         offsetof(fsmp_params, n_mix), offsetof(fsmp_params, mix_sigma), sizeof(fsmp_tune),\n'
+                   '         offsetof(fsmp_tune, lanes_per_chain));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    P, T = fsmp.Params, fsmp.Tune
+    assert got == [ctypes.sizeof(P), P.pe_lanes.offset, P.n_mix.offset, P.mix_sigma.offset, ctypes.sizeof(T),
+                   T.lanes_per_chain.offset]
+
+
+def test_create_rejects_bad_mixtures_without_a_gpu():
+    """fsmp_create validates before touching a device: G must sum to 1, sigma_e > 0, at most
+    FSMP_MAX_MIX components, and a mixture needs the PE-space kernel."""
+    from paper_2403_03156_gb300 import fsmp, workloads
+    base = dict(workloads.CONFIGS["plain_fp64_256x128"]["params"], n_max=128)
+    mix = dict(mix_G=[0.3, 0.7], mix_mu=[1.0, 2.0], mix_sigma=[0.3, 0.5])
+    bad = [dict(mix, mix_G=[0.3, 0.6]), dict(mix, mix_sigma=[0.3, 0.0]), dict(mix, kernel=fsmp.KERNEL_SMEM),
+           dict(mix, kernel=fsmp.KERNEL_PLAIN), dict(mix, n_mix=9)]
+    for extra in bad:
+        with pytest.raises(fsmp.FsmpError) as ei:
+            fsmp.Context(dict(base, **extra))
+        assert ei.value.code == fsmp.ERR_INVALID, extra
