@@ -47,6 +47,15 @@
  *      with the prior of Eq. (mcp-pzmu); an update with zero time shift and e+ = e- is the
  *      accepted no-op of R5, with e+ != e- it is a move. The charge summary of R8 becomes
  *      sum_k (mu_{e_k} + sigma_{e_k}^2 a_k^T Sigma^-1 y).
+ *   R10 LucyDDM (Sec. 2.3) runs on the sample grid with the kernel v(m) = V(m dt) / S,
+ *      m = 0 .. L_V-1, S = sum_m V(m dt) (the peak-normalised SER at the sample times, scaled
+ *      to unit sum), on the data d(t) = max(w(t), 0) / S -- Lucy's method needs non-negative
+ *      data, and the scaling makes q-hat a charge in units of the SER's. q-hat^0 is uniform
+ *      with the sum of d; a ratio d / w^r with w^r = 0 is taken as 0. The printed index
+ *      bounds of the w^r sum are garbled; w^r is the convolution sum over
+ *      tau = t - L_V + 1 .. t. Each tau with q-hat > thresh gives one initial PE at grid index
+ *      tau R; t0 starts at the first of them. A chain started from a given z (orc_batch.z_init)
+ *      gives its PEs the mixture's most probable component.
  */
 #include "fsmp_oracle.h"
 
@@ -475,6 +484,8 @@ typedef struct {
   double* occ;
   int occ_width;
   double* occ_e;
+  const int32_t* z_init; /* initial PE grid indices (NULL: empty) */
+  int n_init;
 } chain_in;
 
 typedef struct {
@@ -550,10 +561,28 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
   }
   int N = 0;
   int k0 = c->k0_init;
-  /* initial state (reading of Sec. 2.3 without the deconvolution): z empty */
+  /* initial state: empty z, or the given one (the LucyDDM state of Sec. 2.3, reading R10):
+   * at most n_cap PEs, each of the mixture's most probable component; Sigma^-1 built from the
+   * empty state by successive births (Eq. (12) with a_- = 0) */
+  if (c->z_init) {
+    int e0 = 0;
+    for (int e = 1; e < p->n_mix; ++e)
+      if (p->mix_G[e] > p->mix_G[e0]) e0 = e;
+    N = c->n_init;
+    if (N > p->n_cap) { N = p->n_cap; out->status |= ORC_ST_CAPACITY; }
+    for (int k = 0; k < N; ++k) { list[k] = c->z_init[k]; list_e[k] = e0; }
+    if (c->mode == ORC_MODE_INCREMENTAL && !p->prior_only)
+      for (int k = 0; k < N; ++k) {
+        double d;
+        for (int x = 0; x < n; ++x) st.am[x] = 0.0;
+        pe_vector(M, n, list[k], st.ap);
+        if (inc_delta_nu(&st, p, e0, e0, &d) != 0) { rc = ORC_ERR_INVALID; goto done; }
+        inc_accept(&st, p);
+      }
+  }
   double logp_cur = 0.0;
   if (c->mode == ORC_MODE_DEFINITION && !p->prior_only)
-    logp_cur = logp_def(M, c->w, n, list, list_e, 0, NULL, NULL, NULL);
+    logp_cur = logp_def(M, c->w, n, list, list_e, N, NULL, NULL, NULL);
 
   double sN = 0, sN2 = 0, st0 = 0, st02 = 0, sQ = 0, sQ2 = 0;
   double* hist = (double*)calloc((size_t)p->n_cap + 1, sizeof(double));
@@ -832,6 +861,78 @@ done:
 }
 
 /* ------------------------------------------------------------------------------------
+ * LucyDDM (Sec. 2.3, reading R10).
+ * ---------------------------------------------------------------------------------- */
+static int lucyddm(const model* M, const float* wv, int n, double t_origin, int n_iter, double thresh,
+                   double* q_out, int32_t* z_out, int z_cap, int32_t* n_z, int32_t* T_lo, int32_t* T_hi,
+                   double* t0_out) {
+  const int LV = M->Lt / M->R, nq = n + LV - 1;
+  double* v = (double*)malloc(sizeof(double) * LV);
+  double* d = (double*)malloc(sizeof(double) * n);
+  double* q = (double*)malloc(sizeof(double) * nq);
+  double* wr = (double*)malloc(sizeof(double) * n);
+  double* ratio = (double*)malloc(sizeof(double) * n);
+  if (!v || !d || !q || !wr || !ratio) {
+    free(v); free(d); free(q); free(wr); free(ratio);
+    return ORC_ERR_NOMEM;
+  }
+  /* kernel: the SER at the sample times, scaled to unit sum */
+  double S = 0.0;
+  for (int m = 0; m < LV; ++m) S += M->V[m * M->R];
+  for (int m = 0; m < LV; ++m) v[m] = M->V[m * M->R] / S;
+  double dsum = 0.0;
+  for (int t = 0; t < n; ++t) {
+    d[t] = wv[t] > 0.0f ? (double)wv[t] / S : 0.0;
+    dsum += d[t];
+  }
+  /* q[i] is q-hat(tau) at tau = i - (LV - 1); q-hat^0 uniform with the sum of d */
+  for (int i = 0; i < nq; ++i) q[i] = dsum / nq;
+  for (int r = 0; r < n_iter; ++r) {
+    /* w^r(t) = sum_{tau = t - LV + 1}^{t} q-hat(tau) v(t - tau) */
+    for (int t = 0; t < n; ++t) {
+      double s = 0.0;
+      for (int m = 0; m < LV; ++m) s += q[t - m + (LV - 1)] * v[m];
+      wr[t] = s;
+      ratio[t] = s > 0.0 ? d[t] / s : 0.0;
+    }
+    /* q-hat(tau) *= sum_{t = max(tau, 0)}^{min(n - 1, tau + LV - 1)} ratio(t) v(t - tau) */
+    for (int i = 0; i < nq; ++i) {
+      const int tau = i - (LV - 1);
+      double s = 0.0;
+      for (int m = 0; m < LV; ++m) {
+        const int t = tau + m;
+        if (t >= 0 && t < n) s += ratio[t] * v[m];
+      }
+      q[i] *= s;
+    }
+  }
+  if (q_out) memcpy(q_out, q, sizeof(double) * nq);
+  /* initial PEs, solution space and t0 (Sec. 2.3) */
+  int cnt = 0, tmin = 0, tmax = 0;
+  for (int i = 0; i < nq; ++i) {
+    if (!(q[i] > thresh)) continue;
+    const int tau = i - (LV - 1);
+    if (cnt == 0) tmin = tau;
+    tmax = tau;
+    if (cnt < z_cap) z_out[cnt] = tau * M->R;
+    ++cnt;
+  }
+  *n_z = cnt;
+  if (cnt == 0) {
+    *T_lo = 0;
+    *T_hi = n * M->R;
+    *t0_out = NAN;
+  } else {
+    const double dt = M->p->dt_sample_ns, g = M->g;
+    *T_lo = (int32_t)floor((tmin * dt - 4.0) / g + 1e-9);
+    *T_hi = (int32_t)ceil((tmax * dt + 4.0) / g - 1e-9) + 1;
+    *t0_out = t_origin + tmin * dt;
+  }
+  free(v); free(d); free(q); free(wr); free(ratio);
+  return LV;
+}
+
+/* ------------------------------------------------------------------------------------
  * Batch plumbing.
  * ---------------------------------------------------------------------------------- */
 static int check_params(const orc_params* p) {
@@ -887,6 +988,13 @@ static int make_chain_in(const orc_params* p, const model* M, const orc_batch* b
   c->occ = b->occ ? b->occ + (size_t)i * b->occ_width : NULL;
   c->occ_width = b->occ_width;
   c->occ_e = b->occ_e ? b->occ_e + (size_t)i * (p->n_mix > 1 ? p->n_mix : 1) : NULL;
+  c->z_init = NULL;
+  c->n_init = 0;
+  if (b->z_init) {
+    if (!b->n_init || b->n_init[i] < 0 || b->n_init[i] > b->z_stride) return ORC_ERR_INVALID;
+    c->z_init = b->z_init + (size_t)i * b->z_stride;
+    c->n_init = b->n_init[i];
+  }
   return 0;
 }
 
@@ -1102,4 +1210,18 @@ int orc_delta_nu_e(const orc_params* p, const float* w, int n, const int32_t* j,
 int orc_delta_nu(const orc_params* p, const float* w, int n, const int32_t* j, int N,
                  int kind, int k, int jp, int mode, double* dnu_out) {
   return orc_delta_nu_e(p, w, n, j, NULL, N, kind, k, jp, 0, mode, dnu_out);
+}
+
+int orc_lucyddm(const orc_params* p, const float* w, int n, double t_origin, int n_iter, double thresh,
+                double* q_out, int32_t* z_out, int z_cap, int32_t* n_z, int32_t* T_lo, int32_t* T_hi,
+                double* t0_out) {
+  if (!w || n < 1 || n_iter < 0 || z_cap < 0 || (z_cap > 0 && !z_out) || !n_z || !T_lo || !T_hi || !t0_out)
+    return ORC_ERR_INVALID;
+  model M;
+  double* V = NULL;
+  int rc = build_model(p, &M, &V);
+  if (rc) return rc;
+  rc = lucyddm(&M, w, n, t_origin, n_iter, thresh, q_out, z_out, z_cap, n_z, T_lo, T_hi, t0_out);
+  free(V);
+  return rc;
 }

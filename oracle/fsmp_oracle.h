@@ -18,6 +18,7 @@
  *   SER and phi               Sec. 3 (SER formula; LS two-exponential phi)
  *   marginal likelihood       Appendix A.1, Eq. (mgauss) and the log-density below it
  *   rank-2 jump, Woodbury     Appendix A.1, Eqs. (11), (12), (14), (DeltaU), (16)-(18)
+ *   LucyDDM initial state     Sec. 2.3 (Lucy's iteration, the solution space T, initial z, t0)
  *   MCP charge model          Eq. (mcp-multi-norm) (Sec. 2.1), Eq. (mcp) (Sec. 2.4),
  *                             Eq. (mcp-pzmu) and the redefined U, Sigma, Lambda (Appendix A.2)
  *
@@ -102,6 +103,10 @@ typedef struct {
   int occ_width;
   double* occ_e;           /* optional [n_waveforms * max(n_mix, 1)]: time-averaged number of PEs
                               of each MCP component after burn-in */
+  const int32_t* z_init;   /* optional [n_waveforms * z_stride]: initial PE grid indices (the
+                              LucyDDM initial state, Sec. 2.3); NULL starts from an empty z */
+  const int32_t* n_init;   /* their counts (required with z_init) */
+  int z_stride;
 } orc_batch;
 
 /* Philox4x64-10 block function. */
@@ -136,6 +141,19 @@ int orc_delta_nu(const orc_params* p, const float* w, int n, const int32_t* j, i
 /* The same with PE components e[0..N) (NULL: all 0) and the component ep of the new PE. */
 int orc_delta_nu_e(const orc_params* p, const float* w, int n, const int32_t* j, const int32_t* e, int N,
                    int kind, int k, int jp, int ep, int mode, double* dnu_out);
+
+/* LucyDDM (Sec. 2.3): Lucy's iterative deconvolution of one waveform w[0..n) by the SER
+ * sampled at the waveform's sample times, then the solution space and initial state.
+ *  - q_out [n + L_V - 1] (may be NULL): q^(n_iter)(tau) for tau = -L_V+1 .. n-1;
+ *  - z_out [z_cap]: grid indices tau R of the taus with q > thresh (at most z_cap; *n_z gets
+ *    the number found, which may exceed z_cap);
+ *  - *T_lo, *T_hi: the solution space [t_min - 4 ns, t_max + 4 ns] on the PE grid (T_hi
+ *    exclusive), the whole window [0, n R) when no tau passes;
+ *  - *t0_out: t_origin + t_min (NaN when none passes).
+ * Returns L_V, or a negative error. */
+int orc_lucyddm(const orc_params* p, const float* w, int n, double t_origin, int n_iter, double thresh,
+                double* q_out, int32_t* z_out, int z_cap, int32_t* n_z, int32_t* T_lo, int32_t* T_hi,
+                double* t0_out);
 
 /* Run the chains of a batch; n_threads <= 0 uses one thread. trace: [n_waveforms*n_steps]
  * or NULL. Returns 0 or a negative error. */

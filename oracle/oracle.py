@@ -65,7 +65,8 @@ class OrcBatch(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("index_base", ctypes.c_uint64),
                 ("wf_ids", ctypes.c_void_p), ("n_steps", ctypes.c_int), ("burn_in", ctypes.c_int),
                 ("forced", ctypes.c_void_p), ("occ", ctypes.c_void_p),
-                ("occ_width", ctypes.c_int), ("occ_e", ctypes.c_void_p)]
+                ("occ_width", ctypes.c_int), ("occ_e", ctypes.c_void_p),
+                ("z_init", ctypes.c_void_p), ("n_init", ctypes.c_void_p), ("z_stride", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -121,6 +122,10 @@ def lib():
         L.orc_run_batch.restype = ctypes.c_int
         L.orc_run_batch.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcBatch),
                                     ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_lucyddm.restype = ctypes.c_int
+        L.orc_lucyddm.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_lambda_mle.restype = ctypes.c_double
         L.orc_lambda_mle.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_run_chain_state.restype = ctypes.c_int
@@ -277,6 +282,8 @@ class _BatchKeep:
         self.t0_init = f("t0_init", np.float64)
         self.forced = f("forced", np.uint8)
         self.wf_ids = f("wf_ids", np.uint64)
+        self.z_init = f("z_init", np.int32)
+        self.n_init = f("n_init", np.int32)
         b = OrcBatch()
         b.n_waveforms = len(self.offsets) - 1
         b.samples = _ptr(self.samples)
@@ -292,6 +299,10 @@ class _BatchKeep:
         b.n_steps = int(batch["n_steps"])
         b.burn_in = int(batch.get("burn_in", 0))
         b.forced = _ptr(self.forced)
+        if self.z_init is not None:
+            b.z_init = _ptr(self.z_init)
+            b.n_init = _ptr(self.n_init)
+            b.z_stride = int(self.z_init.shape[1]) if self.z_init.ndim == 2 else int(batch["z_stride"])
         self.occ = None
         if batch.get("occ_width"):
             self.occ = np.zeros((b.n_waveforms, int(batch["occ_width"])), np.float64)
@@ -349,3 +360,24 @@ def run_chain_state(params, batch, mode=MODE_INCREMENTAL):
         raise ValueError("orc_run_chain_state failed: %d" % rc)
     return dict(summary=out[0], trace=tr, z=lst[:N[0]].copy(), e=lst_e[:N[0]].copy(), N=int(N[0]),
                 k0=int(k0[0]), sinv=sinv, y=y, logdet=float(ld[0]))
+
+
+def lucyddm(params, w, n_iter=2000, thresh=0.1, t_origin=0.0, z_cap=None):
+    """LucyDDM of one waveform (Sec. 2.3). Returns dict(q, z, n_z, T_lo, T_hi, t0): q-hat for
+    tau = -L_V+1 .. n-1, the initial PE grid indices, the solution space and t0."""
+    p = make_params(params)
+    w = np.ascontiguousarray(w, np.float32)
+    n = len(w)
+    nq_max = n + 4096
+    q = np.zeros(nq_max, np.float64)
+    cap = int(z_cap if z_cap is not None else n + 4096)
+    z = np.zeros(max(cap, 1), np.int32)
+    nz, tlo, thi = np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32)
+    t0 = np.zeros(1, np.float64)
+    LV = lib().orc_lucyddm(ctypes.byref(p), w.ctypes.data, n, float(t_origin), int(n_iter), float(thresh),
+                           q.ctypes.data, z.ctypes.data, cap, nz.ctypes.data, tlo.ctypes.data, thi.ctypes.data,
+                           t0.ctypes.data)
+    if LV < 0:
+        raise ValueError("orc_lucyddm failed: %d" % LV)
+    return dict(q=q[:n + LV - 1].copy(), L_V=LV, z=z[:min(int(nz[0]), cap)].copy(), n_z=int(nz[0]),
+                T_lo=int(tlo[0]), T_hi=int(thi[0]), t0=float(t0[0]))
