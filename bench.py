@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered events/s (0: the workload's)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the arrival stream")
     ap.add_argument("--serve-pool", type=int, default=1024, help="serving: distinct events replayed by the stream")
+    ap.add_argument("--stage", default="chain", choices=["chain", "lucyddm"],
+                    help="lucyddm: time the LucyDDM deconvolution (Sec. 2.3) of the workload instead of the chains")
+    ap.add_argument("--lucy-iters", type=int, default=2000, help="lucyddm stage: Lucy iterations")
     return ap.parse_args()
 
 
@@ -572,9 +575,95 @@ def run_serving(args):
         dist.destroy_process_group()
 
 
+def run_lucyddm_stage(args):
+    """LucyDDM (Sec. 2.3) of every waveform of the workload: waveforms/s on one GPU, the FP32
+    FMA roofline of the deconvolution, the oracle on the host cores, and an end-to-end time with
+    the samples copied in and the initial states copied out."""
+    import torch
+    from paper_2403_03156_gb300 import build, fsmp, workloads
+    from oracle import oracle as orc
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = workloads.make_workload(args.workload, n_waveforms=args.n_waveforms or None, seed=args.seed)
+    b = wl["batch"]
+    W = len(b["offsets"]) - 1
+    lengths = np.diff(b["offsets"])
+    n_max = int(max(lengths.max(), 64))
+    ctx = fsmp.Context(dict(wl["params"], n_max=n_max, kernel=fsmp.KERNEL_PE))
+    info, peaks = ctx.info(), ctx.measure_peaks()
+    L_V = info["L_V"]
+    t = {"samples": torch.from_numpy(b["samples"]).to(dev),
+         "offsets": torch.from_numpy(b["offsets"].astype(np.int32)).to(dev),
+         "t_origin_ns": torch.from_numpy(b["t_origin_ns"]).to(dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        ctx.lucyddm(t, n_iter=args.lucy_iters)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.lucyddm(t, n_iter=args.lucy_iters)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    n_init = r["n_init"].cpu().numpy()
+    # algorithmic FLOPs: per iteration and waveform, n outputs of w^r and n + L_V - 1 of the
+    # q-hat update, L_V taps each, one FMA (2 FLOPs) per tap
+    flops = 2.0 * L_V * float(np.sum(2 * lengths + L_V - 1)) * args.lucy_iters
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {"metric": "LucyDDM waveforms/s (%d iterations)" % args.lucy_iters, "value": W / (ms * 1e-3),
+            "unit": "waveforms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "stage": "lucyddm", "n_waveforms": W, "L_V": L_V,
+                       "window_samples": [int(lengths.min()), int(np.median(lengths)), int(lengths.max())],
+                       "mean_initial_pes": float(n_init.mean()), "mean_true_pes": float(wl["truth"]["N"].mean()),
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp32_tflops"], "traffic": None,
+                         "peak_source": "measured live: fsmp_measure_peaks (FP32 FMA)",
+                         "kernel": "lucy_kernel, one launch (%d waveforms)" % W},
+            "gpu_launches": args.steps, "clocks": clk, "peaks_measured": peaks}
+    if not args.no_e2e:
+        host = torch.from_numpy(b["samples"]).pin_memory()
+        e2e = []
+        for i in range(1 + min(args.steps, 3)):
+            t1 = time.perf_counter()
+            t["samples"] = host.to(dev, non_blocking=True)
+            r = ctx.lucyddm(t, n_iter=args.lucy_iters)
+            outs = [r[k].cpu() for k in ("T_lo", "T_hi", "t0_init", "z_init", "n_init")]
+            if i > 0:
+                e2e.append(time.perf_counter() - t1)
+        d2h = sum(o.numel() * o.element_size() for o in outs)
+        line["e2e"] = {"value": W / statistics.mean(e2e), "unit": "waveforms/s", "h2d_bytes_per_step": int(host.numel() * 4),
+                       "d2h_bytes_per_step": int(d2h), "steps": len(e2e)}
+    if not args.no_cpu_baseline:
+        rng = np.random.default_rng(0)
+        idx = rng.permutation(W)
+        t1, k = time.perf_counter(), 0
+        while k < W and time.perf_counter() - t1 < args.cpu_seconds:
+            i = int(idx[k])
+            orc.lucyddm(wl["params"], b["samples"][b["offsets"][i]:b["offsets"][i + 1]], n_iter=args.lucy_iters)
+            k += 1
+        el = time.perf_counter() - t1
+        line["cpu_baseline"] = {"value": k / el, "unit": "waveforms/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d random waveforms of %s, %d iterations, FP64, one thread, %.1f s"
+                                          % (k, args.workload, args.lucy_iters, el)}
+    ctx.close()
+    emit(line)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.stage == "lucyddm":
+        run_lucyddm_stage(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif serving_workload(args.workload):
         run_serving(args)

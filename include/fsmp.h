@@ -200,7 +200,44 @@ typedef struct {
   const uint64_t* wf_ids;        /* may be NULL */
   fsmp_summary* out;
   fsmp_trace* trace;             /* may be NULL */
+  /* Initial state (may be NULL; FSMP_KERNEL_PE only): waveform i starts from the PEs
+   * z_init[i * z_stride + k], k < min(n_init[i], z_stride) (grid indices, as LucyDDM gives
+   * them, Sec. 2.3) instead of an empty z. More than n_cap PEs are cut to n_cap and flagged
+   * FSMP_ST_CAPACITY. With the MCP mixture each starts as the most probable component. */
+  const int32_t* z_init;
+  const int32_t* n_init;
+  int z_stride;
 } fsmp_device_batch;
+
+/* LucyDDM (Sec. 2.3): Lucy's iterative deconvolution of each waveform of a device batch by
+ * the SER at the sample times, v(m) = V(m dt) / S (m < L_V, S = sum_m V(m dt)), of the data
+ * d(t) = max(w(t), 0) / S, from a uniform start with the sum of d, for n_iter iterations
+ * (FP32). The taus with q-hat(tau) > thresh give the initial PEs at grid indices tau R, the
+ * solution space T = [t_min - 4 ns, t_max + 4 ns] on the PE grid, and t0 = t_origin + t_min --
+ * the inputs T_lo, T_hi, t0_init, z_init, n_init of a fsmp_device_batch. A waveform with no
+ * such tau gets n_init = 0, T = [0, n R) and t0_init = NaN (the paper leaves it out). Every
+ * pointer is device memory; samples / offsets as in fsmp_device_batch with offsets[0] = 0. */
+typedef struct {
+  int n_waveforms, n_max_hint;   /* n_max_hint: longest window (0: params.n_max)             */
+  const float* samples;
+  const int32_t* offsets;
+  const double* t_origin_ns;     /* may be NULL (0)                                          */
+  int n_iter;                    /* Lucy iterations (the paper: 2000)                        */
+  double thresh;                 /* initial-PE threshold on q-hat (the paper: 0.1)           */
+  float* q_out;                  /* may be NULL; else q-hat of waveform i, tau = -L_V+1 .. n-1,
+                                    at q_out[offsets[i] + i (L_V - 1)]                       */
+  int32_t* T_lo;                 /* [n_waveforms]                                            */
+  int32_t* T_hi;                 /* [n_waveforms] (exclusive)                                */
+  double* t0_init;               /* [n_waveforms]                                            */
+  int32_t* z_init;               /* [n_waveforms * z_stride] (may be NULL if z_stride = 0)   */
+  int32_t* n_init;               /* [n_waveforms]: taus found (only z_stride are stored)     */
+  int z_stride;
+  int32_t* status;               /* [n_waveforms]: 0, or FSMP_ST_INVALID (empty or too long)  */
+} fsmp_lucy_batch;
+
+/* Run LucyDDM on `stream` (asynchronous). Returns FSMP_OK, FSMP_ERR_INVALID (bad arguments,
+ * window longer than params.n_max or than shared memory allows) or FSMP_ERR_CUDA. */
+int fsmp_lucyddm(fsmp_ctx* ctx, const fsmp_lucy_batch* batch, void* stream);
 
 /* Library and device facts, and the launch shape chosen for each kernel form. */
 typedef struct {

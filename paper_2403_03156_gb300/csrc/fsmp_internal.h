@@ -30,6 +30,7 @@ struct DevModel {
   // its inverse cm_iq, cm_r = sigma_eps^2 / cm_q and its log, cumulative probability
   // G(0) + .. + G(e), and the float pairs of cm_mu and cm_r.
   int n_comp, cm_last;        // components; the last one with G > 0
+  int cm_mode;                // the most probable component (of an initial PE)
   double cm_mu[FSMP_MAX_MIX], cm_q[FSMP_MAX_MIX], cm_iq[FSMP_MAX_MIX], cm_r[FSMP_MAX_MIX], cm_lr[FSMP_MAX_MIX];
   double cm_cum[FSMP_MAX_MIX];
   float cm_mu_hi[FSMP_MAX_MIX], cm_mu_lo[FSMP_MAX_MIX], cm_r_hi[FSMP_MAX_MIX], cm_r_lo[FSMP_MAX_MIX];
@@ -83,6 +84,9 @@ struct BatchView {
   const int32_t* order;        // may be null: processing order (a permutation of waveforms)
   fsmp_summary* out;
   fsmp_trace* trace;           // may be null
+  const int32_t* z_init;       // may be null: initial PEs, waveform i at z_init[i * z_stride]
+  const int32_t* n_init;
+  int z_stride;
 };
 
 // Philox4x64-10 (Salmon et al., SC'11): two 64x64->128 multiplies per round, Weyl key bumps.
@@ -247,6 +251,15 @@ bool pe_lanes_ok(int lanes, int n_cap);
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
                       void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
                       cudaStream_t st);
+// LucyDDM (fsmp_lucy.cu): shared memory per CTA for windows up to n_alloc; the kernel taps
+// v(m) = V(m dt) / S, padded to whole groups of four, and S; the deconvolution launch.
+size_t lucy_smem_bytes(int LV, int n_alloc);
+cudaError_t lucy_kernel_attributes(int max_smem);
+cudaError_t launch_lucy_taps(const float* V32, int LV, int R, float* v4, float* S_dev, cudaStream_t st);
+cudaError_t launch_lucy(const float* v4, float S, int LV, int R, double dt, double g, int n_waveforms, int n_alloc,
+                        const float* samples, const int32_t* offsets, const double* t_origin, int n_iter, float thresh,
+                        float* q_out, int32_t* T_lo, int32_t* T_hi, double* t0, int32_t* z, int32_t* n_z, int z_stride,
+                        int* status, cudaStream_t st);
 // Set (or, with what == nullptr, clear) the calling thread's fsmp_last_error() message.
 void record_error(const char* what, const char* detail);
 

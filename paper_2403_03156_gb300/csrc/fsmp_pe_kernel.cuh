@@ -898,7 +898,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     fsmp_summary* out = B.out + wi;
     fsmp_trace* trace = B.trace ? B.trace + (B.trace_off ? B.trace_off[wi] : (int64_t)wi * n_steps) : nullptr;
     const bool invalid = n < 1 || n > n_alloc || T_hi <= T_lo || k0_hi < k0_lo || !(lambda0 > 0.0) || n_steps < 0 ||
-                         burn_in < 0 || (fp32 && ws == nullptr) || k0_hi - k0_lo + 1 > M.win_extra ||
+                         burn_in < 0 || ((fp32 || B.z_init) && ws == nullptr) || k0_hi - k0_lo + 1 > M.win_extra ||
                          (Cg == nullptr && Ns < n_cap);
     if (invalid) {
       if (ln.sl == 0) {
@@ -955,6 +955,44 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     C* Cp = Ns > 0 ? W.Cs : Cg;  // C^-1 (packed), room for cap PEs
     int cap = Ns > 0 ? Ns : n_cap;
     int N = 0;
+    if (B.z_init) {
+      // a given initial state (LucyDDM, Sec. 2.3): the PE list, each PE of the most probable
+      // component, then C^-1, v, y, log|Sigma| and log L from it by the FP64 rebuild
+      int ni = min(B.n_init[wi], B.z_stride);
+      const bool cut = ni > n_cap;
+      if (cut) ni = n_cap;
+      for (int k = ln.sl; k < ni; k += L) {
+        W.list[k] = B.z_init[(size_t)wi * B.z_stride + k];
+        if constexpr (MIX) W.le[k] = (unsigned char)M.cm_mode;
+      }
+      __syncwarp(ln.gm);
+      if (ni > cap) { Cp = Cg; cap = n_cap; }
+      if (ni > 0) {
+        const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, ni, ln);
+        C qs = czero<C>();
+        double ms = 0.0;
+        for (int i = ln.sl; i < ni; i += L) {
+          qs = cadd(qs, W.v[i]);
+          if (mix) ms += M.cm_mu[W.le[i]];
+        }
+        qs = csum(qs, ln);
+        ms = mix ? wsum(ms, ln) : ni * M.cm_mu[0];
+        if (ro.ok) {
+          N = ni;
+        } else {  // C not numerically positive definite: start empty
+          for (int x = ln.sl; x < n; x += L) W.y[x] = (T)w[x];
+        }
+        if (ln.sl == 0) {
+          if (ro.ok) {
+            S.logdet = ro.logdet; S.logL = ro.logL; S.q_cur = ms + c64(qs);
+          } else {
+            S.status |= FSMP_ST_BADDET;
+          }
+        }
+      }
+      if (ln.sl == 0 && cut) S.status |= FSMP_ST_CAPACITY;
+      __syncwarp(ln.gm);
+    }
 
     for (int step = 0; step < n_steps; ++step) {
       // ---- random draws of the next L steps: lane l takes step step + l

@@ -100,6 +100,10 @@ struct fsmp_ctx {
   double* tc64 = nullptr;
   float* tc32 = nullptr;
   float* tcff = nullptr;
+  // LucyDDM: the kernel taps v(m) = V(m dt) / S (padded to groups of four) and S
+  float* lucy_v4 = nullptr;
+  float* lucy_S_dev = nullptr;
+  float lucy_S = 0.0f;
   struct PeSet {
     void* cinv = nullptr;    // C^-1 slots
     double* ws = nullptr;    // FP64 refresh workspace slots
@@ -210,6 +214,7 @@ void free_ctx(fsmp_ctx* c) {
   cudaFree(c->scan); cudaFree(c->Lt_dev); cudaFree(c->gscratch);
   cudaFree(c->phi32); cudaFree(c->logphi32); cudaFree(c->cphi32); cudaFree(c->rscratch);
   cudaFree(c->tc64); cudaFree(c->tc32); cudaFree(c->tcff);
+  cudaFree(c->lucy_v4); cudaFree(c->lucy_S_dev);
   for (auto& ps : c->pe_sets) { cudaFree(ps.cinv); cudaFree(ps.ws); cudaFree(ps.hist); cudaFree(ps.counter); }
   for (auto s : c->streams) cudaStreamDestroy(s);
   if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
@@ -684,6 +689,9 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   // charge components (the cumulative G is summed left to right, as the draw compares it)
   M.n_comp = p.n_mix > 0 ? p.n_mix : 1;
   M.cm_last = 0;
+  M.cm_mode = 0;
+  for (int e = 1; e < p.n_mix; ++e)
+    if (p.mix_G[e] > p.mix_G[M.cm_mode]) M.cm_mode = e;
   {
     double cum = 0.0;
     for (int e = 0; e < FSMP_MAX_MIX; ++e) {
@@ -746,10 +754,16 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     CK(cudaDeviceSynchronize());
     M.tc64 = c->tc64; M.tc32 = c->tc32; M.tcff = c->tcff; M.tcM = xcorr_rows(M.Lt, M.R);
   }
+  // LucyDDM taps
+  CK(cudaMalloc((void**)&c->lucy_v4, sizeof(float) * 4 * ((M.L_V + 3) / 4)));
+  CK(cudaMalloc((void**)&c->lucy_S_dev, sizeof(float)));
+  CK(launch_lucy_taps(c->V32, M.L_V, M.R, c->lucy_v4, c->lucy_S_dev, 0));
+  CK(cudaMemcpy(&c->lucy_S, c->lucy_S_dev, sizeof(float), cudaMemcpyDeviceToHost));
   c->n_smem_max = smem_n_max(c.get());
   int max_smem = (int)c->prop.sharedMemPerBlockOptin;
   CK(chain_kernel_attributes(p.precision, true, max_smem));
   CK(chain_kernel_attributes(p.precision, false, max_smem));
+  CK(lucy_kernel_attributes(max_smem));
   if (p.precision != FSMP_FP64) {
     CK(chain_kernel_attributes(FSMP_FP64, false, max_smem));
   }
@@ -800,7 +814,9 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     if (slots < 1) FAIL(FSMP_ERR_INVALID, "n_max too large for the PE-space kernel");
     c->pe_slots = slots;
     c->pe_c_stride = c->pe_tile < p.n_cap ? pe_c_entries(p.n_cap) : 0;
-    c->pe_ws_stride = p.precision == FSMP_FP64 ? 0 : pe_ws_slot_doubles(p.n_cap, p.n_max);
+    // the FP64 rebuild runs in FP32 mode every K accepts, and in both modes for a chain that
+    // starts from a given z
+    c->pe_ws_stride = pe_ws_slot_doubles(p.n_cap, p.n_max);
     for (int i = 0; i <= p.n_streams; ++i) {
       fsmp_ctx::PeSet ps;
       const size_t cb = c->pe_c_stride * esz * (size_t)slots, wb = c->pe_ws_stride * 8 * (size_t)slots;
@@ -904,8 +920,32 @@ int fsmp_run_device(fsmp_ctx* c, const fsmp_device_batch* b, void* stream) {
   B.samples = b->samples; B.offsets = b->offsets; B.lambda0 = b->lambda0; B.t_origin = b->t_origin_ns;
   B.T_lo = b->T_lo; B.T_hi = b->T_hi; B.t0_init = b->t0_init; B.wf_ids = b->wf_ids;
   B.out = b->out; B.trace = b->trace;
+  if (b->z_init) {
+    if (!b->n_init || b->z_stride < 1) FAIL(FSMP_ERR_INVALID, "z_init needs n_init and z_stride >= 1");
+    if (c->p.kernel != FSMP_KERNEL_PE) FAIL(FSMP_ERR_INVALID, "an initial z needs the PE-space kernel");
+    B.z_init = b->z_init; B.n_init = b->n_init; B.z_stride = b->z_stride;
+  }
   { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   return run_view(c, B, (cudaStream_t)stream, (int)c->streams.size());
+}
+
+int fsmp_lucyddm(fsmp_ctx* c, const fsmp_lucy_batch* b, void* stream) {
+  g_last_error[0] = 0;
+  if (!c || !b || b->n_waveforms < 0 || !b->samples || !b->offsets || b->n_iter < 0 || !b->T_lo || !b->T_hi ||
+      !b->t0_init || !b->n_init || !b->status || b->z_stride < 0 || (b->z_stride > 0 && !b->z_init))
+    FAIL(FSMP_ERR_INVALID, "fsmp_lucyddm: bad arguments");
+  const int n_alloc = b->n_max_hint > 0 ? b->n_max_hint : c->p.n_max;
+  if (n_alloc > c->p.n_max) FAIL(FSMP_ERR_INVALID, "fsmp_lucyddm: window longer than n_max");
+  if (lucy_smem_bytes(c->M.L_V, n_alloc) > (size_t)c->prop.sharedMemPerBlockOptin)
+    FAIL(FSMP_ERR_INVALID, "fsmp_lucyddm: window too long for shared memory");
+  { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
+  cudaError_t e = launch_lucy(c->lucy_v4, c->lucy_S, c->M.L_V, c->M.R, c->M.dt, c->M.g, b->n_waveforms, n_alloc,
+                              b->samples, b->offsets, b->t_origin_ns, b->n_iter, (float)b->thresh, b->q_out, b->T_lo,
+                              b->T_hi, b->t0_init, b->z_init, b->n_init, b->z_stride, b->status,
+                              (cudaStream_t)stream);
+  c->n_launches++;
+  if (e != cudaSuccess) { set_error("launch_lucy", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
+  return FSMP_OK;
 }
 
 int fsmp_gelman_rubin(const fsmp_summary* chains, int m, int field, double* rhat) {

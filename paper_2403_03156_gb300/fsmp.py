@@ -69,7 +69,14 @@ class DeviceBatch(ctypes.Structure):
                 ("n_max_hint", _c_int), ("seed", _c_u64), ("index_base", _c_u64),
                 ("samples", _vp), ("offsets", _vp), ("lambda0", _vp), ("t_origin_ns", _vp),
                 ("T_lo", _vp), ("T_hi", _vp), ("t0_init", _vp), ("wf_ids", _vp), ("out", _vp),
-                ("trace", _vp)]
+                ("trace", _vp), ("z_init", _vp), ("n_init", _vp), ("z_stride", _c_int)]
+
+
+class LucyBatch(ctypes.Structure):
+    _fields_ = [("n_waveforms", _c_int), ("n_max_hint", _c_int), ("samples", _vp), ("offsets", _vp),
+                ("t_origin_ns", _vp), ("n_iter", _c_int), ("thresh", _c_double), ("q_out", _vp),
+                ("T_lo", _vp), ("T_hi", _vp), ("t0_init", _vp), ("z_init", _vp), ("n_init", _vp),
+                ("z_stride", _c_int), ("status", _vp)]
 
 
 class Tune(ctypes.Structure):
@@ -89,7 +96,7 @@ class Info(ctypes.Structure):
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
            "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc", "fsmp_autotune",
-           "fsmp_gelman_rubin"]
+           "fsmp_gelman_rubin", "fsmp_lucyddm"]
 
 _lib = None
 
@@ -117,6 +124,7 @@ def load(build_if_missing: bool = False):
     L.fsmp_run_device_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(DeviceBatch), _vp]
     L.fsmp_autotune.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _c_int, _c_int, ctypes.POINTER(Tune)]
     L.fsmp_gelman_rubin.argtypes = [_vp, _c_int, _c_int, ctypes.POINTER(_c_double)]
+    L.fsmp_lucyddm.argtypes = [_vp, ctypes.POINTER(LucyBatch), _vp]
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
     L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
     L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
@@ -301,8 +309,40 @@ class Context:
         b.samples, b.offsets, b.lambda0, b.t_origin_ns = p("samples"), p("offsets"), p("lambda0"), p("t_origin_ns")
         b.T_lo, b.T_hi, b.t0_init, b.wf_ids = p("T_lo"), p("T_hi"), p("t0_init"), p("wf_ids")
         b.out, b.trace = p("out"), p("trace")
+        _set_z_init(b, dev)
         st = None if stream is None else int(stream.cuda_stream)
         _check(load().fsmp_run_device(self.h, ctypes.byref(b), st), "fsmp_run_device")
+
+    def lucyddm(self, dev: dict, n_iter: int = 2000, thresh: float = 0.1, z_stride: int = 0, with_q: bool = False,
+                n_max_hint: int = 0, stream=None) -> dict:
+        """fsmp_lucyddm (Sec. 2.3) on device tensors (samples f32, offsets i32, optional
+        t_origin_ns f64). Returns torch tensors on the same device: T_lo, T_hi (i32), t0_init
+        (f64), z_init (i32, [n, z_stride]; z_stride defaults to n_cap), n_init, status (i32)
+        and, with ``with_q``, q (f32, waveform i at offsets[i] + i (L_V - 1)) -- ready to pass
+        to run_device as an initial state."""
+        import torch
+        W = int(dev["offsets"].numel()) - 1
+        zs = int(z_stride or self.params.n_cap)
+        d = dev["offsets"].device
+        out = dict(T_lo=torch.zeros(W, dtype=torch.int32, device=d), T_hi=torch.zeros(W, dtype=torch.int32, device=d),
+                   t0_init=torch.zeros(W, dtype=torch.float64, device=d),
+                   z_init=torch.zeros((W, zs), dtype=torch.int32, device=d),
+                   n_init=torch.zeros(W, dtype=torch.int32, device=d), status=torch.zeros(W, dtype=torch.int32, device=d))
+        if with_q:
+            L_V = self.info()["L_V"]
+            out["q"] = torch.zeros(int(dev["samples"].numel()) + W * (L_V - 1), dtype=torch.float32, device=d)
+        b = LucyBatch()
+        b.n_waveforms, b.n_max_hint = W, int(n_max_hint)
+        b.samples, b.offsets = dev["samples"].data_ptr(), dev["offsets"].data_ptr()
+        b.t_origin_ns = dev["t_origin_ns"].data_ptr() if dev.get("t_origin_ns") is not None else None
+        b.n_iter, b.thresh = int(n_iter), float(thresh)
+        b.q_out = out["q"].data_ptr() if with_q else None
+        b.T_lo, b.T_hi, b.t0_init = out["T_lo"].data_ptr(), out["T_hi"].data_ptr(), out["t0_init"].data_ptr()
+        b.z_init, b.n_init, b.z_stride = out["z_init"].data_ptr(), out["n_init"].data_ptr(), zs
+        b.status = out["status"].data_ptr()
+        st = None if stream is None else int(stream.cuda_stream)
+        _check(load().fsmp_lucyddm(self.h, ctypes.byref(b), st), "fsmp_lucyddm")
+        return out
 
     def autotune(self, dev: dict, sample: int = 8192, trial_steps: int = 128, n_steps: int = 0, seed: int = 0,
                  n_max_hint: int = 0) -> dict:
@@ -360,7 +400,18 @@ def _device_batch(dev, n_steps, burn_in, seed, index_base, n_max_hint):
     b.samples, b.offsets, b.lambda0, b.t_origin_ns = p("samples"), p("offsets"), p("lambda0"), p("t_origin_ns")
     b.T_lo, b.T_hi, b.t0_init, b.wf_ids = p("T_lo"), p("T_hi"), p("t0_init"), p("wf_ids")
     b.out, b.trace = p("out"), p("trace")
+    _set_z_init(b, dev)
     return b
+
+
+def _set_z_init(b, dev):
+    """Initial-state fields of a DeviceBatch from dev["z_init"] ([n, z_stride] i32) and
+    dev["n_init"] (i32), if given."""
+    z = dev.get("z_init")
+    if z is None:
+        return
+    b.z_init, b.n_init = z.data_ptr(), dev["n_init"].data_ptr()
+    b.z_stride = int(z.shape[1]) if z.dim() == 2 else int(dev["z_stride"])
 
 
 def run_device_noalloc(params: dict, dev: dict, n_steps: int, burn_in: int = 0, seed: int = 0,

@@ -81,3 +81,16 @@ def test_create_rejects_bad_mixtures_without_a_gpu():
         with pytest.raises(fsmp.FsmpError) as ei:
             fsmp.Context(dict(base, **extra))
         assert ei.value.code == fsmp.ERR_INVALID, extra
+
+
+def test_library_has_no_undefined_internal_symbols():
+    """Every internal function the library calls is defined in it (a source missing from the
+    build would otherwise surface only when the library loads on the GPU machine)."""
+    import shutil
+    import subprocess
+    from paper_2403_03156_gb300 import build
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.check_output([nm, "-u", "-C", build.build()]).decode()
+    assert not [line for line in out.splitlines() if "fsmp::" in line]
