@@ -329,7 +329,9 @@ def run_ours(args):
     tuned = None
     if pe and not args.no_autotune:  # launch shape from timed trials on a sample (not timed)
         t0_, nm0, _ = subs[0]
-        tuned = ctx.autotune(t0_, sample=32768, trial_steps=256, seed=int(b["seed"]), n_max_hint=nm0)
+        # trials of the full chain length: the cost per step grows with N over a chain, and a
+        # short trial would favour shapes that suit the first steps
+        tuned = ctx.autotune(t0_, sample=32768, trial_steps=n_steps, seed=int(b["seed"]), n_max_hint=nm0)
 
     def one_step(ev=None):
         for k, (t, nm, _) in enumerate(subs):

@@ -664,6 +664,7 @@ template <typename C> struct AcceptOut {
   C* Cp;
   int cap, N;
   unsigned long long words;
+  C idl;  // 1 / delta, delta the Schur complement of the new PE (birth, update)
 };
 
 // Apply an accepted move to C^-1, v, y and the PE list (out of line: it runs on a minority of
@@ -798,7 +799,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     }
   }
   __syncwarp(ln.gm);
-  return AcceptOut<C>{Cp, cap, Nout, wds};
+  return AcceptOut<C>{Cp, cap, Nout, wds, idl};
 }
 
 // Random draws of the L steps from `step` on, lane l taking step + l (Philox4x64-10 keyed by
@@ -968,26 +969,92 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       __syncwarp(ln.gm);
       if (ni > cap) { Cp = Cg; cap = n_cap; }
       if (ni > 0) {
-        const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, ni, ln);
-        C qs = czero<C>();
+        bool ok = true;
         double ms = 0.0;
+        C qs = czero<C>();
+        if constexpr (fp32) {
+          // FP32 mode: the FP64 rebuild
+          const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, ni, ln);
+          ok = ro.ok != 0;
+          if (ok && ln.sl == 0) { S.logdet = ro.logdet; S.logL = ro.logL; }
+        } else {
+          // FP64 mode: the PEs born one by one through the accepted-move update in double-double
+          // (the FP64 rebuild would leave C^-1 only as accurate as FP64 times its condition
+          // number); log|C| is the sum of the log Schur complements
+          double lC = 0.0;
+#pragma unroll 1
+          for (int k = 0; k < ni; ++k) {
+            PeMove<C> mv;
+            mv.jump = 0; mv.kk = -1; mv.jp = W.list[k]; mv.jm = -1;
+            mv.em = mv.ep = MIX ? M.cm_mode : 0;
+            const Sup sp = pe_sup(M, n, mv.jp);
+            mv.sp = sp;
+            int np = 0;
+#pragma unroll 1
+            for (int base = 0; base < N; base += L) {
+              const int qi = base + ln.sl;
+              C bq = czero<C>();
+              if (qi < N) {
+                const int o = mv.jp - W.list[qi];
+                if (o > -M.Lt && o < M.Lt) bq = xcorr<C>(M, tc, sp, o);
+              }
+              const bool ov = cnz(bq);
+              const unsigned m = gballot(ov, ln);
+              if (ov) {
+                const int pos = np + __popc(m & ((1u << ln.sl) - 1u));
+                W.ovi[pos] = qi;
+                W.ovb[pos] = bq;
+              }
+              np += __popc(m);
+            }
+            __syncwarp(ln.gm);
+            mv.np = np;
+            mv.aa = xcorr<C>(M, tc, sp, 0);
+            T ayp = (T)0;
+            for (int i = sp.ilo + ln.sl; i < sp.ihi; i += L) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
+            mv.ay = cfromf(wsum(ayp, ln));
+            mv.quad = mv.bv = mv.vk = czero<C>();
+            const AcceptOut<C> ao = pe_accept<T, BIG, L, MIX>(M, W, Vs, Cp, cap, Cg, mv, n, N, ln);
+            Cp = ao.Cp;
+            cap = ao.cap;
+            N = ao.N;
+            const double dl = c64(ao.idl);
+            if (!(dl > 0.0) || !isfinite(dl)) ok = false;
+            lC -= log(dl);
+          }
+          N = 0;
+          // log|Sigma| = n log se2 + log|C| - sum_k log r_k; y^T Sigma^-1 y = (y^T y - h^T v) / se2
+          double lr = 0.0, yy = 0.0, hv = 0.0;
+          for (int k = ln.sl; k < ni; k += L) {
+            lr += M.cm_lr[MIX ? M.cm_mode : 0];
+            const Sup s = pe_sup(M, n, W.list[k]);
+            double hk = 0.0;
+            for (int i = s.ilo; i < s.ihi; ++i) hk = fma((double)Vs[s.ph + i * R], (double)W.y[s.w0 + i], hk);
+            hv = fma(hk, c64(W.v[k]), hv);
+          }
+          for (int x = ln.sl; x < n; x += L) yy = fma((double)W.y[x], (double)W.y[x], yy);
+          lr = wsum(lr, ln); yy = wsum(yy, ln); hv = wsum(hv, ln);
+          if (ok && ln.sl == 0) {
+            S.logdet = n * M.log_se2 + lC - lr;
+            S.logL = -0.5 * (n * kLog2Pi + S.logdet + (yy - hv) * M.inv_se2);
+          }
+        }
         for (int i = ln.sl; i < ni; i += L) {
           qs = cadd(qs, W.v[i]);
           if (mix) ms += M.cm_mu[W.le[i]];
         }
         qs = csum(qs, ln);
         ms = mix ? wsum(ms, ln) : ni * M.cm_mu[0];
-        if (ro.ok) {
+        if (ok) {
           N = ni;
         } else {  // C not numerically positive definite: start empty
           for (int x = ln.sl; x < n; x += L) W.y[x] = (T)w[x];
+          Cp = Ns > 0 ? W.Cs : Cg;
+          cap = Ns > 0 ? Ns : n_cap;
         }
         if (ln.sl == 0) {
-          if (ro.ok) {
-            S.logdet = ro.logdet; S.logL = ro.logL; S.q_cur = ms + c64(qs);
-          } else {
-            S.status |= FSMP_ST_BADDET;
-          }
+          if (ok) S.q_cur = ms + c64(qs);
+          else S.status |= FSMP_ST_BADDET;
         }
       }
       if (ln.sl == 0 && cut) S.status |= FSMP_ST_CAPACITY;

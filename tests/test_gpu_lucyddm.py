@@ -33,8 +33,9 @@ def _dev(torch, b):
 
 def test_lucyddm_matches_oracle(lib, orc):
     """q-hat after 2000 FP32 iterations within 1e-3 of the oracle's FP64 value (relative to the
-    waveform's largest q-hat); the initial PEs, T and t0 equal wherever no q-hat of the
-    waveform lies within that tolerance of the 0.1 threshold."""
+    waveform's largest q-hat). Every tau where the two sides take different sides of the 0.1
+    threshold must have the oracle's q-hat within that tolerance of 0.1 (FP32 decides there);
+    on the other waveforms the initial PEs, T and t0 are equal."""
     torch = pytest.importorskip("torch")
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=160, seed=21)
     b = wl["batch"]
@@ -45,7 +46,7 @@ def test_lucyddm_matches_oracle(lib, orc):
         torch.cuda.synchronize()
         g = {k: v.cpu().numpy() for k, v in r.items()}
     off = b["offsets"]
-    worst, ambiguous = 0.0, 0
+    worst, split = 0.0, 0
     for i in range(len(off) - 1):
         w = b["samples"][off[i]:off[i + 1]]
         o = orc.lucyddm(wl["params"], w, n_iter=N_ITER, thresh=THRESH, t_origin=b["t_origin_ns"][i], z_cap=64)
@@ -56,8 +57,10 @@ def test_lucyddm_matches_oracle(lib, orc):
         worst = max(worst, err)
         assert err < 1e-3, (i, err)
         assert g["status"][i] == 0
-        if np.any(np.abs(o["q"] - THRESH) <= 1e-3 * scale):
-            ambiguous += 1
+        differ = (qg > THRESH) != (o["q"] > THRESH)
+        if differ.any():
+            assert np.all(np.abs(o["q"][differ] - THRESH) <= 1e-3 * scale), i
+            split += 1
             continue
         assert g["n_init"][i] == o["n_z"]
         assert list(g["z_init"][i, :min(o["n_z"], 64)]) == list(o["z"])
@@ -66,8 +69,9 @@ def test_lucyddm_matches_oracle(lib, orc):
             assert g["t0_init"][i] == pytest.approx(o["t0"], abs=1e-9)
         else:
             assert math.isnan(g["t0_init"][i])
-    assert ambiguous <= 8
-    print("LucyDDM: worst relative q-hat error %.2e, %d ambiguous waveforms of %d" % (worst, ambiguous, len(off) - 1))
+    assert split <= 16
+    print("LucyDDM: worst relative q-hat error %.2e; %d of %d waveforms with a threshold decision taken "
+          "differently in FP32" % (worst, split, len(off) - 1))
 
 
 def _trace_buf(torch, W, n_steps):
@@ -76,9 +80,9 @@ def _trace_buf(torch, W, n_steps):
 
 @pytest.mark.parametrize("lanes", [32, 16])
 def test_chain_from_lucyddm_state_fp64_lockstep(lib, orc, lanes):
-    """The oracle's LucyDDM state (z, T, t0) as the initial state of both sides: the GPU's FP64
-    rebuild of C^-1 from z and the oracle's Cholesky (definition mode) give the same log
-    acceptance ratios to 1e-9 and the same decisions over 500 steps."""
+    """The oracle's LucyDDM state (z, T, t0) as the initial state of both sides: the GPU's C^-1
+    built by successive double-double births and the oracle's Cholesky (definition mode) give
+    the same log acceptance ratios to 1e-9 and the same decisions over 500 steps."""
     torch = pytest.importorskip("torch")
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=48, seed=33, n_steps=500)
     b = dict(wl["batch"])
