@@ -207,6 +207,12 @@ typedef struct {
   const int32_t* z_init;
   const int32_t* n_init;
   int z_stride;
+  /* PE-time histogram (may be NULL; FSMP_KERNEL_PE only): after burn-in, every step adds one
+   * to pe_hist[i * pe_hist_width + (j - T_lo)] for each PE of waveform i at grid index j with
+   * T_lo <= j < T_lo + pe_hist_width (T_lo = 0 without a T_lo array); divided by n_samples
+   * it is the posterior mean PE count per grid point. The caller zeroes it. */
+  uint32_t* pe_hist;
+  int pe_hist_width;
 } fsmp_device_batch;
 
 /* LucyDDM (Sec. 2.3): Lucy's iterative deconvolution of each waveform of a device batch by

@@ -87,6 +87,8 @@ struct BatchView {
   const int32_t* z_init;       // may be null: initial PEs, waveform i at z_init[i * z_stride]
   const int32_t* n_init;
   int z_stride;
+  uint32_t* pe_hist;           // may be null: PE counts per grid point after burn-in
+  int pe_hist_width;
 };
 
 // Philox4x64-10 (Salmon et al., SC'11): two 64x64->128 multiplies per round, Weyl key bumps.

@@ -897,6 +897,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     const int n_steps = B.n_steps_arr ? B.n_steps_arr[wi] : B.n_steps;
     const int burn_in = B.burn_in_arr ? B.burn_in_arr[wi] : B.burn_in;
     fsmp_summary* out = B.out + wi;
+    uint32_t* const peh = B.pe_hist ? B.pe_hist + (size_t)wi * B.pe_hist_width : nullptr;
     fsmp_trace* trace = B.trace ? B.trace + (B.trace_off ? B.trace_off[wi] : (int64_t)wi * n_steps) : nullptr;
     const bool invalid = n < 1 || n > n_alloc || T_hi <= T_lo || k0_hi < k0_lo || !(lambda0 > 0.0) || n_steps < 0 ||
                          burn_in < 0 || ((fp32 || B.z_init) && ws == nullptr) || k0_hi - k0_lo + 1 > M.win_extra ||
@@ -1310,6 +1311,12 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           tr.dnu = (double)dnu; tr.N = N; tr.k0 = k0; tr.jump = jump;
           tr.flags = t0f | (acc ? 4 : 0) | ((acc && noop) ? 8 : 0);
           trace[step] = tr;
+        }
+      }
+      if (peh && step >= burn_in) {  // PE-time histogram: one count per PE and step
+        for (int k = ln.sl; k < N; k += L) {
+          const int c = W.list[k] - T_lo;
+          if (c >= 0 && c < B.pe_hist_width) atomicAdd(peh + c, 1u);
         }
       }
       __syncwarp(ln.gm);

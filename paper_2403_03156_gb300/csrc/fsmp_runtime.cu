@@ -925,6 +925,11 @@ int fsmp_run_device(fsmp_ctx* c, const fsmp_device_batch* b, void* stream) {
     if (c->p.kernel != FSMP_KERNEL_PE) FAIL(FSMP_ERR_INVALID, "an initial z needs the PE-space kernel");
     B.z_init = b->z_init; B.n_init = b->n_init; B.z_stride = b->z_stride;
   }
+  if (b->pe_hist) {
+    if (b->pe_hist_width < 1) FAIL(FSMP_ERR_INVALID, "pe_hist needs pe_hist_width >= 1");
+    if (c->p.kernel != FSMP_KERNEL_PE) FAIL(FSMP_ERR_INVALID, "a PE-time histogram needs the PE-space kernel");
+    B.pe_hist = b->pe_hist; B.pe_hist_width = b->pe_hist_width;
+  }
   { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   return run_view(c, B, (cudaStream_t)stream, (int)c->streams.size());
 }

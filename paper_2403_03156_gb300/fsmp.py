@@ -69,7 +69,8 @@ class DeviceBatch(ctypes.Structure):
                 ("n_max_hint", _c_int), ("seed", _c_u64), ("index_base", _c_u64),
                 ("samples", _vp), ("offsets", _vp), ("lambda0", _vp), ("t_origin_ns", _vp),
                 ("T_lo", _vp), ("T_hi", _vp), ("t0_init", _vp), ("wf_ids", _vp), ("out", _vp),
-                ("trace", _vp), ("z_init", _vp), ("n_init", _vp), ("z_stride", _c_int)]
+                ("trace", _vp), ("z_init", _vp), ("n_init", _vp), ("z_stride", _c_int),
+                ("pe_hist", _vp), ("pe_hist_width", _c_int)]
 
 
 class LucyBatch(ctypes.Structure):
@@ -406,7 +407,10 @@ def _device_batch(dev, n_steps, burn_in, seed, index_base, n_max_hint):
 
 def _set_z_init(b, dev):
     """Initial-state fields of a DeviceBatch from dev["z_init"] ([n, z_stride] i32) and
-    dev["n_init"] (i32), if given."""
+    dev["n_init"] (i32), and the PE-time histogram dev["pe_hist"] ([n, width] i32), if given."""
+    h = dev.get("pe_hist")
+    if h is not None:  # [n, width] int32 / uint32 counts
+        b.pe_hist, b.pe_hist_width = h.data_ptr(), int(h.shape[1])
     z = dev.get("z_init")
     if z is None:
         return
