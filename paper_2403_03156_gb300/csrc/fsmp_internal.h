@@ -121,13 +121,52 @@ FSMP_HD double u01_from_bits(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x
 // over its N-sample counts h[0 .. n_max]. l can have several local maxima (a chain that visits
 // clusters of N far apart), all inside (0, top] with top the largest N sampled, since a
 // stationary point satisfies lambda = E_w[N] with w_N ∝ h[N] (lambda / lambda0)^N. So:
-// (1) scan l on 8 L points of (0, top] in FP32 (lanes over points) and take the best;
-// (2) Newton steps in FP64 on l'(lambda) = -1 + E_w[N] / lambda, l''(lambda) =
-//     (Var_w[N] - E_w[N]) / lambda^2, kept within two scan cells of the best point
-//     (bisection where a step would leave it, fixed-point steps lambda <- E_w[N] where
-//     l'' >= 0); (3) the boundary lambda = 0 when l(0) is not smaller. A group of L
-// consecutive lanes (mask gm, sl the lane within it) calls it and every lane gets the result;
-// NAN if h is empty.
+// (1) scan l on 2 L to 8 L points of (0, top] in FP32 (lanes over points) and take the best;
+// (2) Newton steps on l'(lambda) = -1 + E_w[N] / lambda, l''(lambda) = (Var_w[N] - E_w[N]) /
+//     lambda^2, kept within two scan cells of the best point (bisection where a step would
+//     leave them, fixed-point steps lambda <- E_w[N] where l'' >= 0): first in FP32 to 1e-6,
+//     then at most 12 steps in FP64 to 1e-14 (two or three from there) -- FP64 costs this part
+//     64 FP32 operations each, and every chain of a launch ends here; (3) the boundary
+//     lambda = 0 when l(0) is not smaller (a maximum that the FP32 steps push below 1e-6 of a
+//     scan cell is taken as the boundary). A group of L consecutive lanes (mask gm, sl the lane
+//     within it) calls it and every lane gets the result; NAN if h is empty.
+template <typename F, int L>
+__device__ inline F lmle_newton(const int* h, int bot, int top, F lambda0, F lam, F& lo, F& hi, F tol, int max_it,
+                                int sl, unsigned gm, F* ll_out) {
+  F ll = -INFINITY;
+  for (int it = 0; it < max_it; ++it) {
+    if (hi - lo <= tol * hi) break;  // the bracket has closed
+    const F s = log(lam / lambda0);
+    F mx = -INFINITY;
+    for (int k = bot + sl; k <= top; k += L)
+      if (h[k] > 0) mx = fmax(mx, log((F)h[k]) + k * s);
+    for (int o = L / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(gm, mx, o, L));
+    F sw = 0, s1 = 0, s2 = 0;
+    for (int k = bot + sl; k <= top; k += L)
+      if (h[k] > 0) {
+        const F e = exp(log((F)h[k]) + k * s - mx);
+        sw += e; s1 += k * e; s2 += (F)k * k * e;
+      }
+    for (int o = L / 2; o > 0; o >>= 1) {
+      sw += __shfl_xor_sync(gm, sw, o, L);
+      s1 += __shfl_xor_sync(gm, s1, o, L);
+      s2 += __shfl_xor_sync(gm, s2, o, L);
+    }
+    const F E = s1 / sw, Vr = s2 / sw - E * E;
+    ll = -lam + mx + log(sw);
+    const F g = -1 + E / lam, H = (Vr - E) / (lam * lam);
+    if (g == 0) break;                    // a stationary point
+    if (g > 0) lo = lam; else hi = lam;   // the maximum lies on the side l' points to
+    F nl = H < 0 ? lam - g / H : E;
+    if (!(nl > lo && nl < hi)) nl = (F)0.5 * (lo + hi);
+    const bool done = fabs(nl - lam) <= tol * lam;
+    lam = nl;
+    if (done) break;
+  }
+  *ll_out = ll;
+  return lam;
+}
+
 template <int L>
 __device__ inline double group_lambda_mle(const int* h, int n_max, double lambda0, int sl, unsigned gm) {
   int top = -1, bot = n_max + 1;
@@ -139,8 +178,9 @@ __device__ inline double group_lambda_mle(const int* h, int n_max, double lambda
   }
   if (top < 0) return NAN;
   if (top == 0) return 0.0;
-  // (1) coarse scan, log2 units: l / ln 2 = -lambda / ln 2 + log2 sum_N h[N] 2^(N log2(lambda / lambda0))
-  constexpr int G = 8 * L;
+  // (1) coarse scan, log2 units: l / ln 2 = -lambda / ln 2 + log2 sum_N h[N] 2^(N log2(lambda / lambda0)),
+  // on G points with a spacing of at most top / (8 L), and of at most 16 / (2 L) below top = 16
+  const int G = min(8, 2 * ((top + 15) / 16)) * L;
   const float lr0 = log2f((float)lambda0);
   float best = -INFINITY;
   int bi = 0;
@@ -161,40 +201,19 @@ __device__ inline double group_lambda_mle(const int* h, int n_max, double lambda
     const int oi = __shfl_xor_sync(gm, bi, o, L);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
-  // (2) Newton in FP64 inside [lambda_(b-2), lambda_(b+2)] (two scan cells of slack for the
-  // FP32 rounding of the scan)
+  // (2) Newton within [lambda_(b-2), lambda_(b+2)] (two scan cells of slack for the FP32
+  // rounding of the scan): FP32, then FP64 from its result
   const double cell = (double)top / G;
-  double lo = fmax(cell * (bi - 1), 1e-300), hi = cell * (bi + 3);
-  double lam = cell * (bi + 1), ll = -INFINITY;
-  for (int it = 0; it < 200; ++it) {
-    const double s = log(lam / lambda0);
-    double mx = -INFINITY;
-    for (int k = sl; k <= n_max; k += L)
-      if (h[k] > 0) mx = fmax(mx, log((double)h[k]) + k * s);
-    for (int o = L / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(gm, mx, o, L));
-    double sw = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int k = sl; k <= n_max; k += L)
-      if (h[k] > 0) {
-        const double e = exp(log((double)h[k]) + k * s - mx);
-        sw += e; s1 += k * e; s2 += (double)k * k * e;
-      }
-    for (int o = L / 2; o > 0; o >>= 1) {
-      sw += __shfl_xor_sync(gm, sw, o, L);
-      s1 += __shfl_xor_sync(gm, s1, o, L);
-      s2 += __shfl_xor_sync(gm, s2, o, L);
-    }
-    const double E = s1 / sw, Vr = s2 / sw - E * E;
-    ll = -lam + mx + log(sw);
-    const double g = -1.0 + E / lam, H = (Vr - E) / (lam * lam);
-    if (g == 0.0) break;                   // a stationary point
-    if (g > 0.0) lo = lam; else hi = lam;  // the maximum lies on the side l' points to
-    double nl = H < 0.0 ? lam - g / H : E;
-    if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
-    const bool done = fabs(nl - lam) <= 1e-14 * lam;
-    lam = nl;
-    if (done) break;
-  }
+  const double lo0 = fmax(cell * (bi - 1), 1e-6 * cell), hi0 = cell * (bi + 3);
+  float lo32 = (float)lo0, hi32 = (float)hi0, ll32;
+  const float lam32 = lmle_newton<float, L>(h, bot, top, (float)lambda0, (float)(cell * (bi + 1)), lo32, hi32,
+                                            1e-6f, 60, sl, gm, &ll32);
   const double l0 = h[0] > 0 ? log((double)h[0]) : -INFINITY;  // l(0): only N = 0 contributes
+  double lo = lo0, hi = hi0, ll;
+  double lam = (double)lam32;
+  if (!(lam > lo && lam < hi)) lam = cell * (bi + 1);
+  if (h[0] > 0 && hi32 <= 2e-6 * cell) return 0.0;  // the steps ran into the boundary
+  lam = lmle_newton<double, L>(h, bot, top, lambda0, lam, lo, hi, 1e-14, 12, sl, gm, &ll);
   return l0 >= ll ? 0.0 : lam;
 }
 __device__ inline double warp_lambda_mle(const int* h, int n_max, double lambda0, int lane) {
