@@ -497,6 +497,28 @@ def run_serving(args):
     rate = args.rate or cfg["rate_hz"]
     ctx = fsmp.Context(dict(params, precision=fsmp.FP32_REFRESH, refresh_every=cfg.get("refresh_every", 64),
                             n_max=cfg["win_max"], device=local, max_queued=1 << 20))
+    # launch shape from timed trials on the pool of events (untimed), and the same events as one
+    # device batch: the rate the serving loop would reach if every event arrived at once
+    pb = concat_events(pool)
+    dvc = torch.device("cuda", local)
+    tb = {"samples": torch.from_numpy(pb["samples"]).to(dvc), "offsets": torch.from_numpy(pb["offsets"]).to(dvc),
+          "lambda0": torch.from_numpy(pb["lambda0"]).to(dvc), "t_origin_ns": torch.from_numpy(pb["t_origin_ns"]).to(dvc),
+          "wf_ids": torch.from_numpy(pb["wf_ids"].astype(np.int64)).to(dvc)}
+    nm = int(np.diff(pb["offsets"]).max())
+    tuned = None if args.no_autotune else ctx.autotune(tb, sample=32768, trial_steps=n_steps, seed=int(pb["seed"]),
+                                                        n_max_hint=nm)
+    Wp = len(pb["offsets"]) - 1
+    tb["out"] = torch.zeros(Wp * fsmp.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dvc)
+    batch_ms = []
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.run_device(tb, n_steps=n_steps, burn_in=n_steps // 5, seed=int(pb["seed"]), n_max_hint=nm)
+        e1.record()
+        torch.cuda.synchronize()
+        batch_ms.append(e0.elapsed_time(e1))
+    batch_rate = Wp * n_steps / (batch_ms[-1] * 1e-3)
+    del tb
     # warm-up: the first requests pay for lazy initialisation
     for i in range(args.warmup):
         ctx.run(pool[i % len(pool)], request_id=(1 << 40) + i)
@@ -565,7 +587,8 @@ def run_serving(args):
                        "mcmc_steps_per_chain": n_steps, "completed_rate_hz": completed_rate,
                        "sustained": bool(completed_rate >= 0.95 * rate), "busy_retries": busy,
                        "timing": "host wall clock from the first submit to the last result (end to end)",
-                       "kernel": "pe_kernel<float> (serving loop, one launch per pack)"},
+                       "kernel": "pe_kernel<float> (serving loop, one launch per pack)", "autotune": tuned,
+                       "pool_as_one_batch_steps_per_s": batch_rate, "pool_waveforms": Wp},
             "latency": {"p50_s": float(np.nanpercentile(lat, 50)), "p99_s": float(np.nanpercentile(lat, 99)),
                         "mean_s": float(np.nanmean(lat)), "max_s": float(np.nanmax(lat))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(bytes_in),

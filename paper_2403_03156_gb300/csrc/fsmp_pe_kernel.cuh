@@ -480,17 +480,28 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   const double* V = M.V64;
   constexpr bool mix = MIX;
   const double mu = M.cm_mu[0], r = M.cm_r[0];  // the dynode model's (one component)
-  // C = diag(r_k) + A^T A (full, row-major)
+  // C = diag(r_k) + A^T A (full, row-major); lanes over columns, RC rows at a time so that the
+  // table loads of the rows overlap. The unrolled forms (BIG: many PEs per chain) cost the
+  // caller registers around the call, which the compact variant cannot spare.
+  constexpr int RC = BIG ? 4 : 1, RG = BIG ? 8 : 1;
 #pragma unroll 1
-  for (int i = 0; i < N; ++i) {
-    const int ji = W.list[i];
-    const Sup si = pe_sup(M, n, ji);
+  for (int j = ln.sl; j < N; j += L) {
+    const int jj = W.list[j];
 #pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      const int o = ji - W.list[j];
-      double c = (o > -M.Lt && o < M.Lt) ? xcorr<double>(M, M.tc64, si, o) : 0.0;
-      if (j == i) c += mix ? M.cm_r[W.le[i]] : r;
-      A[(size_t)i * ws_ld + j] = c;
+    for (int i0 = 0; i0 < N; i0 += RC) {
+      double c[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        const int i = min(i0 + q, N - 1);
+        const int ji = W.list[i];
+        const int o = ji - jj;
+        c[q] = (o > -M.Lt && o < M.Lt) ? xcorr<double>(M, M.tc64, pe_sup(M, n, ji), o) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        const int i = i0 + q;
+        if (i < N) A[(size_t)i * ws_ld + j] = c[q] + (j == i ? (mix ? M.cm_r[W.le[i]] : r) : 0.0);
+      }
     }
   }
   __syncwarp(ln.gm);
@@ -549,13 +560,7 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   int pe = 0;
 #pragma unroll 1
   for (int k = 0; k < N; ++k) {
-#pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      rowk[j] = A[(size_t)k * ws_ld + j];
-      colk[j] = A[(size_t)j * ws_ld + k];
-    }
-    __syncwarp(ln.gm);
-    const double piv = rowk[k];
+    const double piv = A[(size_t)k * ws_ld + k];
     if (!(piv > 0.0) || !isfinite(piv)) return out;
     const double ip = 1.0 / piv;
     int ex;
@@ -563,40 +568,39 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
     pe += ex;
     pm = frexp(pm, &ex);
     pe += ex;
+    // the pivot row and the row multipliers f_i = A_ik / pivot
 #pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) colk[j] *= ip;  // the row multipliers
+    for (int j = ln.sl; j < N; j += L) {
+      rowk[j] = A[(size_t)k * ws_ld + j];
+      colk[j] = A[(size_t)j * ws_ld + k] * ip;
+    }
     __syncwarp(ln.gm);
-    // rows i != k: A_ij -= f_i A_kj (A_ik = -f_i); row k: A_kj / pivot. Lanes over columns
-    // (BIG: four rows per iteration so that their loads overlap).
+    // rows i != k: A_ij -= f_i A_kj (A_ik = -f_i); row k: A_kj / pivot. Lanes over columns,
+    // RG rows at a time so that their loads overlap.
 #pragma unroll 1
     for (int j = ln.sl; j < N; j += L) {
       const double rkj = rowk[j];
-      int i = 0;
-      if constexpr (BIG) {
 #pragma unroll 1
-        for (; i + 3 < N; i += 4) {
-          double x[4];
+      for (int i0 = 0; i0 < N; i0 += RG) {
+        double x[RG], f[RG];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) x[r] = A[(size_t)(i + r) * ws_ld + j];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int ir = i + r;
-            const double f = colk[ir];
-            A[(size_t)ir * ws_ld + j] = (ir == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x[r]));
-          }
+        for (int q = 0; q < RG; ++q) {
+          const int i = min(i0 + q, N - 1);
+          x[q] = A[(size_t)i * ws_ld + j];
+          f[q] = colk[i];
         }
-      }
-#pragma unroll 1
-      for (; i < N; ++i) {
-        const double f = colk[i];
-        const double x = A[(size_t)i * ws_ld + j];
-        A[(size_t)i * ws_ld + j] = (i == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f : fma(-f, rkj, x));
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+          const int i = i0 + q;
+          if (i < N)
+            A[(size_t)i * ws_ld + j] = (i == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f[q] : fma(-f[q], rkj, x[q]));
+        }
       }
     }
     __syncwarp(ln.gm);
   }
   const double logdetC = log(pm) + (double)pe * 0.6931471805599453;
-  // v = C^-1 h (C^-1 symmetric: lanes over columns)
+  // v = C^-1 h (C^-1 symmetric: lanes over columns; BIG: four partial sums)
 #pragma unroll 1
   for (int i = ln.sl; i < N; i += L) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
