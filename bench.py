@@ -331,7 +331,9 @@ def run_ours(args):
         t0_, nm0, _ = subs[0]
         # trials of the full chain length: the cost per step grows with N over a chain, and a
         # short trial would favour shapes that suit the first steps
-        tuned = ctx.autotune(t0_, sample=32768, trial_steps=n_steps, seed=int(b["seed"]), n_max_hint=nm0)
+        # (a sample of at most a quarter of the batch, so that the trials stay short next to it)
+        tuned = ctx.autotune(t0_, sample=min(32768, max(2048, W // 4)), trial_steps=n_steps, seed=int(b["seed"]),
+                             n_max_hint=nm0)
 
     def one_step(ev=None):
         for k, (t, nm, _) in enumerate(subs):
