@@ -757,8 +757,34 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   // entry only where it writes it, or in the last row for a death (which it does not write).
   const C nig = cneg(ig);
   const int kmap = jump == 1 ? kk : -1;  // the slot the last PE moves into
+  const int ne = tri(Nout);               // rows 0 .. Nout-1
+  int e0 = 0;
+  if constexpr (BIG) {
+    // C^-1 in the global slot: four entries per lane and pass, all read before any is written
+    // (each read is the entry itself or one in the unwritten last row), so that the loads of a
+    // pass overlap
 #pragma unroll 1
-  for (int e = ln.sl; e < tri(Nout); e += L) {  // rows 0 .. Nout-1
+    for (; e0 + 4 * L <= ne; e0 += 4 * L) {
+      int ii[4], jj[4];
+      C old[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        untri(e0 + q * L + ln.sl, ii[q], jj[q]);
+        const int mi = (ii[q] == kmap) ? last : ii[q], mj = (jj[q] == kmap) ? last : jj[q];
+        old[q] = Cp[pk(mi, mj)];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = ii[q], j = jj[q];
+        const int mi = (i == kmap) ? last : i, mj = (j == kmap) ? last : j;
+        const C val = cfma(W.uv[i], cmul(W.uv[j], idl), cfma(W.cv[mi], cmul(W.cv[mj], nig), old[q]));
+        const C sv = (i == s && j == s) ? idl : cneg(cmul(W.uv[i == s ? j : i], idl));
+        Cp[e0 + q * L + ln.sl] = (i == s || j == s) ? sv : val;
+      }
+    }
+  }
+#pragma unroll 1
+  for (int e = e0 + ln.sl; e < ne; e += L) {
     int i, j;
     untri(e, i, j);
     const int mi = (i == kmap) ? last : i, mj = (j == kmap) ? last : j;

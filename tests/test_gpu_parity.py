@@ -95,3 +95,42 @@ def test_gelman_rubin_of_gpu_chains_matches_oracle(lib, orc):
         for field in (fsmp.RHAT_N, fsmp.RHAT_T0):
             rg, ro = fsmp.gelman_rubin(g, field), fsmp.gelman_rubin(o, field)
             assert np.isfinite(rg) and abs(rg - ro) <= 1e-9 * max(1.0, ro), (w, field, rg, ro)
+
+
+def test_lockstep_fp64_pileup_variant(lib, orc):
+    """The pile-up variant of the PE-space kernel (n_cap > 192: unrolled gathers, accept pass and
+    rebuild) with C^-1 in its global slot from the fifth PE on (pe_tile = 4): 48 uneven-window
+    chains, FP64, every log acceptance ratio to 1e-9 against the oracle's definition mode."""
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=48, n_steps=500, seed=41)
+    b = wl["batch"]
+    n_max = int(np.diff(b["offsets"]).max())
+    params = dict(wl["params"], n_cap=200)
+    with fsmp.Context(params, n_max=n_max, precision=fsmp.FP64, kernel=fsmp.KERNEL_PE, pe_tile=4) as ctx:
+        s_gpu, t_gpu = ctx.run(b, record_trace=True)
+    s_orc, t_orc = orc.run_batch(params, b, orc.MODE_DEFINITION, n_threads=16, trace=True)
+    gpu_util.compare_traces(t_gpu, t_orc)
+    for f in ("mean_Q", "logL", "logdet", "lambda_hat"):
+        np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
+    np.testing.assert_array_equal(s_gpu["acc"], s_orc["acc"])
+    assert t_gpu["N"].max() >= 20  # the unrolled accept pass ran (4 x 32 entries per pass)
+
+
+def test_fp32_pileup_variant_statistics(lib, orc):
+    """The pile-up variant in FP32 mode (float-float C^-1 in the global slot, the unrolled FP64
+    rebuild every 16 accepts): mean paired differences GPU - oracle of the posterior N and
+    charge within 3 standard errors over 192 uneven-window waveforms."""
+    import math
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=192, n_steps=1200, seed=43, burn_in=240)
+    b = wl["batch"]
+    n_max = int(np.diff(b["offsets"]).max())
+    params = dict(wl["params"], n_cap=200)
+    with fsmp.Context(params, n_max=n_max, precision=fsmp.FP32_REFRESH, refresh_every=16, kernel=fsmp.KERNEL_PE,
+                      pe_tile=8) as ctx:
+        s_gpu, _ = ctx.run(b)
+    s_orc, _ = orc.run_batch(params, b, orc.MODE_INCREMENTAL, n_threads=16)
+    for f in ("mean_N", "mean_Q"):
+        d = s_gpu[f] - s_orc[f]
+        se = d.std(ddof=1) / math.sqrt(len(d))
+        assert abs(d.mean()) <= 3 * se + 1e-9, (f, d.mean(), se)
+    assert np.all((s_gpu["status"] & (fsmp.ST_DRIFT | fsmp.ST_BADDET | fsmp.ST_NONFINITE | fsmp.ST_INVALID)) == 0)
+    assert s_gpu["n_refresh"].sum() > 0
