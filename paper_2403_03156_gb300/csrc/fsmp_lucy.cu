@@ -59,7 +59,7 @@ struct LucyArgs {
   double* t0;
   int32_t* z;
   int32_t* n_z;
-  int* status;  // per waveform: 0, or 1 when the window is empty or longer than n_alloc
+  int* status;  // per waveform: 0, or FSMP_ST_INVALID when the window is empty or longer than n_alloc
 };
 
 __global__ void __launch_bounds__(kLucyWarps * 32) lucy_kernel(const float4* __restrict__ v4, const __grid_constant__ LucyArgs A) {
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kLucyWarps * 32) lucy_kernel(const float4* __r
   const int LV = A.LV, nq = n + LV - 1;
   if (n < 1 || n > A.n_alloc) {
     if (lane == 0) {
-      A.status[wi] = 1;
+      A.status[wi] = FSMP_ST_INVALID;
       A.n_z[wi] = 0; A.T_lo[wi] = 0; A.T_hi[wi] = max(n, 0) * A.R; A.t0[wi] = NAN;
     }
     return;

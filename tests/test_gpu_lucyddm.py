@@ -148,3 +148,30 @@ def test_lucyddm_then_fp32_chains(lib):
     cap = wl["params"]["n_cap"]
     assert np.all(np.abs(t["N"][:, 0] - np.minimum(n_init, cap)) <= 1)
     print("LucyDDM initial N: mean %.2f (truth %.2f)" % (n_init.mean(), wl["truth"]["N"].mean()))
+
+
+def test_lucyddm_edge_cases(lib, orc):
+    """A one-sample window, an all-zero window, a window longer than the launch's bound (flagged
+    FSMP_ST_INVALID, nothing else written but T = the whole window) and a noiseless PE: each as
+    the oracle gives it (the zero and the long one give no initial PE and t0 = NaN)."""
+    torch = pytest.importorskip("torch")
+    params = workloads.CONFIGS["plain_fp64_256x128"]["params"]
+    V, _ = orc.ser_table(params)
+    pulse = np.zeros(96, np.float32)
+    pulse[20:20 + 65] = 1.7 * V[::4][:65] / 1.0
+    wins = [np.array([0.3], np.float32), np.zeros(64, np.float32), np.zeros(200, np.float32), pulse]
+    offs = np.concatenate([[0], np.cumsum([len(w) for w in wins])]).astype(np.int32)
+    b = dict(samples=np.concatenate(wins), offsets=offs, lambda0=np.ones(4), t_origin_ns=np.zeros(4))
+    with fsmp.Context(params, n_max=256, kernel=fsmp.KERNEL_PE) as ctx:
+        r = ctx.lucyddm(_dev(torch, b), n_iter=N_ITER, thresh=THRESH, n_max_hint=128)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in r.items()}
+    assert list(g["status"]) == [0, 0, fsmp.ST_INVALID, 0]
+    for i in (0, 1, 3):
+        o = orc.lucyddm(params, wins[i], n_iter=N_ITER, thresh=THRESH)
+        assert g["n_init"][i] == o["n_z"], i
+        assert list(g["z_init"][i, :o["n_z"]]) == list(o["z"]), i
+        assert (g["T_lo"][i], g["T_hi"][i]) == (o["T_lo"], o["T_hi"]), i
+        assert (math.isnan(g["t0_init"][i]) and math.isnan(o["t0"])) or g["t0_init"][i] == pytest.approx(o["t0"])
+    assert g["n_init"][2] == 0 and math.isnan(g["t0_init"][2]) and (g["T_lo"][2], g["T_hi"][2]) == (0, 200 * 4)
+    assert g["n_init"][3] >= 1 and g["z_init"][3, 0] in (19 * 4, 20 * 4)
