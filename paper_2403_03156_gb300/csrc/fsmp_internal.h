@@ -273,11 +273,12 @@ cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lane
                       void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
                       cudaStream_t st);
 // LucyDDM (fsmp_lucy.cu): shared memory per CTA for windows up to n_alloc; the kernel taps
-// v(m) = V(m dt) / S, padded to whole groups of four, and S; the deconvolution launch.
+// v(m) = V(m dt) / S, padded to whole groups of four, and S (on the device); the deconvolution
+// launch, given the taps in host memory (they travel in the kernel's parameters).
 size_t lucy_smem_bytes(int LV, int n_alloc);
 cudaError_t lucy_kernel_attributes(int max_smem);
 cudaError_t launch_lucy_taps(const float* V32, int LV, int R, float* v4, float* S_dev, cudaStream_t st);
-cudaError_t launch_lucy(const float* v4, float S, int LV, int R, double dt, double g, int n_waveforms, int n_alloc,
+cudaError_t launch_lucy(const float* v4_host, float S, int LV, int R, double dt, double g, int n_waveforms, int n_alloc,
                         const float* samples, const int32_t* offsets, const double* t_origin, int n_iter, float thresh,
                         float* q_out, int32_t* T_lo, int32_t* T_hi, double* t0, int32_t* z, int32_t* n_z, int z_stride,
                         int* status, cudaStream_t st);

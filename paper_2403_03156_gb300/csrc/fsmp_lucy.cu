@@ -12,8 +12,9 @@
 // Layout: one warp per waveform, its d, q-hat and ratio in shared memory (FP32), zero-padded so
 // that no tap needs a bounds check. Each lane computes four consecutive outputs: per group of
 // four taps it loads one aligned float4 of the source and does 16 FMAs, the previous float4
-// supplying the other operands (the loads are conflict-free 128-bit accesses and the kernel's
-// taps are broadcast). Arithmetic: 2 (n + L_V) L_V FMAs per iteration, FP32.
+// supplying the other operands (the loads are conflict-free 128-bit accesses). The taps travel
+// in the kernel's parameters and are read through the constant cache, which leaves the shared
+// memory pipe to the sources. Arithmetic: 2 (n + L_V) L_V FMAs per iteration, FP32.
 #include <math.h>
 
 #include "fsmp_internal.h"
@@ -22,6 +23,7 @@ namespace fsmp {
 namespace {
 
 constexpr int kLucyWarps = 4;  // waveforms per CTA
+constexpr int kLucyMaxJV = 32;  // groups of four taps the parameters carry (L_V <= 128)
 
 // Padded per-warp arrays: Q[kq + tau] (tau from -kq), Rr[kr + t] (t from -kr), d[t].
 struct LucyLayout {
@@ -47,6 +49,7 @@ __host__ __device__ inline size_t lucy_warp_bytes(int LV, int n_alloc) {
 }
 
 struct LucyArgs {
+  float4 taps[kLucyMaxJV];  // v(4j .. 4j+3), zero beyond L_V
   const float* samples;
   const int32_t* offsets;
   const double* t_origin;
@@ -62,7 +65,7 @@ struct LucyArgs {
   int* status;  // per waveform: 0, or FSMP_ST_INVALID when the window is empty or longer than n_alloc
 };
 
-__global__ void __launch_bounds__(kLucyWarps * 32) lucy_kernel(const float4* __restrict__ v4, const __grid_constant__ LucyArgs A) {
+__global__ void __launch_bounds__(kLucyWarps * 32) lucy_kernel(const __grid_constant__ LucyArgs A) {
   extern __shared__ __align__(16) float lsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wi = blockIdx.x * kLucyWarps + warp;
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kLucyWarps * 32) lucy_kernel(const float4* __r
 #pragma unroll 1
       for (int j = 0; j < jv; ++j) {
         const float4 nxt = Q4[(ly.kq + t0) / 4 - j - 1];
-        const float4 vv = v4[j];
+        const float4 vv = A.taps[j];
         // r = 0: q(t0 + k - 4j)
         a0 = fmaf(cur.x, vv.x, a0); a1 = fmaf(cur.y, vv.x, a1); a2 = fmaf(cur.z, vv.x, a2); a3 = fmaf(cur.w, vv.x, a3);
         // r = 1: q(t0 + k - 4j - 1)
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(kLucyWarps * 32) lucy_kernel(const float4* __r
 #pragma unroll 1
       for (int j = 0; j < jv; ++j) {
         const float4 nxt = R4[(ly.kr + u0) / 4 + j + 1];
-        const float4 vv = v4[j];
+        const float4 vv = A.taps[j];
         a0 = fmaf(cur.x, vv.x, a0); a1 = fmaf(cur.y, vv.x, a1); a2 = fmaf(cur.z, vv.x, a2); a3 = fmaf(cur.w, vv.x, a3);
         a0 = fmaf(cur.y, vv.y, a0); a1 = fmaf(cur.z, vv.y, a1); a2 = fmaf(cur.w, vv.y, a2); a3 = fmaf(nxt.x, vv.y, a3);
         a0 = fmaf(cur.z, vv.z, a0); a1 = fmaf(cur.w, vv.z, a1); a2 = fmaf(nxt.x, vv.z, a2); a3 = fmaf(nxt.y, vv.z, a3);
@@ -214,18 +217,23 @@ cudaError_t launch_lucy_taps(const float* V32, int LV, int R, float* v4, float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_lucy(const float* v4, float S, int LV, int R, double dt, double g, int n_waveforms, int n_alloc,
+cudaError_t launch_lucy(const float* v4_host, float S, int LV, int R, double dt, double g, int n_waveforms, int n_alloc,
                         const float* samples, const int32_t* offsets, const double* t_origin, int n_iter, float thresh,
                         float* q_out, int32_t* T_lo, int32_t* T_hi, double* t0, int32_t* z, int32_t* n_z, int z_stride,
                         int* status, cudaStream_t st) {
   if (n_waveforms <= 0) return cudaSuccess;
+  const int jv = (LV + 3) / 4;
+  if (jv > kLucyMaxJV) return cudaErrorInvalidValue;
   LucyArgs A;
+  for (int j = 0; j < kLucyMaxJV; ++j)
+    A.taps[j] = j < jv ? make_float4(v4_host[4 * j], v4_host[4 * j + 1], v4_host[4 * j + 2], v4_host[4 * j + 3])
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
   A.samples = samples; A.offsets = offsets; A.t_origin = t_origin;
   A.n_waveforms = n_waveforms; A.n_alloc = n_alloc; A.n_iter = n_iter; A.LV = LV; A.R = R; A.z_stride = z_stride;
   A.thresh = thresh; A.inv_S = 1.0f / S; A.dt = dt; A.g = g;
   A.q_out = q_out; A.T_lo = T_lo; A.T_hi = T_hi; A.t0 = t0; A.z = z; A.n_z = n_z; A.status = status;
   const unsigned blocks = (unsigned)((n_waveforms + kLucyWarps - 1) / kLucyWarps);
-  lucy_kernel<<<blocks, kLucyWarps * 32, lucy_smem_bytes(LV, n_alloc), st>>>(reinterpret_cast<const float4*>(v4), A);
+  lucy_kernel<<<blocks, kLucyWarps * 32, lucy_smem_bytes(LV, n_alloc), st>>>(A);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ struct fsmp_ctx {
   float* lucy_v4 = nullptr;
   float* lucy_S_dev = nullptr;
   float lucy_S = 0.0f;
+  std::vector<float> lucy_v4_host;
   struct PeSet {
     void* cinv = nullptr;    // C^-1 slots
     double* ws = nullptr;    // FP64 refresh workspace slots
@@ -759,6 +760,8 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   CK(cudaMalloc((void**)&c->lucy_S_dev, sizeof(float)));
   CK(launch_lucy_taps(c->V32, M.L_V, M.R, c->lucy_v4, c->lucy_S_dev, 0));
   CK(cudaMemcpy(&c->lucy_S, c->lucy_S_dev, sizeof(float), cudaMemcpyDeviceToHost));
+  c->lucy_v4_host.assign(4 * ((M.L_V + 3) / 4), 0.0f);
+  CK(cudaMemcpy(c->lucy_v4_host.data(), c->lucy_v4, sizeof(float) * c->lucy_v4_host.size(), cudaMemcpyDeviceToHost));
   c->n_smem_max = smem_n_max(c.get());
   int max_smem = (int)c->prop.sharedMemPerBlockOptin;
   CK(chain_kernel_attributes(p.precision, true, max_smem));
@@ -944,7 +947,7 @@ int fsmp_lucyddm(fsmp_ctx* c, const fsmp_lucy_batch* b, void* stream) {
   if (lucy_smem_bytes(c->M.L_V, n_alloc) > (size_t)c->prop.sharedMemPerBlockOptin)
     FAIL(FSMP_ERR_INVALID, "fsmp_lucyddm: window too long for shared memory");
   { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
-  cudaError_t e = launch_lucy(c->lucy_v4, c->lucy_S, c->M.L_V, c->M.R, c->M.dt, c->M.g, b->n_waveforms, n_alloc,
+  cudaError_t e = launch_lucy(c->lucy_v4_host.data(), c->lucy_S, c->M.L_V, c->M.R, c->M.dt, c->M.g, b->n_waveforms, n_alloc,
                               b->samples, b->offsets, b->t_origin_ns, b->n_iter, (float)b->thresh, b->q_out, b->T_lo,
                               b->T_hi, b->t0_init, b->z_init, b->n_init, b->z_stride, b->status,
                               (cudaStream_t)stream);
