@@ -158,7 +158,7 @@ def run_reference(args):
     b = wl["batch"]
     cores = os.cpu_count() or 1
     # each step: a bounded random sample, sized so warmup + steps end within a few minutes
-    per_step_target = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step_target = min(args.cpu_seconds, 20.0, 150.0 / max(1, args.steps + args.warmup))
     base, _, n_wf = oracle_rate(wl, per_step_target)
     from oracle import oracle
     from paper_2403_03156_gb300 import workloads
