@@ -442,10 +442,14 @@ struct PeSlots {
   int Ns;              // shared-memory tile of C^-1 (0: always global)
 };
 
-// FP64 refresh workspace of one chain: C (n_cap x n_cap) and four vectors of max(n_cap, n_alloc).
-__host__ __device__ inline int pe_lvec(int n_cap, int n_alloc) { return n_cap > n_alloc ? n_cap : n_alloc; }
+// FP64 refresh workspace of one chain: C (n_cap x n_cap), two vectors of max(n_cap, n_alloc), the
+// staged rows of one sweep block (kSweepBlock of them, transposed) and its diagonal block; every
+// part starts on a 16-byte boundary.
+constexpr int kSweepBlock = 8;
+__host__ __device__ inline int pe_lvec(int n_cap, int n_alloc) { return ((n_cap > n_alloc ? n_cap : n_alloc) + 1) & ~1; }
+__host__ __device__ inline size_t pe_ws_a(int n_cap) { return ((size_t)n_cap * n_cap + 1) & ~(size_t)1; }
 __host__ __device__ inline size_t pe_ws_doubles(int n_cap, int n_alloc) {
-  return (size_t)n_cap * n_cap + 4 * (size_t)pe_lvec(n_cap, n_alloc);
+  return pe_ws_a(n_cap) + (2 + kSweepBlock) * (size_t)pe_lvec(n_cap, n_alloc) + kSweepBlock * kSweepBlock;
 }
 
 // Charge hold: the state's charge summary q_cur holds from step q_from on; close it at step s.
@@ -473,22 +477,25 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   using C = typename PeTab<T>::C;
   RefreshOut out{0, 0.0, 0.0, 0.0};
   const int ws_ld = N > 0 ? N : 1;
-  double* A = ws;                               // C, then C^-1 (row-major N x N)
-  double* h = A + (size_t)n_cap * n_cap;        // A^T y
-  double* rowk = h + lvec;                      // staged pivot row
-  double* colk = rowk + lvec;                   // staged pivot column
+  constexpr int SB = BIG ? kSweepBlock : kSweepBlock / 2;  // fewer registers in the compact variant
+  double* A = ws;                               // C, then -C^-1 (row-major N x N, lower triangle)
+  double* h = A + pe_ws_a(n_cap);               // A^T y
+  double* rowk = h + lvec;                      // v
+  double* P = rowk + lvec;                      // a sweep block's rows, transposed (N x SB)
+  double* Kb = P + (size_t)kSweepBlock * lvec;  // the block's diagonal block (SB x SB, full)
   const double* V = M.V64;
   constexpr bool mix = MIX;
   const double mu = M.cm_mu[0], r = M.cm_r[0];  // the dynode model's (one component)
-  // C = diag(r_k) + A^T A (full, row-major); lanes over columns, RC rows at a time so that the
+  // C = diag(r_k) + A^T A (its lower triangle, row-major: entry (i, j) at i N + j for j <= i);
+  // lanes over columns, RC rows at a time so that the
   // table loads of the rows overlap. The unrolled forms (BIG: many PEs per chain) cost the
   // caller registers around the call, which the compact variant cannot spare.
-  constexpr int RC = BIG ? 4 : 1, RG = BIG ? 8 : 1;
+  constexpr int RC = BIG ? 4 : 1, RG = BIG ? 4 : 1;
 #pragma unroll 1
   for (int j = ln.sl; j < N; j += L) {
     const int jj = W.list[j];
 #pragma unroll 1
-    for (int i0 = 0; i0 < N; i0 += RC) {
+    for (int i0 = j; i0 < N; i0 += RC) {
       double c[RC];
 #pragma unroll
       for (int q = 0; q < RC; ++q) {
@@ -526,14 +533,15 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
       const double mk = M.cm_mu[ek];
       double hs = -M.cm_r[ek] * mk;  // (A^T A m)_k = sum_j C_kj m_j - r_k m_k
 #pragma unroll 1
-      for (int j = 0; j < N; ++j) hs = fma(A[(size_t)k * ws_ld + j], M.cm_mu[W.le[j]], hs);
+      for (int j = 0; j < N; ++j)
+        hs = fma(j <= k ? A[(size_t)k * ws_ld + j] : A[(size_t)j * ws_ld + k], M.cm_mu[W.le[j]], hs);
       h[k] = aw - hs;
       awt = fma(mk, aw, awt);
       rst = fma(mk, hs, rst);
     } else {
       double rs = -r;
 #pragma unroll 1
-      for (int j = 0; j < N; ++j) rs += A[(size_t)k * ws_ld + j];
+      for (int j = 0; j < N; ++j) rs += j <= k ? A[(size_t)k * ws_ld + j] : A[(size_t)j * ws_ld + k];
       h[k] = aw - mu * rs;
       awt += aw;
       rst += rs;
@@ -554,67 +562,131 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
     W.y[x] = (T)yv;
   }
   __syncwarp(ln.gm);
-  // Gauss-Jordan inversion in place with diagonal pivots (C is SPD: the pivots are the
-  // LDL^T pivots, all positive); log|C| = sum log pivot, kept as mantissa x 2^exponent
+  // Inversion by the symmetric sweep operator (Gauss-Jordan with diagonal pivots, kept
+  // symmetric): sweeping pivot p maps A_pp -> -1/A_pp, A_pj -> A_pj/A_pp, A_ip -> A_ip/A_pp and
+  // A_ij -> A_ij - A_ip A_pj/A_pp. Sweeps commute, sweeping every index leaves -C^-1, and only
+  // the lower triangle is kept. The pivots are C's LDL^T pivots (all positive for SPD C):
+  // log|C| = sum log pivot, kept as mantissa x 2^exponent. Pivots go SB at a time with one pass
+  // over the matrix per block K = [k0, k1): the block's rows A_K. (the panel) are swept first --
+  // they change only through their own entries -- then every other entry (i, j), i, j outside K,
+  // takes the rank-SB update A_ij -= sum_q P_iq G_qj, with P_i. = A_Ki before the sweep and
+  // G_.j = A_Kj after it. In lower-triangle storage lane j finds its panel entries A_Kj in row K
+  // (j < k0), in row j (j >= k1) or in the full copy Kb of A_KK (j in K).
   double pm = 1.0;
   int pe = 0;
 #pragma unroll 1
-  for (int k = 0; k < N; ++k) {
-    const double piv = A[(size_t)k * ws_ld + k];
-    if (!(piv > 0.0) || !isfinite(piv)) return out;
-    const double ip = 1.0 / piv;
-    int ex;
-    pm *= frexp(piv, &ex);
-    pe += ex;
-    pm = frexp(pm, &ex);
-    pe += ex;
-    // the pivot row and the row multipliers f_i = A_ik / pivot
+  for (int k0 = 0; k0 < N; k0 += SB) {
+    const int nb = min(SB, N - k0), k1 = k0 + nb;
 #pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      rowk[j] = A[(size_t)k * ws_ld + j];
-      colk[j] = A[(size_t)j * ws_ld + k] * ip;
+    for (int i = ln.sl; i < N; i += L) {
+      if (i >= k0 && i < k1) {
+        const int r = i - k0;
+#pragma unroll
+        for (int c = 0; c < SB; ++c)
+          Kb[r * SB + c] = c < nb ? (c <= r ? A[(size_t)i * ws_ld + k0 + c] : A[(size_t)(k0 + c) * ws_ld + i]) : 0.0;
+      } else {
+#pragma unroll
+        for (int q = 0; q < SB; ++q)
+          P[(size_t)i * SB + q] = q < nb ? (i > k0 ? A[(size_t)i * ws_ld + k0 + q] : A[(size_t)(k0 + q) * ws_ld + i]) : 0.0;
+      }
     }
     __syncwarp(ln.gm);
-    // rows i != k: A_ij -= f_i A_kj (A_ik = -f_i); row k: A_kj / pivot. Lanes over columns,
-    // RG rows at a time so that their loads overlap.
 #pragma unroll 1
-    for (int j = ln.sl; j < N; j += L) {
-      const double rkj = rowk[j];
+    for (int q = 0; q < nb; ++q) {
+      const int p = k0 + q;
+      const double piv = Kb[q * SB + q];
+      if (!(piv > 0.0) || !isfinite(piv)) return out;
+      const double ip = 1.0 / piv;
+      int ex;
+      pm *= frexp(piv, &ex);
+      pe += ex;
+      pm = frexp(pm, &ex);
+      pe += ex;
+      double f[SB];  // A_rp / pivot for the block's rows r
+#pragma unroll
+      for (int r = 0; r < SB; ++r) f[r] = r < nb ? Kb[r * SB + q] * ip : 0.0;
+      __syncwarp(ln.gm);
 #pragma unroll 1
-      for (int i0 = 0; i0 < N; i0 += RG) {
-        double x[RG], f[RG];
+      for (int j = ln.sl; j < N; j += L) {
+        double* b;
+        size_t st;
+        if (j < k0) { b = A + (size_t)k0 * ws_ld + j; st = ws_ld; }
+        else if (j >= k1) { b = A + (size_t)j * ws_ld + k0; st = 1; }
+        else { b = Kb + (j - k0); st = SB; }
+        const double apj = b[(size_t)q * st];
 #pragma unroll
-        for (int q = 0; q < RG; ++q) {
-          const int i = min(i0 + q, N - 1);
-          x[q] = A[(size_t)i * ws_ld + j];
-          f[q] = colk[i];
-        }
-#pragma unroll
-        for (int q = 0; q < RG; ++q) {
-          const int i = i0 + q;
-          if (i < N)
-            A[(size_t)i * ws_ld + j] = (i == k) ? ((j == k) ? ip : rkj * ip) : ((j == k) ? -f[q] : fma(-f[q], rkj, x[q]));
+        for (int r = 0; r < SB; ++r) {
+          if (r < nb) {
+            double* x = b + (size_t)r * st;
+            *x = (r == q) ? ((j == p) ? -ip : apj * ip) : ((j == p) ? f[r] : fma(-f[r], apj, *x));
+          }
         }
       }
+      __syncwarp(ln.gm);
+    }
+    // the entries outside the block's rows and columns, RG rows at a time so that their loads
+    // overlap
+#pragma unroll 1
+    for (int j = ln.sl; j < N; j += L) {
+      if (j >= k0 && j < k1) continue;
+      const double* b = j < k0 ? A + (size_t)k0 * ws_ld + j : A + (size_t)j * ws_ld + k0;
+      const size_t st = j < k0 ? (size_t)ws_ld : 1;
+      double g[SB];
+#pragma unroll
+      for (int q = 0; q < SB; ++q) g[q] = q < nb ? b[(size_t)q * st] : 0.0;
+      int i = j, hi = j < k0 ? k0 : N;
+#pragma unroll 1
+      for (int part = 0; part < 2; ++part) {
+#pragma unroll 1
+        for (; i < hi; i += RG) {
+          double x[RG];
+#pragma unroll
+          for (int t = 0; t < RG; ++t) x[t] = A[(size_t)min(i + t, hi - 1) * ws_ld + j];
+#pragma unroll
+          for (int t = 0; t < RG; ++t) {
+            const double2* Pi = reinterpret_cast<const double2*>(P + (size_t)min(i + t, hi - 1) * SB);
+#pragma unroll
+            for (int q = 0; q < SB / 2; ++q) {
+              const double2 pq = Pi[q];
+              x[t] = fma(-pq.x, g[2 * q], x[t]);
+              x[t] = fma(-pq.y, g[2 * q + 1], x[t]);
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < RG; ++t)
+            if (i + t < hi) A[(size_t)(i + t) * ws_ld + j] = x[t];
+        }
+        if (j >= k0) break;
+        i = k1;
+        hi = N;
+      }
+    }
+    __syncwarp(ln.gm);
+#pragma unroll 1
+    for (int e = ln.sl; e < nb * nb; e += L) {
+      const int r = e / nb, c = e - r * nb;
+      if (c <= r) A[(size_t)(k0 + r) * ws_ld + k0 + c] = Kb[r * SB + c];
     }
     __syncwarp(ln.gm);
   }
   const double logdetC = log(pm) + (double)pe * 0.6931471805599453;
-  // v = C^-1 h (C^-1 symmetric: lanes over columns; BIG: four partial sums)
+  // v = C^-1 h = -A h (entry (i, j) of the symmetric A from the lower triangle; lanes over rows;
+  // BIG: four partial sums)
 #pragma unroll 1
   for (int i = ln.sl; i < N; i += L) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    auto a_ij = [&](int j) { return j < i ? A[(size_t)i * ws_ld + j] : A[(size_t)j * ws_ld + i]; };
     int j = 0;
 #pragma unroll 1
     for (; BIG && j + 3 < N; j += 4) {
-      s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
-      s1 = fma(A[(size_t)(j + 1) * ws_ld + i], h[j + 1], s1);
-      s2 = fma(A[(size_t)(j + 2) * ws_ld + i], h[j + 2], s2);
-      s3 = fma(A[(size_t)(j + 3) * ws_ld + i], h[j + 3], s3);
+      s0 = fma(a_ij(j), h[j], s0);
+      s1 = fma(a_ij(j + 1), h[j + 1], s1);
+      s2 = fma(a_ij(j + 2), h[j + 2], s2);
+      s3 = fma(a_ij(j + 3), h[j + 3], s3);
     }
 #pragma unroll 1
-    for (; j < N; ++j) s0 = fma(A[(size_t)j * ws_ld + i], h[j], s0);
-    rowk[i] = (s0 + s1) + (s2 + s3);
+    for (; j < N; ++j) s0 = fma(a_ij(j), h[j], s0);
+    rowk[i] = -((s0 + s1) + (s2 + s3));
   }
   __syncwarp(ln.gm);
   double hv = 0.0;
@@ -627,7 +699,7 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   for (int e = ln.sl; e < tri(N); e += L) {
     int i, j;
     untri(e, i, j);
-    const double nv = A[(size_t)i * ws_ld + j];
+    const double nv = -A[(size_t)i * ws_ld + j];
     dmax = fmax(dmax, fabs(nv - c64(Cp[e])));
     amax = fmax(amax, fabs(nv));
     Cp[e] = cfrom64<C>(nv);
