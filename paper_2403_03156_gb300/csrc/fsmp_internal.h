@@ -252,7 +252,7 @@ cudaError_t measure_peaks(int sm_count, double* smem_gbs, double* fp64_tflops, d
 // workspace doubles per chain slot (FP32 mode); entries of a global C^-1 slot; ints of an N
 // histogram slot.
 size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int Ns);
-size_t pe_ws_slot_doubles(int n_cap, int n_alloc);
+size_t pe_ws_slot_doubles(int n_cap);
 size_t pe_c_entries(int n_cap);  // entries of a global C^-1 slot (packed triangle)
 size_t pe_c_entry_bytes(int precision);  // bytes of one C^-1 entry (a pair of FP64 or FP32 values)
 inline size_t pe_hist_ints(int n_cap) { return (size_t)n_cap + 1; }

@@ -16,7 +16,7 @@ size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int N
                                : pe_chain_bytes<float, 32>(M.n_cap, n_alloc, M.win_extra, Ns));
 }
 
-size_t pe_ws_slot_doubles(int n_cap, int n_alloc) { return pe_ws_doubles(n_cap, n_alloc); }
+size_t pe_ws_slot_doubles(int n_cap) { return pe_ws_doubles(n_cap); }
 
 size_t pe_c_entries(int n_cap) { return (size_t)tri(n_cap); }
 

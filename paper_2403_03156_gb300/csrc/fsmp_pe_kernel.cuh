@@ -442,14 +442,13 @@ struct PeSlots {
   int Ns;              // shared-memory tile of C^-1 (0: always global)
 };
 
-// FP64 refresh workspace of one chain: C (n_cap x n_cap), two vectors of max(n_cap, n_alloc), the
-// staged rows of one sweep block (kSweepBlock of them, transposed) and its diagonal block; every
-// part starts on a 16-byte boundary.
+// FP64 refresh workspace of one chain: C (n_cap x n_cap), h and v (n_cap each), a sweep block's
+// rows before and after its sweep (n_cap x kSweepBlock each) and its diagonal block; every part
+// starts on a 16-byte boundary.
 constexpr int kSweepBlock = 8;
-__host__ __device__ inline int pe_lvec(int n_cap, int n_alloc) { return ((n_cap > n_alloc ? n_cap : n_alloc) + 1) & ~1; }
-__host__ __device__ inline size_t pe_ws_a(int n_cap) { return ((size_t)n_cap * n_cap + 1) & ~(size_t)1; }
-__host__ __device__ inline size_t pe_ws_doubles(int n_cap, int n_alloc) {
-  return pe_ws_a(n_cap) + (2 + kSweepBlock) * (size_t)pe_lvec(n_cap, n_alloc) + kSweepBlock * kSweepBlock;
+__host__ __device__ inline size_t pe_ws_a2(size_t n) { return (n + 1) & ~(size_t)1; }
+__host__ __device__ inline size_t pe_ws_doubles(int n_cap) {
+  return pe_ws_a2((size_t)n_cap * n_cap) + (2 + 2 * kSweepBlock) * pe_ws_a2(n_cap) + kSweepBlock * kSweepBlock;
 }
 
 // Charge hold: the state's charge summary q_cur holds from step q_from on; close it at step s.
@@ -472,17 +471,19 @@ struct RefreshOut {
 // value (no address of the caller's locals escapes, so they stay in registers).
 template <typename T, bool BIG, int L, bool MIX>
 __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T> W, typename PeTab<T>::C* Cp,
-                                              double* ws, int n_cap, int lvec, const float* w, double wsq, int n,
+                                              double* ws, int n_cap, const float* w, double wsq, int n,
                                               int N, const Lanes<L> ln) {
   using C = typename PeTab<T>::C;
   RefreshOut out{0, 0.0, 0.0, 0.0};
   const int ws_ld = N > 0 ? N : 1;
   constexpr int SB = BIG ? kSweepBlock : kSweepBlock / 2;  // fewer registers in the compact variant
-  double* A = ws;                               // C, then -C^-1 (row-major N x N, lower triangle)
-  double* h = A + pe_ws_a(n_cap);               // A^T y
-  double* rowk = h + lvec;                      // v
-  double* P = rowk + lvec;                      // a sweep block's rows, transposed (N x SB)
-  double* Kb = P + (size_t)kSweepBlock * lvec;  // the block's diagonal block (SB x SB, full)
+  const size_t lv = pe_ws_a2(n_cap);
+  double* A = ws;                                 // C, then -C^-1 (row-major N x N, lower triangle)
+  double* h = A + pe_ws_a2((size_t)n_cap * n_cap);  // A^T y
+  double* rowk = h + lv;                          // v
+  double* P = rowk + lv;                          // a sweep block's rows before its sweep (N x SB)
+  double* Pn = P + (size_t)kSweepBlock * lv;      // the same rows during and after it
+  double* Kb = Pn + (size_t)kSweepBlock * lv;     // the block's diagonal block (SB x SB, full)
   const double* V = M.V64;
   constexpr bool mix = MIX;
   const double mu = M.cm_mu[0], r = M.cm_r[0];  // the dynode model's (one component)
@@ -534,14 +535,14 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
       double hs = -M.cm_r[ek] * mk;  // (A^T A m)_k = sum_j C_kj m_j - r_k m_k
 #pragma unroll 1
       for (int j = 0; j < N; ++j)
-        hs = fma(j <= k ? A[(size_t)k * ws_ld + j] : A[(size_t)j * ws_ld + k], M.cm_mu[W.le[j]], hs);
+        hs = fma(*(j <= k ? A + (size_t)k * ws_ld + j : A + (size_t)j * ws_ld + k), M.cm_mu[W.le[j]], hs);
       h[k] = aw - hs;
       awt = fma(mk, aw, awt);
       rst = fma(mk, hs, rst);
     } else {
       double rs = -r;
 #pragma unroll 1
-      for (int j = 0; j < N; ++j) rs += j <= k ? A[(size_t)k * ws_ld + j] : A[(size_t)j * ws_ld + k];
+      for (int j = 0; j < N; ++j) rs += *(j <= k ? A + (size_t)k * ws_ld + j : A + (size_t)j * ws_ld + k);
       h[k] = aw - mu * rs;
       awt += aw;
       rst += rs;
@@ -570,8 +571,8 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   // over the matrix per block K = [k0, k1): the block's rows A_K. (the panel) are swept first --
   // they change only through their own entries -- then every other entry (i, j), i, j outside K,
   // takes the rank-SB update A_ij -= sum_q P_iq G_qj, with P_i. = A_Ki before the sweep and
-  // G_.j = A_Kj after it. In lower-triangle storage lane j finds its panel entries A_Kj in row K
-  // (j < k0), in row j (j >= k1) or in the full copy Kb of A_KK (j in K).
+  // G_.j = A_Kj after it. The panel is swept in a staged copy: Pn_j. = A_Kj for j outside K, Kb
+  // = A_KK in full.
   double pm = 1.0;
   int pe = 0;
 #pragma unroll 1
@@ -583,11 +584,14 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
         const int r = i - k0;
 #pragma unroll
         for (int c = 0; c < SB; ++c)
-          Kb[r * SB + c] = c < nb ? (c <= r ? A[(size_t)i * ws_ld + k0 + c] : A[(size_t)(k0 + c) * ws_ld + i]) : 0.0;
+          Kb[r * SB + c] = c < nb ? *(c <= r ? A + (size_t)i * ws_ld + k0 + c : A + (size_t)(k0 + c) * ws_ld + i) : 0.0;
       } else {
 #pragma unroll
-        for (int q = 0; q < SB; ++q)
-          P[(size_t)i * SB + q] = q < nb ? (i > k0 ? A[(size_t)i * ws_ld + k0 + q] : A[(size_t)(k0 + q) * ws_ld + i]) : 0.0;
+        for (int q = 0; q < SB; ++q) {
+          const double a = q < nb ? *(i > k0 ? A + (size_t)i * ws_ld + k0 + q : A + (size_t)(k0 + q) * ws_ld + i) : 0.0;
+          P[(size_t)i * SB + q] = a;
+          Pn[(size_t)i * SB + q] = a;
+        }
       }
     }
     __syncwarp(ln.gm);
@@ -608,32 +612,31 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
       __syncwarp(ln.gm);
 #pragma unroll 1
       for (int j = ln.sl; j < N; j += L) {
-        double* b;
-        size_t st;
-        if (j < k0) { b = A + (size_t)k0 * ws_ld + j; st = ws_ld; }
-        else if (j >= k1) { b = A + (size_t)j * ws_ld + k0; st = 1; }
-        else { b = Kb + (j - k0); st = SB; }
-        const double apj = b[(size_t)q * st];
+        const bool inK = j >= k0 && j < k1;
+        double* b = inK ? Kb + (j - k0) : Pn + (size_t)j * SB;
+        const int st = inK ? SB : 1;
+        const double apj = b[q * st];
 #pragma unroll
         for (int r = 0; r < SB; ++r) {
           if (r < nb) {
-            double* x = b + (size_t)r * st;
+            double* x = b + r * st;
             *x = (r == q) ? ((j == p) ? -ip : apj * ip) : ((j == p) ? f[r] : fma(-f[r], apj, *x));
           }
         }
       }
       __syncwarp(ln.gm);
     }
-    // the entries outside the block's rows and columns, RG rows at a time so that their loads
-    // overlap
+    // the swept panel back into the matrix, and the entries outside the block's rows and
+    // columns, RG rows at a time so that their loads overlap
 #pragma unroll 1
     for (int j = ln.sl; j < N; j += L) {
       if (j >= k0 && j < k1) continue;
-      const double* b = j < k0 ? A + (size_t)k0 * ws_ld + j : A + (size_t)j * ws_ld + k0;
-      const size_t st = j < k0 ? (size_t)ws_ld : 1;
       double g[SB];
 #pragma unroll
-      for (int q = 0; q < SB; ++q) g[q] = q < nb ? b[(size_t)q * st] : 0.0;
+      for (int q = 0; q < SB; ++q) g[q] = Pn[(size_t)j * SB + q];
+#pragma unroll
+      for (int q = 0; q < SB; ++q)
+        if (q < nb) *(j < k0 ? A + (size_t)(k0 + q) * ws_ld + j : A + (size_t)j * ws_ld + k0 + q) = g[q];
       int i = j, hi = j < k0 ? k0 : N;
 #pragma unroll 1
       for (int part = 0; part < 2; ++part) {
@@ -661,7 +664,6 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
         hi = N;
       }
     }
-    __syncwarp(ln.gm);
 #pragma unroll 1
     for (int e = ln.sl; e < nb * nb; e += L) {
       const int r = e / nb, c = e - r * nb;
@@ -675,7 +677,7 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
 #pragma unroll 1
   for (int i = ln.sl; i < N; i += L) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    auto a_ij = [&](int j) { return j < i ? A[(size_t)i * ws_ld + j] : A[(size_t)j * ws_ld + i]; };
+    auto a_ij = [&](int j) { return *(j < i ? A + (size_t)i * ws_ld + j : A + (size_t)j * ws_ld + i); };
     int j = 0;
 #pragma unroll 1
     for (; BIG && j + 3 < N; j += 4) {
@@ -1077,7 +1079,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         C qs = czero<C>();
         if constexpr (fp32) {
           // FP32 mode: the FP64 rebuild
-          const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, ni, ln);
+          const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, w, S.wsq, n, ni, ln);
           ok = ro.ok != 0;
           if (ok && ln.sl == 0) { S.logdet = ro.logdet; S.logL = ro.logL; }
         } else {
@@ -1374,7 +1376,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
         __syncwarp(ln.gm);
         if (fp32 && M.refresh_every > 0 && S.n_acc_refresh >= M.refresh_every) {
-          const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, ln);
+          const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, w, S.wsq, n, N, ln);
           C qr = czero<C>();
           for (int i = ln.sl; i < N; i += L) qr = cadd(qr, W.v[i]);
           qr = csum(qr, ln);
@@ -1427,7 +1429,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     // ------------------------------------------------------------- chain end
     if (fp32 && M.refresh_every > 0 && S.n_acc_refresh > 0) {
       // the reported log-likelihood and log|Sigma| come from an FP64 rebuild
-      const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, pe_lvec(n_cap, n_alloc), w, S.wsq, n, N, ln);
+      const RefreshOut ro = pe_refresh<T, BIG, L, MIX>(M, W, Cp, ws, n_cap, w, S.wsq, n, N, ln);
       if (ln.sl == 0) {
         if (ro.ok) {
           S.logdet = ro.logdet; S.logL = ro.logL;

@@ -819,7 +819,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     c->pe_c_stride = c->pe_tile < p.n_cap ? pe_c_entries(p.n_cap) : 0;
     // the FP64 rebuild runs in FP32 mode every K accepts, and in both modes for a chain that
     // starts from a given z
-    c->pe_ws_stride = pe_ws_slot_doubles(p.n_cap, p.n_max);
+    c->pe_ws_stride = pe_ws_slot_doubles(p.n_cap);
     for (int i = 0; i <= p.n_streams; ++i) {
       fsmp_ctx::PeSet ps;
       const size_t cb = c->pe_c_stride * esz * (size_t)slots, wb = c->pe_ws_stride * 8 * (size_t)slots;
