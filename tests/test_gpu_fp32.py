@@ -62,7 +62,7 @@ def test_fp32_tracks_oracle_step_by_step(lib, orc, refresh_every, kernel):
     assert np.median(pref) >= 300, np.sort(pref)[:20]
     err, ref = _la_err(t_gpu, t_orc, pref)
     # where the decision is in play (|log alpha| < 20) the error must be small in absolute
-    # terms; the paper's own FP32 check found |error of Delta nu| mainly within 1.0
+    # terms; the paper's own FP32 check (Sec. 3.1) put most Delta nu errors below 1
     near = np.abs(ref) < 20
     tol = 5e-3 if refresh_every == 1 else 2e-2
     assert np.percentile(err[near], 99) < tol, np.percentile(err[near], [50, 99, 100])
