@@ -336,8 +336,11 @@ int fsmp_autotune(fsmp_ctx* ctx, const fsmp_device_batch* batch, int sample, int
  *    kernel's shared-memory limit), and the first call with a new set of model parameters
  *    rebuilds the tables and synchronises `stream` once: make such a call before any stream
  *    capture.
- *  - All calls share the array and leave it holding the last call's tables and workspaces;
- *    calls that overlap on the GPU race on it.
+ *  - All calls share the array and leave it holding the last call's tables and workspaces.
+ *    Calls on one stream run in order and are safe whatever their parameters; calls on
+ *    different streams that overlap on the GPU race on it.
+ *  - params are checked as fsmp_create checks them (threads_per_chain 0 or a multiple of 32
+ *    in 32..512, finite mu_q, ...) before anything is enqueued.
  * The current device is restored on return. Returns FSMP_OK, FSMP_ERR_INVALID or
  * FSMP_ERR_CUDA. */
 int fsmp_run_device_noalloc(const fsmp_params* params, const fsmp_device_batch* batch, void* stream);
@@ -354,6 +357,17 @@ int fsmp_get_info(fsmp_ctx* ctx, fsmp_info* out);
  * key). ctrs and out are host arrays of 4 * n words. Synchronous. */
 int fsmp_philox_blocks(fsmp_ctx* ctx, const uint64_t key[2], const uint64_t* ctrs, int n,
                        uint64_t* out);
+
+/* lambda_FSMP (Eq. (reduce-mu0), Sec. 2.2) of given N histograms, computed on the GPU by the
+ * same device function every chain of fsmp_run_device ends with (testing aid): out[i] = the
+ * maximiser over lambda >= 0 of -lambda + log sum_N h_i[N] (lambda / lambda0[i])^N, with h_i =
+ * hist[i (n_max + 1) .. (i + 1)(n_max + 1)) the counts of N = 0 .. n_max, on `lanes` (32 or 16)
+ * lanes per histogram as a chain of that lane count would run it; 0 if only N = 0 was counted,
+ * NaN if no N was. hist, lambda0 and out are host arrays of n_hist entries (hist of
+ * n_hist (n_max + 1)). Synchronous. Returns FSMP_OK, FSMP_ERR_INVALID, FSMP_ERR_NOMEM or
+ * FSMP_ERR_CUDA. */
+int fsmp_lambda_mle(fsmp_ctx* ctx, const int32_t* hist, int n_hist, int n_max, const double* lambda0, int lanes,
+                    double* out);
 
 /* Roofline denominators measured on the context's GPU (the paper has no counterpart; it is
  * a measurement aid): shared-memory load bandwidth in GB/s (16-byte loads, 4 CTAs per SM),

@@ -272,6 +272,10 @@ bool pe_lanes_ok(int lanes, int n_cap);
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
                       void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
                       cudaStream_t st);
+// lambda_FSMP of n_hist histograms of n_max + 1 counts on `lanes` (32 or 16) lanes each, by the
+// device function the chain kernels end with (testing aid; fsmp_pe.cu).
+cudaError_t launch_lambda_mle(const int* h, int n_hist, int n_max, const double* lambda0, double* out, int lanes,
+                              cudaStream_t st);
 // LucyDDM (fsmp_lucy.cu): shared memory per CTA for windows up to n_alloc; the kernel taps
 // v(m) = V(m dt) / S, padded to whole groups of four, and S (on the device); the deconvolution
 // launch, given the taps in host memory (they travel in the kernel's parameters).
@@ -282,6 +286,8 @@ cudaError_t launch_lucy(const float* v4_host, float S, int LV, int R, double dt,
                         const float* samples, const int32_t* offsets, const double* t_origin, int n_iter, float thresh,
                         float* q_out, int32_t* T_lo, int32_t* T_hi, double* t0, int32_t* z, int32_t* n_z, int z_stride,
                         int* status, cudaStream_t st);
+// FSMP_OK if the model and engine parameters are valid, else FSMP_ERR_INVALID (fsmp_runtime.cu).
+int validate_params(const fsmp_params* p);
 // Set (or, with what == nullptr, clear) the calling thread's fsmp_last_error() message.
 void record_error(const char* what, const char* detail);
 

@@ -11,10 +11,11 @@
 // builds the tables into the array and synchronises the stream once to read the SER length.
 // Such a call should therefore come before any stream capture.
 //
-// Every call shares the array and leaves its contents behind for the next call: calls that
-// overlap on the GPU (on different streams, or on one stream with different parameters
-// before the previous call finished) race on it. Nothing in the array has to start at zero:
-// every table entry and workspace word is written before it is read.
+// Every call shares the array and leaves its contents behind for the next call. Work on one
+// stream runs in order, so calls on one stream are safe whatever their parameters (a table
+// rebuild follows the previous call's kernel on that stream). Calls on different streams that
+// overlap on the GPU race on the array. Nothing in the array has to start at zero: every table
+// entry and workspace word is written before it is read.
 #include <math.h>
 #include <string.h>
 
@@ -96,15 +97,10 @@ extern "C" int fsmp_run_device_noalloc(const fsmp_params* p, const fsmp_device_b
   record_error(nullptr, nullptr);
   if (!p || !b) return fail(FSMP_ERR_INVALID, "null argument");
   if (p->precision != FSMP_FP32_REFRESH) return fail(FSMP_ERR_INVALID, "precision must be FSMP_FP32_REFRESH");
-  if (!(p->dt_sample_ns > 0) || !(p->grid_ns > 0)) return fail(FSMP_ERR_INVALID, "bad sample period or grid");
-  const double rr = p->dt_sample_ns / p->grid_ns;
-  const long R = lround(rr);
-  if (R < 1 || R > 64 || fabs(rr - (double)R) > 1e-9 * rr) return fail(FSMP_ERR_INVALID, "dt_sample_ns / grid_ns must be an integer in [1, 64]");
-  if (!(p->ser_sigma > 0) || !(p->ser_tau > 0) || !(p->ser_eps > 0) || !(p->ser_eps < 1) ||
-      (p->ser_kind != 0 && p->ser_kind != 1) || (p->ser_kind == 1 && (!(p->ser_under_sigma > 0) || !(p->ser_under_tau > 0))) ||
-      (p->phi_kind != 0 && p->phi_kind != 1) || !(p->phi_p1 > 0) || !(p->phi_p2 > 0) || !(p->phi_support_ns > 0) ||
-      !(p->sigma_q > 0) || !(p->sigma_noise > 0) || !(p->t0_hi >= p->t0_lo) || !(p->jump_J > 0) || !(p->jump_J <= 0.5))
-    return fail(FSMP_ERR_INVALID, "invalid model parameters");
+  // the checks fsmp_create makes (threads_per_chain a multiple of 32 in 32..512, finite mu_q,
+  // an integer dt / grid ratio, ...), then this entry point's own limits
+  if (validate_params(p) != FSMP_OK) return fail(FSMP_ERR_INVALID, "invalid fsmp_params (the checks of fsmp_create)");
+  const long R = lround(p->dt_sample_ns / p->grid_ns);
   if (p->n_mix != 0) return fail(FSMP_ERR_INVALID, "the MCP charge mixture runs only in the PE-space kernel");
   if (p->n_cap < 1 || p->n_cap > kNoallocMaxCap) return fail(FSMP_ERR_INVALID, "n_cap exceeds the static-scratch limit of 64");
   const int n_max = b->n_max_hint > 0 ? b->n_max_hint : p->n_max;

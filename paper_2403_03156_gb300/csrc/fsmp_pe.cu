@@ -49,6 +49,28 @@ int pe_kernel_occupancy(int precision, int threads, size_t smem, bool big, int l
   return pe_occupancy<false>(precision, threads, smem, big, lanes);
 }
 
+// lambda_FSMP of given N histograms (testing aid): the device function every chain ends with,
+// one histogram per group of L lanes. Histogram i is h[i * (n_max + 1) .. (i + 1) * (n_max + 1)).
+template <int L>
+__global__ void lambda_mle_kernel(const int* __restrict__ h, int n_hist, int n_max, const double* __restrict__ lambda0,
+                                  double* __restrict__ out) {
+  const Lanes<L> ln = pe_lanes<L>();
+  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / L);
+  if (i >= n_hist) return;  // i is the same on every lane of a group
+  const double lam = group_lambda_mle<L>(h + (size_t)i * (n_max + 1), n_max, lambda0[i], ln.sl, ln.gm);
+  if (ln.sl == 0) out[i] = lam;
+}
+
+cudaError_t launch_lambda_mle(const int* h, int n_hist, int n_max, const double* lambda0, double* out, int lanes,
+                              cudaStream_t st) {
+  if (n_hist <= 0) return cudaSuccess;
+  const int threads = 128, per_block = threads / lanes;
+  const unsigned blocks = (unsigned)((n_hist + per_block - 1) / per_block);
+  if (lanes == 16) lambda_mle_kernel<16><<<blocks, threads, 0, st>>>(h, n_hist, n_max, lambda0, out);
+  else lambda_mle_kernel<32><<<blocks, threads, 0, st>>>(h, n_hist, n_max, lambda0, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pe(const DevModel& M, const BatchView& B, int warps, int lanes, int ctas, int Ns, size_t smem,
                       void* cinv, size_t c_stride, double* ws, size_t ws_stride, int* hist, int* counter,
                       cudaStream_t st) {

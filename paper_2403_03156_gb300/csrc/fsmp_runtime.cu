@@ -131,6 +131,9 @@ struct fsmp_ctx {
   int fatal = FSMP_OK;
   std::thread worker;
   int next_stream = 0;
+  // the last fsmp_run_device / fsmp_lucyddm work of each caller stream (fsmp_destroy waits on it)
+  std::mutex user_mu;
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> user_events;
 };
 
 namespace {
@@ -170,7 +173,10 @@ int make_shape(fsmp_ctx* c, int n_alloc, bool smemP, LaunchShape* out) {
   return FSMP_OK;
 }
 
-int validate_params(const fsmp_params* p) {
+}  // namespace
+
+// Checks of fsmp_params shared by fsmp_create and fsmp_run_device_noalloc.
+int fsmp::validate_params(const fsmp_params* p) {
   if (!p) return FSMP_ERR_INVALID;
   if (!(p->dt_sample_ns > 0) || !(p->grid_ns > 0)) return FSMP_ERR_INVALID;
   double r = p->dt_sample_ns / p->grid_ns;
@@ -209,6 +215,8 @@ int validate_params(const fsmp_params* p) {
   return FSMP_OK;
 }
 
+namespace {
+
 void free_ctx(fsmp_ctx* c) {
   if (!c) return;
   cudaFree(c->V64); cudaFree(c->V32); cudaFree(c->phi); cudaFree(c->logphi); cudaFree(c->cphi);
@@ -219,6 +227,7 @@ void free_ctx(fsmp_ctx* c) {
   for (auto& ps : c->pe_sets) { cudaFree(ps.cinv); cudaFree(ps.ws); cudaFree(ps.hist); cudaFree(ps.counter); }
   for (auto s : c->streams) cudaStreamDestroy(s);
   if (c->gmem_stream) cudaStreamDestroy(c->gmem_stream);
+  for (auto& se : c->user_events) cudaEventDestroy(se.second);
   delete c;
 }
 
@@ -593,6 +602,23 @@ void worker_main(fsmp_ctx* c) {
   }
 }
 
+// Mark the end of work the caller enqueued on `st` through the context (fsmp_destroy waits
+// for it). Skipped while `st` is being captured into a graph: the graph's launches are the
+// caller's to wait for.
+int note_user_work(fsmp_ctx* c, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return FSMP_OK;
+  std::lock_guard<std::mutex> lk(c->user_mu);
+  cudaEvent_t ev = nullptr;
+  for (auto& se : c->user_events)
+    if (se.first == st) ev = se.second;
+  if (!ev) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return FSMP_ERR_CUDA;
+    c->user_events.emplace_back(st, ev);
+  }
+  return cudaEventRecord(ev, st) == cudaSuccess ? FSMP_OK : FSMP_ERR_CUDA;
+}
+
 int copy_batch(fsmp_ctx* c, const fsmp_batch* b, Request* r) {
   if (!b->samples || !b->offsets || !b->lambda0 || b->n_waveforms < 1 || b->n_steps < 0 || b->burn_in < 0)
     return FSMP_ERR_INVALID;
@@ -672,6 +698,10 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   if (c->p.n_streams <= 0) c->p.n_streams = 4;
   CK(cudaSetDevice(c->p.device));
   CK(cudaGetDeviceProperties(&c->prop, c->p.device));
+  // the context's own stream for its set-up work (and later for the work that shares the
+  // context's Sigma^-1 scratch): set-up waits on it alone, never on other work of the device
+  CK(cudaStreamCreateWithFlags(&c->gmem_stream, cudaStreamNonBlocking));
+  cudaStream_t setup = c->gmem_stream;
   const fsmp_params& p = c->p;
   DevModel& M = c->M;
   M.R = (int)lround(p.dt_sample_ns / p.grid_ns);
@@ -731,10 +761,10 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   CK(cudaMalloc(&c->cphi32, sizeof(float) * (2 * M.D + 1)));
   CK(cudaMalloc(&c->Lt_dev, sizeof(int)));
   CK(launch_tables(p, M.R, M.D, m_end, c->V64, c->V32, c->phi, c->logphi, c->cphi, c->phi32,
-                   c->logphi32, c->cphi32, c->Lt_dev, c->scan, 0));
+                   c->logphi32, c->cphi32, c->Lt_dev, c->scan, setup));
   int Lt = 0;
-  CK(cudaMemcpy(&Lt, c->Lt_dev, sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpyAsync(&Lt, c->Lt_dev, sizeof(int), cudaMemcpyDeviceToHost, setup));
+  CK(cudaStreamSynchronize(setup));
   if (Lt < M.R) FAIL(FSMP_ERR_INVALID, "SER table shorter than one sample");
   M.Lt = Lt;
   M.L_V = Lt / M.R;
@@ -750,18 +780,19 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     CK(cudaMalloc(&c->tc64, sizeof(double) * ntc));
     CK(cudaMalloc(&c->tc32, sizeof(float) * ntc));
     CK(cudaMalloc(&c->tcff, 2 * sizeof(float) * ntc));
-    CK(launch_xcorr_table(c->V64, M.Lt, M.R, c->tc64, c->tc32, 0));
-    CK(launch_split_ff(c->tc64, c->tcff, ntc, 0));
-    CK(cudaDeviceSynchronize());
+    CK(launch_xcorr_table(c->V64, M.Lt, M.R, c->tc64, c->tc32, setup));
+    CK(launch_split_ff(c->tc64, c->tcff, ntc, setup));
     M.tc64 = c->tc64; M.tc32 = c->tc32; M.tcff = c->tcff; M.tcM = xcorr_rows(M.Lt, M.R);
   }
   // LucyDDM taps
   CK(cudaMalloc((void**)&c->lucy_v4, sizeof(float) * 4 * ((M.L_V + 3) / 4)));
   CK(cudaMalloc((void**)&c->lucy_S_dev, sizeof(float)));
-  CK(launch_lucy_taps(c->V32, M.L_V, M.R, c->lucy_v4, c->lucy_S_dev, 0));
-  CK(cudaMemcpy(&c->lucy_S, c->lucy_S_dev, sizeof(float), cudaMemcpyDeviceToHost));
+  CK(launch_lucy_taps(c->V32, M.L_V, M.R, c->lucy_v4, c->lucy_S_dev, setup));
   c->lucy_v4_host.assign(4 * ((M.L_V + 3) / 4), 0.0f);
-  CK(cudaMemcpy(c->lucy_v4_host.data(), c->lucy_v4, sizeof(float) * c->lucy_v4_host.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&c->lucy_S, c->lucy_S_dev, sizeof(float), cudaMemcpyDeviceToHost, setup));
+  CK(cudaMemcpyAsync(c->lucy_v4_host.data(), c->lucy_v4, sizeof(float) * c->lucy_v4_host.size(),
+                     cudaMemcpyDeviceToHost, setup));
+  CK(cudaStreamSynchronize(setup));
   c->n_smem_max = smem_n_max(c.get());
   int max_smem = (int)c->prop.sharedMemPerBlockOptin;
   CK(chain_kernel_attributes(p.precision, true, max_smem));
@@ -837,7 +868,6 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
     CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     c->streams.push_back(s);
   }
-  CK(cudaStreamCreateWithFlags(&c->gmem_stream, cudaStreamNonBlocking));
   fsmp_ctx* raw = c.release();
   raw->worker = std::thread(worker_main, raw);
   *out = raw;
@@ -899,7 +929,14 @@ int fsmp_destroy(fsmp_ctx* c) {
   c->cv_work.notify_all();
   if (c->worker.joinable()) c->worker.join();
   cudaSetDevice(c->p.device);
-  cudaDeviceSynchronize();
+  // wait for the context's own streams and for the last work the caller enqueued through the
+  // context on each of its streams (fsmp_run_device, fsmp_lucyddm), not for the whole device
+  for (cudaStream_t s : c->streams) cudaStreamSynchronize(s);
+  if (c->gmem_stream) cudaStreamSynchronize(c->gmem_stream);
+  {
+    std::lock_guard<std::mutex> lk(c->user_mu);
+    for (auto& se : c->user_events) cudaEventSynchronize(se.second);
+  }
   for (Request* r : c->done) delete r;
   for (Request* r : c->returned) delete r;
   free_ctx(c);
@@ -934,7 +971,9 @@ int fsmp_run_device(fsmp_ctx* c, const fsmp_device_batch* b, void* stream) {
     B.pe_hist = b->pe_hist; B.pe_hist_width = b->pe_hist_width;
   }
   { cudaError_t e_ = cudaSetDevice(c->p.device); if (e_ != cudaSuccess) { set_error("cudaSetDevice", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
-  return run_view(c, B, (cudaStream_t)stream, (int)c->streams.size());
+  const int rc = run_view(c, B, (cudaStream_t)stream, (int)c->streams.size());
+  if (rc != FSMP_OK) return rc;
+  return note_user_work(c, (cudaStream_t)stream);
 }
 
 int fsmp_lucyddm(fsmp_ctx* c, const fsmp_lucy_batch* b, void* stream) {
@@ -953,7 +992,7 @@ int fsmp_lucyddm(fsmp_ctx* c, const fsmp_lucy_batch* b, void* stream) {
                               (cudaStream_t)stream);
   c->n_launches++;
   if (e != cudaSuccess) { set_error("launch_lucy", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
-  return FSMP_OK;
+  return note_user_work(c, (cudaStream_t)stream);
 }
 
 int fsmp_gelman_rubin(const fsmp_summary* chains, int m, int field, double* rhat) {
@@ -1153,6 +1192,36 @@ int fsmp_philox_blocks(fsmp_ctx* c, const uint64_t key[2], const uint64_t* ctrs,
     rc = FSMP_ERR_CUDA;
   cudaFree(dc);
   cudaFree(dout);
+  return rc;
+}
+
+int fsmp_lambda_mle(fsmp_ctx* c, const int32_t* hist, int n_hist, int n_max, const double* lambda0, int lanes,
+                    double* out) {
+  g_last_error[0] = 0;
+  if (!c || !hist || !lambda0 || !out || n_hist < 0 || n_max < 0 || (lanes != 16 && lanes != 32))
+    FAIL(FSMP_ERR_INVALID, "fsmp_lambda_mle: bad arguments");
+  for (int i = 0; i < n_hist; ++i)
+    if (!(lambda0[i] > 0.0)) FAIL(FSMP_ERR_INVALID, "fsmp_lambda_mle: lambda0 must be positive");
+  if (n_hist == 0) return FSMP_OK;
+  CK(cudaSetDevice(c->p.device));
+  const size_t hb = sizeof(int32_t) * (size_t)n_hist * (n_max + 1), lb = sizeof(double) * (size_t)n_hist;
+  int* dh = nullptr;
+  double *dl = nullptr, *dout = nullptr;
+  int rc = FSMP_OK;
+  if (cudaMalloc(&dh, hb) != cudaSuccess || cudaMalloc(&dl, lb) != cudaSuccess || cudaMalloc(&dout, lb) != cudaSuccess) {
+    rc = FSMP_ERR_NOMEM;
+  } else {
+    cudaStream_t st = c->gmem_stream;
+    if (cudaMemcpyAsync(dh, hist, hb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dl, lambda0, lb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        launch_lambda_mle(dh, n_hist, n_max, dl, dout, lanes, st) != cudaSuccess ||
+        cudaMemcpyAsync(out, dout, lb, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      rc = FSMP_ERR_CUDA;
+  }
+  cudaFree(dh);
+  cudaFree(dl);
+  cudaFree(dout);
+  if (rc == FSMP_ERR_CUDA) set_error("fsmp_lambda_mle", "a copy or the launch failed", __LINE__);
   return rc;
 }
 

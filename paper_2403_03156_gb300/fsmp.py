@@ -97,7 +97,7 @@ class Info(ctypes.Structure):
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
            "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc", "fsmp_autotune",
-           "fsmp_gelman_rubin", "fsmp_lucyddm"]
+           "fsmp_gelman_rubin", "fsmp_lucyddm", "fsmp_lambda_mle"]
 
 _lib = None
 
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = False):
     L.fsmp_autotune.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _c_int, _c_int, ctypes.POINTER(Tune)]
     L.fsmp_gelman_rubin.argtypes = [_vp, _c_int, _c_int, ctypes.POINTER(_c_double)]
     L.fsmp_lucyddm.argtypes = [_vp, ctypes.POINTER(LucyBatch), _vp]
+    L.fsmp_lambda_mle.argtypes = [_vp, _vp, _c_int, _c_int, _vp, _c_int, _vp]
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
     L.fsmp_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
     L.fsmp_philox_blocks.argtypes = [_vp, ctypes.POINTER(_c_u64), _vp, _c_int, _vp]
@@ -380,6 +381,16 @@ class Context:
                "fsmp_measure_peaks")
         return dict(smem_gbs=a.value, fp64_tflops=b.value, fp32_tflops=c.value)
 
+    def lambda_mle(self, hist, lambda0, lanes: int = 32) -> np.ndarray:
+        """fsmp_lambda_mle: lambda_FSMP of each row of ``hist`` (counts of N = 0 .. n_max) on
+        the GPU, by the device function the chains end with."""
+        h = np.ascontiguousarray(np.atleast_2d(hist), np.int32)
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lambda0, np.float64), (h.shape[0],)))
+        out = np.zeros(h.shape[0], np.float64)
+        _check(load().fsmp_lambda_mle(self.h, h.ctypes.data, h.shape[0], h.shape[1] - 1, lam.ctypes.data, int(lanes),
+                                      out.ctypes.data), "fsmp_lambda_mle")
+        return out
+
     def philox_blocks(self, key, ctrs):
         ctrs = np.ascontiguousarray(ctrs, np.uint64)
         out = np.zeros_like(ctrs)
@@ -423,8 +434,8 @@ def run_device_noalloc(params: dict, dev: dict, n_steps: int, burn_in: int = 0, 
     """Run chains on device tensors (as ``Context.run_device``) without allocating device
     memory, for callers that cannot allocate: code under a framework allocator that owns all
     device memory, or a service that forbids allocation after start-up. Needs no Context; its
-    scratch is one static 64 MiB device array shared by all calls, so calls must not overlap
-    on the GPU. FP32 mode only, windows of at most 256 samples, n_cap at most 64. The first
+    scratch is one static 64 MiB device array shared by all calls: calls on one stream run in
+    order, calls on different streams must not overlap on the GPU. FP32 mode only, windows of at most 256 samples, n_cap at most 64. The first
     call on a device, and the first after the model parameters change, synchronise ``stream``
     once; make such a call before any stream capture."""
     prm = make_params(params)

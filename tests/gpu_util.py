@@ -28,5 +28,13 @@ def compare_traces(gpu, orc, rel=1e-9):
         b = np.maximum(np.where(nan_b, 0.0, b), LA_FLOOR)
         err = np.abs(a - b) / np.maximum(1.0, np.abs(b))
         assert err.max() <= rel, (f, err.max(), np.unravel_index(err.argmax(), err.shape))
-    np.testing.assert_array_equal(gpu["lu"], orc["lu"]) if False else None
+    # The log uniforms each side compared its ratios with: the same Philox outputs, the same
+    # u = ((x >> 11) + 0.5) 2^-53 and the same order of use within a step (u2 for t0, u7 for
+    # the jump), up to the last-place rounding of the two libm logs. lu0 exists only where t0
+    # was proposed.
+    for f, where in (("lu", np.ones(orc.shape, bool)), ("lu0", (orc["flags"] & 1) != 0)):
+        a, b = gpu[f][where], orc[f][where]
+        assert np.all(np.isfinite(a)) and np.all(np.isfinite(b)), f
+        err = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+        assert err.max(initial=0.0) <= 1e-15, (f, err.max(), np.unravel_index(err.argmax(), err.shape))
     return True

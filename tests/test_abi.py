@@ -94,3 +94,23 @@ def test_library_has_no_undefined_internal_symbols():
         pytest.skip("nm not available")
     out = subprocess.check_output([nm, "-u", "-C", build.build()]).decode()
     assert not [line for line in out.splitlines() if "fsmp::" in line]
+
+
+def test_noalloc_checks_params_like_create_without_a_gpu():
+    """fsmp_run_device_noalloc applies fsmp_create's parameter checks before it touches a
+    device: a CTA of 48 threads (not a whole number of warps), or a non-finite mu_q, is
+    refused with FSMP_ERR_INVALID and nothing is launched (this runs on a host with no GPU)."""
+    from paper_2403_03156_gb300 import build, fsmp, workloads
+    build.build()
+    L = fsmp.load()
+    base = dict(workloads.CONFIGS["plain_fp64_256x128"]["params"], precision=fsmp.FP32_REFRESH, n_cap=32,
+                n_max=128)
+    b = fsmp.DeviceBatch()
+    b.n_waveforms, b.n_steps, b.n_max_hint = 1, 10, 128
+    # stand-in addresses: the call must fail before any pointer is used
+    b.samples = b.offsets = b.lambda0 = b.out = 16
+    for bad in (dict(threads_per_chain=48), dict(threads_per_chain=2000), dict(mu_q=float("nan"))):
+        prm = fsmp.make_params(dict(base, **bad))
+        rc = L.fsmp_run_device_noalloc(ctypes.byref(prm), ctypes.byref(b), None)
+        assert rc == fsmp.ERR_INVALID, bad
+        assert b"checks of fsmp_create" in L.fsmp_last_error(), bad

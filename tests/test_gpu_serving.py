@@ -83,3 +83,93 @@ def test_requests_overlap_on_the_device(lib):
         t_mix = time.perf_counter() - t
     assert t_mix < 0.5 * t_serial, (t_mix, t_serial)
     assert all(0 < x < t_mix + 1 for x in lat)
+
+
+# ---------------------------------------------------------------- error paths of the serving ABI
+def _drain(ctx, n, timeout_s=120.0):
+    got, t = [], time.perf_counter()
+    while len(got) < n:
+        got += ctx.poll(64, 1000)
+        assert time.perf_counter() - t < timeout_s, "serving loop stalled"
+    return got
+
+
+def test_submit_returns_busy_when_the_queue_is_full(lib):
+    """max_queued = 1 and one launch stream: while a long request holds the stream, one more
+    request waits in the queue and the next submit returns FSMP_ERR_BUSY (nothing queued).
+    Every request that was accepted still completes."""
+    params, events = workloads.make_events("serving_20k_eps", n_events=2, seed=7, n_steps=200)
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=20000, n_steps=6000, seed=8)
+    with fsmp.Context(_params(params, n_streams=1, max_queued=1)) as ctx:
+        assert ctx.submit(wl["batch"], request_id=0) == fsmp.OK  # several seconds of work
+        codes = []
+        t = time.perf_counter()
+        while fsmp.ERR_BUSY not in codes and time.perf_counter() - t < 1.0:
+            codes.append(ctx.submit(events[len(codes) % 2], request_id=1 + len(codes)))
+        assert fsmp.ERR_BUSY in codes, codes
+        accepted = [c for c in codes if c == fsmp.OK]
+        assert len(accepted) <= 2 and set(codes) <= {fsmp.OK, fsmp.ERR_BUSY}
+        done = _drain(ctx, 1 + len(accepted))
+    assert all(r["status"] == fsmp.OK for r in done)
+
+
+def test_submit_refuses_a_request_over_the_memory_budget(lib):
+    """A request whose device footprint exceeds device_mem_budget is refused at submit with
+    FSMP_ERR_NOMEM (it could never be admitted); a smaller one still runs."""
+    params, events = workloads.make_events("serving_20k_eps", n_events=8, seed=9, n_steps=100)
+    big = max(events, key=lambda e: len(e["samples"]))
+    small = min(events, key=lambda e: len(e["samples"]))
+    budget = 32 * 1024
+    assert len(big["samples"]) * 4 > budget and len(small["samples"]) * 8 + 8192 < budget
+    with fsmp.Context(_params(params, device_mem_budget=budget)) as ctx:
+        assert ctx.submit(big, request_id=1) == fsmp.ERR_NOMEM
+        assert ctx.submit(small, request_id=2) == fsmp.OK
+        assert _drain(ctx, 1)[0]["status"] == fsmp.OK
+
+
+def test_submit_refuses_malformed_batches(lib):
+    """Malformed host batches are refused at submit with FSMP_ERR_INVALID and nothing queued:
+    offsets not starting at 0, a non-positive lambda0, an empty window, a window longer than
+    n_max, T_lo without T_hi, T_hi <= T_lo, negative steps."""
+    params, events = workloads.make_events("serving_20k_eps", n_events=1, seed=11, n_steps=50)
+    ev = events[0]
+    W = len(ev["offsets"]) - 1
+    offs = np.asarray(ev["offsets"], np.int32)
+    n = np.diff(offs)
+    bad = [dict(offsets=offs + 1), dict(lambda0=np.where(np.arange(W) == 0, 0.0, ev["lambda0"])),
+           dict(offsets=np.concatenate([[0, 0], offs[1:]]).astype(np.int32)[:W + 1]),
+           dict(T_lo=np.zeros(W, np.int32)), dict(T_lo=np.full(W, 5, np.int32), T_hi=np.full(W, 5, np.int32)),
+           dict(n_steps=-1)]
+    with fsmp.Context(_params(params, n_max=int(n.max()))) as ctx:
+        for k, extra in enumerate(bad):
+            with pytest.raises(fsmp.FsmpError) as ei:
+                ctx.submit(dict(ev, **extra), request_id=k)
+            assert ei.value.code == fsmp.ERR_INVALID, extra
+        long_ev = dict(ev, samples=np.zeros(int(offs[-1]) + 600, np.float32),
+                       offsets=np.concatenate([offs[:-1], [offs[-1] + 600]]).astype(np.int32))
+        with pytest.raises(fsmp.FsmpError) as ei:
+            ctx.submit(long_ev, request_id=99)
+        assert ei.value.code == fsmp.ERR_INVALID
+        assert ctx.poll(8, 200) == []  # nothing was queued
+        assert ctx.submit(ev, request_id=100) == fsmp.OK
+        assert _drain(ctx, 1)[0]["status"] == fsmp.OK
+
+
+def test_drift_flag_under_a_tiny_tolerance(lib):
+    """FP32 mode with drift_tol = 1e-300: an FP64 refresh that finds the incremental FP32 state
+    different from its rebuild at all flags the chain FSMP_ST_DRIFT, so nearly every chain that
+    refreshed is flagged (a refresh with no PE has nothing to drift) and none without a
+    refresh is; with the default tolerance none is."""
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=256, n_steps=400, seed=13)
+    n_max = int(np.diff(wl["batch"]["offsets"]).max())
+    res = {}
+    for tol in (1e-300, 0.0):
+        with fsmp.Context(wl["params"], n_max=n_max, precision=fsmp.FP32_REFRESH, refresh_every=8,
+                          drift_tol=tol) as ctx:
+            res[tol], _ = ctx.run(wl["batch"])
+    s = res[1e-300]
+    refreshed = s["n_refresh"] > 0
+    assert refreshed.sum() > 100
+    assert np.mean((s["status"][refreshed] & fsmp.ST_DRIFT) != 0) > 0.9
+    assert np.all((s["status"][~refreshed] & fsmp.ST_DRIFT) == 0)
+    assert np.all((res[0.0]["status"] & fsmp.ST_DRIFT) == 0)

@@ -372,3 +372,76 @@ def test_chain_summary_lambda_matches_its_own_histogram(orc):
         N = t["N"][i, 100:]
         h = np.bincount(N, minlength=wl["params"]["n_cap"] + 1).astype(float)
         assert abs(s["lambda_hat"][i] - orc.lambda_mle(h, wl["batch"]["lambda0"][i])) < 1e-12
+
+
+def _lambda_loglik_np(h, lambda0, lam):
+    """l(lambda) = -lambda + log sum_N h_N (lambda / lambda0)^N (Eq. (reduce-mu0)), by
+    scipy's logsumexp; independent of the oracle's C code. lam may be an array (> 0)."""
+    from scipy.special import logsumexp
+    lam = np.atleast_1d(np.asarray(lam, np.float64))
+    k = np.nonzero(h > 0)[0]
+    terms = np.log(h[k])[None, :] + k[None, :] * np.log(lam[:, None] / lambda0)
+    return -lam + logsumexp(terms, axis=1)
+
+
+def _lambda_global_max(h, lambda0):
+    """Global maximiser of l over [0, inf) found without the oracle: every local maximum of a
+    dense evaluation on (0, 2 top + 10], each refined by scipy's bounded Brent search, and the
+    boundary lambda = 0 (l(0) = log h_0). Returns (lambda*, l(lambda*), number of interior
+    local maxima)."""
+    from scipy.optimize import minimize_scalar
+    top = int(np.nonzero(h > 0)[0].max())
+    grid = np.linspace(0.0, 2.0 * top + 10.0, 60001)[1:]
+    ll = _lambda_loglik_np(h, lambda0, grid)
+    peaks = [i for i in range(len(grid)) if (i == 0 or ll[i] >= ll[i - 1]) and (i == len(grid) - 1 or ll[i] > ll[i + 1])]
+    best = (0.0, math.log(h[0]) if h[0] > 0 else -math.inf)
+    for i in peaks:
+        lo, hi = grid[max(i - 1, 0)] if i > 0 else 1e-12, grid[min(i + 1, len(grid) - 1)]
+        r = minimize_scalar(lambda x: -_lambda_loglik_np(h, lambda0, x)[0], bounds=(lo, hi), method="bounded",
+                            options={"xatol": 1e-13 * max(1.0, hi)})
+        lv = -float(r.fun)
+        if lv > best[1]:
+            best = (float(r.x), lv)
+    return best[0], best[1], len(peaks)
+
+
+def test_lambda_mle_multimodal_global_maximum(orc):
+    """lambda_FSMP (Eq. (reduce-mu0)) when l has several local maxima: N histograms made of two
+    or three well separated clusters (a chain that visits clusters of N far apart), with
+    lambda0 chosen so that the clusters' local maxima compete (heights within a few units).
+    The oracle must return the GLOBAL maximiser found independently (dense scan + Brent
+    refinement of every local maximum, scipy); a method that stopped at a local maximum fails."""
+    rng = np.random.default_rng(2024)
+    n_multi = n_close = 0
+    for case in range(60):
+        n_max = int(rng.choice([64, 128, 384]))
+        n_cl = int(rng.choice([2, 3]))
+        centers = np.sort(rng.choice(np.arange(0, n_max - 4), n_cl, replace=False))
+        h = np.zeros(n_max + 1)
+        for c in centers:
+            width = max(1, int(rng.integers(1, 4)))
+            for d in range(-width, width + 1):
+                if 0 <= c + d <= n_max:
+                    h[c + d] += float(rng.integers(1, 400))
+        # lambda0 where the two outermost clusters' single-term heights are equal, moved by a
+        # random factor: l_c(lambda) ~ -c + log h_c + c log(c / lambda0) at lambda = c
+        a, b = int(centers[0]), int(centers[-1])
+        ha, hb = h[a], h[b]
+        la = (-a + (a * math.log(a) if a > 0 else 0.0) + math.log(ha))
+        lb = (-b + b * math.log(b) + math.log(hb))
+        log_l0 = (lb - la) / (b - a) + rng.uniform(-0.08, 0.08)
+        lambda0 = math.exp(log_l0)
+        want, lwant, npk = _lambda_global_max(h, lambda0)
+        got = orc.lambda_mle(h, lambda0)
+        lgot = _lambda_loglik_np(h, lambda0, max(got, 1e-300))[0] if got > 0 else (math.log(h[0]) if h[0] > 0 else -math.inf)
+        assert lgot >= lwant - 1e-9 * max(1.0, abs(lwant)), (case, got, want, lgot, lwant)
+        assert abs(got - want) <= 1e-6 * max(1.0, want), (case, got, want, npk)
+        if npk >= 2:
+            n_multi += 1
+            ll_grid = _lambda_loglik_np(h, lambda0, np.linspace(0.0, 2.0 * n_max + 10.0, 60001)[1:])
+            # the runner-up local maximum lies within 3 units of the global one
+            second = np.sort(ll_grid[[i for i in range(1, len(ll_grid) - 1)
+                                      if ll_grid[i] >= ll_grid[i - 1] and ll_grid[i] > ll_grid[i + 1]]])
+            if len(second) >= 2 and second[-1] - second[-2] < 3.0:
+                n_close += 1
+    assert n_multi >= 30 and n_close >= 15, (n_multi, n_close)
