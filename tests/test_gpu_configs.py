@@ -75,9 +75,12 @@ def _lucy_state(orc, params, b, cap):
 
 
 def _assert_summaries(s_gpu, s_orc, lam=True):
-    for f in ("mean_N", "var_N", "mean_t0", "var_t0"):
+    for f in ("mean_N", "mean_t0"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12, err_msg=f)
-    for f in ("mean_Q", "var_Q", "logL", "logdet") + (("lambda_hat",) if lam else ()):
+    # the variances come from the same exact integer sums as E[x^2] - E[x]^2, which cancels by
+    # a factor E[x^2] / var (about 2000 for t0 on a 1024-sample window): the two sides' last-bit
+    # roundings there show at 1e-12
+    for f in ("var_N", "var_t0", "mean_Q", "var_Q", "logL", "logdet") + (("lambda_hat",) if lam else ()):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9, err_msg=f)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f], err_msg=f)

@@ -22,7 +22,7 @@ def lib():
 
 
 def _params(params, **kw):
-    return dict(params, precision=fsmp.FP32_REFRESH, refresh_every=64, n_max=512, **kw)
+    return dict(dict(params, precision=fsmp.FP32_REFRESH, refresh_every=64, n_max=512), **kw)
 
 
 def test_result_same_alone_and_in_the_mix(lib):
