@@ -66,6 +66,13 @@ def parse():
     ap.add_argument("--stage", default="chain", choices=["chain", "lucyddm"],
                     help="lucyddm: time the LucyDDM deconvolution (Sec. 2.3) of the workload instead of the chains")
     ap.add_argument("--lucy-iters", type=int, default=2000, help="lucyddm stage: Lucy iterations")
+    ap.add_argument("--plain-sample", type=int, default=48,
+                    help="waveforms of the workload timed in the plain FP64 form (vs_baseline; 0: skip)")
+    ap.add_argument("--error-sample", type=int, default=256,
+                    help="waveforms of the workload compared with the FP64 oracle (error; 0: skip)")
+    ap.add_argument("--latency-rate", type=float, default=1000.0,
+                    help="events/s of the serving leg that gives the p50/p99 latency (0: skip)")
+    ap.add_argument("--latency-seconds", type=float, default=8.0, help="length of that serving leg's stream")
     return ap.parse_args()
 
 
@@ -280,7 +287,7 @@ def device_batches(torch, wl, dev, n_smem_max, one_launch=False):
             if sb.get("T_lo") is not None:
                 t["T_lo"] = torch.from_numpy(sb["T_lo"].astype(np.int32)).to(dev)
                 t["T_hi"] = torch.from_numpy(sb["T_hi"].astype(np.int32)).to(dev)
-            subs.append((t, nm, W))
+            subs.append((t, nm, W, np.asarray(ii)))
     return subs
 
 
@@ -294,6 +301,182 @@ def load_traffic(kernel_src, name):
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     return d if d.get("kernel_sha") == sha else None
+
+
+def plain_fp64_baseline(torch, wl, dev, n_sample, sample_seed=3):
+    """The plain one-launch-per-chain FP64 form (FSMP_KERNEL_PLAIN: one kernel launch per chain,
+    full Sigma^-1 in global memory), the baseline the metric compares with, timed with CUDA
+    events on a random sample of the same workload on the same GPU. Returns (stats, summaries,
+    the sample's waveform indices)."""
+    from paper_2403_03156_gb300 import fsmp, workloads
+    b = wl["batch"]
+    W = len(b["offsets"]) - 1
+    rng = np.random.default_rng(sample_seed)
+    idx = np.sort(rng.choice(W, min(n_sample, W), replace=False))
+    sb = workloads.subset(b, idx)
+    n_max = int(np.diff(sb["offsets"]).max())
+    params = dict(wl["params"], precision=fsmp.FP64, kernel=fsmp.KERNEL_PLAIN, n_max=max(n_max, 64),
+                  device=dev.index or 0)
+    n_steps, burn = int(b["n_steps"]), int(b.get("burn_in", 0))
+    t = _device_tensors(torch, sb, dev)
+    with fsmp.Context(params) as ctx:
+        w = _device_tensors(torch, workloads.subset(sb, np.arange(2)), dev)  # warm-up (code, caches)
+        ctx.run_device(w, n_steps=50, burn_in=0, seed=int(b["seed"]), n_max_hint=n_max)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        e0.record(stream)
+        ctx.run_device(t, n_steps=n_steps, burn_in=burn, seed=int(b["seed"]), n_max_hint=n_max, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+    summ = fsmp.summaries_from_bytes(t["out"].cpu().numpy())
+    rate = len(idx) * n_steps / (ms * 1e-3)
+    stats = {"value": rate, "unit": UNIT, "form": "plain FP64: one launch per chain, Sigma^-1 in global memory",
+             "sample": "%d random waveforms of %s x %d MCMC steps, %d launches, %.2f s (CUDA events)"
+                       % (len(idx), wl["name"], n_steps, len(idx), ms * 1e-3)}
+    return stats, summ, idx
+
+
+def _device_tensors(torch, sb, dev, trace_steps=0):
+    from paper_2403_03156_gb300 import fsmp
+    W = len(sb["offsets"]) - 1
+    t = {"samples": torch.from_numpy(sb["samples"]).to(dev),
+         "offsets": torch.from_numpy(sb["offsets"].astype(np.int32)).to(dev),
+         "lambda0": torch.from_numpy(np.asarray(sb["lambda0"], np.float64)).to(dev),
+         "t_origin_ns": torch.from_numpy(np.asarray(sb["t_origin_ns"], np.float64)).to(dev),
+         "wf_ids": torch.from_numpy(np.asarray(sb["wf_ids"], np.uint64).astype(np.int64)).to(dev),
+         "out": torch.zeros(W * fsmp.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dev)}
+    if sb.get("T_lo") is not None:
+        t["T_lo"] = torch.from_numpy(sb["T_lo"].astype(np.int32)).to(dev)
+        t["T_hi"] = torch.from_numpy(sb["T_hi"].astype(np.int32)).to(dev)
+    if trace_steps:
+        t["trace"] = torch.zeros(W * trace_steps * fsmp.TRACE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    return t
+
+
+def _paired(d):
+    """mean +- standard error of paired differences, and whether |mean| < 3 SE."""
+    d = np.asarray(d, np.float64)
+    se = float(d.std(ddof=1) / math.sqrt(len(d))) if len(d) > 1 else float("nan")
+    m = float(d.mean())
+    return {"mean": m, "se": se, "within_3se": bool(abs(m) <= 3 * se + 1e-12)}
+
+
+def error_vs_fp64(torch, ctx, wl, dev, n_sample, sample_seed=5):
+    """The stated error of the measured FP32 path against the FP64 oracle on a random sample of
+    the same workload (same chains: same Philox streams): paired differences of the posterior
+    summaries (mean +- SE over waveforms), and |Delta log alpha| per step over each chain's
+    lockstep prefix (the steps before its first decision that differs from the FP64 chain's)."""
+    from oracle import oracle
+    from paper_2403_03156_gb300 import fsmp, workloads
+    b = wl["batch"]
+    W = len(b["offsets"]) - 1
+    rng = np.random.default_rng(sample_seed)
+    idx = np.sort(rng.choice(W, min(n_sample, W), replace=False))
+    sb = workloads.subset(b, idx)
+    n_steps, burn = int(b["n_steps"]), int(b.get("burn_in", 0))
+    n_max = int(np.diff(sb["offsets"]).max())
+    t = _device_tensors(torch, sb, dev, trace_steps=n_steps)
+    ctx.run_device(t, n_steps=n_steps, burn_in=burn, seed=int(b["seed"]), n_max_hint=n_max)
+    torch.cuda.synchronize(dev)
+    sg = fsmp.summaries_from_bytes(t["out"].cpu().numpy())
+    tg = fsmp.traces_from_bytes(t["trace"].cpu().numpy(), len(idx))
+    so, to = oracle.run_batch(wl["params"], sb, oracle.MODE_INCREMENTAL, n_threads=os.cpu_count() or 1, trace=True)
+    out = {"reference": "FP64 CPU oracle (incremental Woodbury), %d random waveforms x %d steps, burn-in %d"
+                        % (len(idx), n_steps, burn)}
+    for f in ("mean_N", "mean_Q", "mean_t0", "lambda_hat"):
+        out[f] = _paired(sg[f] - so[f])
+    differ = tg["flags"] != to["flags"]
+    first = np.where(differ.any(1), differ.argmax(1), n_steps)
+    keep = np.arange(n_steps)[None, :] < first[:, None]
+    la_g, la_o = tg["la"][keep], to["la"][keep]
+    ok = np.isfinite(la_g) & np.isfinite(la_o) & (la_o > -40.0)
+    dla = np.abs(la_g[ok] - la_o[ok])
+    out["dlog_alpha"] = {"p50": float(np.percentile(dla, 50)), "p99": float(np.percentile(dla, 99)),
+                         "max": float(dla.max()), "steps": int(ok.sum()),
+                         "lockstep_fraction": float(keep.sum() / keep.size)}
+    return out
+
+
+def serve_stream(ctx, pool, rate, seconds, seed, warmup=3):
+    """The serving loop under a Poisson stream of events (submit / poll through the C ABI, host
+    buffers, copies included). Events are replayed from `pool`, each arrival with its own RNG
+    seed. Returns steps/s of the served events, p50/p99 event latency (submit to result) and
+    whether the offered rate was sustained."""
+    import threading
+    from paper_2403_03156_gb300 import fsmp
+    n_steps = int(pool[0]["n_steps"])
+    for i in range(warmup):  # the first requests pay for lazy initialisation
+        ctx.run(pool[i % len(pool)], request_id=(1 << 40) + i)
+    rng = np.random.default_rng(1234 + seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 1.2) + 16))
+    arrivals = arrivals[arrivals < seconds]
+    n_ev = len(arrivals)
+    sizes = np.zeros(n_ev, np.int64)
+    lat = np.full(n_ev, np.nan)
+    t_done_last = [0.0]
+    done = [0]
+    stop = threading.Event()
+
+    def poller():
+        while not stop.is_set() or done[0] < n_ev:
+            for r in ctx.poll(4096, 50):
+                i = int(r["request_id"])
+                lat[i] = r["latency_s"]
+                done[0] += 1
+                t_done_last[0] = time.perf_counter()
+            if stop.is_set() and done[0] >= n_ev:
+                break
+
+    launches0 = ctx.info()["n_launches"]
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    busy = 0
+    for i in range(n_ev):
+        ev = dict(pool[i % len(pool)])
+        ev["seed"] = int(seed) * 1000003 + i  # each arrival is a new event for the sampler
+        sizes[i] = len(ev["offsets"]) - 1
+        wait = t0 + arrivals[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        while ctx.submit(ev, request_id=i) == fsmp.ERR_BUSY:
+            busy += 1
+            time.sleep(0.001)
+    t_sub = time.perf_counter() - t0
+    stop.set()
+    th.join()
+    t_all = t_done_last[0] - t0
+    steps = float(sizes.sum()) * n_steps
+    completed = n_ev / t_all
+    bytes_in = sum(int(pool[i % len(pool)]["samples"].nbytes) for i in range(n_ev)) / n_ev
+    return {"value": steps / t_all, "steps": steps, "t_all": t_all, "events": n_ev, "waveforms": int(sizes.sum()),
+            "offered_rate_hz": rate, "completed_rate_hz": completed, "sustained": bool(completed >= 0.95 * rate),
+            "submitted_in_s": t_sub, "stream_s": seconds, "busy_retries": busy,
+            "launches": int(ctx.info()["n_launches"] - launches0), "mcmc_steps_per_chain": n_steps,
+            "p50_s": float(np.nanpercentile(lat, 50)), "p99_s": float(np.nanpercentile(lat, 99)),
+            "mean_s": float(np.nanmean(lat)), "max_s": float(np.nanmax(lat)),
+            "h2d_bytes_per_event": int(bytes_in), "d2h_bytes_per_event": int(sizes.mean() * fsmp.SUMMARY_DTYPE.itemsize)}
+
+
+def serving_latency_leg(local, rate, seconds, seed, pool_n=256):
+    """A short serving stream of the serving workload (events of 1-64 waveforms of 64-512
+    samples, lambda to 100, 1500 steps) at a rate the loop sustains on one GPU: the p50/p99 event
+    latency part of the metric."""
+    from paper_2403_03156_gb300 import fsmp, workloads
+    cfg = workloads.CONFIGS["serving_20k_eps"]
+    params, pool = workloads.make_events("serving_20k_eps", pool_n, seed=seed)
+    for e in pool:
+        e["burn_in"] = int(e["n_steps"]) // 5
+    with fsmp.Context(dict(params, precision=fsmp.FP32_REFRESH, refresh_every=cfg.get("refresh_every", 64),
+                           n_max=cfg["win_max"], device=local, max_queued=1 << 20)) as ctx:
+        r = serve_stream(ctx, pool, rate, seconds, seed)
+    return {"workload": "serving_20k_eps", "p50_s": r["p50_s"], "p99_s": r["p99_s"], "mean_s": r["mean_s"],
+            "max_s": r["max_s"], "offered_rate_hz": rate, "completed_rate_hz": r["completed_rate_hz"],
+            "sustained": r["sustained"], "events": r["events"], "waveforms": r["waveforms"],
+            "stream_s": seconds, "steps_per_s": r["value"],
+            "timing": "host clock, submit to result visible in fsmp_poll, host buffers"}
 
 
 def run_ours(args):
@@ -328,7 +511,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tuned = None
     if pe and not args.no_autotune:  # launch shape from timed trials on a sample (not timed)
-        t0_, nm0, _ = subs[0]
+        t0_, nm0, _, _ = subs[0]
         # trials of the full chain length: the cost per step grows with N over a chain, and a
         # short trial would favour shapes that suit the first steps
         # (a sample of at most a quarter of the batch, so that the trials stay short next to it)
@@ -336,7 +519,7 @@ def run_ours(args):
                              n_max_hint=nm0)
 
     def one_step(ev=None):
-        for k, (t, nm, _) in enumerate(subs):
+        for k, (t, nm, _, _) in enumerate(subs):
             if ev is not None:
                 ev[k][0].record(stream)
             ctx.run_device(t, n_steps=n_steps, burn_in=int(b.get("burn_in", 0)), seed=int(b["seed"]),
@@ -357,7 +540,7 @@ def run_ours(args):
         cs.wait_stream(stream)
         with torch.cuda.stream(cs):
             with torch.cuda.graph(graph, stream=cs):
-                for (t, nm, _) in subs:
+                for (t, nm, _, _) in subs:
                     ctx.run_device(t, n_steps=n_steps, burn_in=int(b.get("burn_in", 0)), seed=int(b["seed"]),
                                    n_max_hint=nm, stream=cs)
         stream.wait_stream(cs)
@@ -394,7 +577,7 @@ def run_ours(args):
     value = W_total * n_steps / (ms_per_step / 1000.0)
 
     # per-launch roofline of the dominant kernel (the longest bucket launch)
-    summ = [fsmp.summaries_from_bytes(t["out"].cpu().numpy()) for (t, _, _) in subs]
+    summ = [fsmp.summaries_from_bytes(t["out"].cpu().numpy()) for (t, _, _, _) in subs]
     if graph is not None:  # one timed interval per step: the whole graph
         durs = np.array([[evs[i][0][0].elapsed_time(evs[i][0][1])] + [0.0] * (len(subs) - 1)
                          for i in range(args.steps)])
@@ -465,10 +648,32 @@ def run_ours(args):
             e2e_val = W_total * n_steps / float(te.item())
         line["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times)}
+    # the metric's other clauses, measured after the timed region on rank 0: the plain FP64 form
+    # on a sample of the same workload (vs_baseline), the stated error against FP64, and the
+    # p50/p99 event latency of a serving stream
+    if rank == 0 and not serving_workload(args.workload):
+        full = np.zeros(W, fsmp.SUMMARY_DTYPE)
+        for (_, _, _, ii), sm in zip(subs, summ):
+            full[ii] = sm
+        if args.plain_sample > 0 and args.kernel != "plain":
+            plain, s_plain, pidx = plain_fp64_baseline(torch, wl, dev, args.plain_sample)
+            line["vs_baseline"] = value / plain["value"]
+            plain["ratio"] = line["vs_baseline"]
+            # the same chains (same Philox streams) in both forms: the measured path's error
+            # against the plain FP64 form itself
+            plain["error_vs_plain"] = {f: _paired(full[f][pidx] - s_plain[f]) for f in
+                                       ("mean_N", "mean_Q", "mean_t0", "lambda_hat")}
+            plain["error_vs_plain"]["waveforms"] = int(len(pidx))
+            line["baseline"] = plain
+            line["config"]["vs_baseline_of"] = "the plain one-launch-per-chain FP64 form on the same GPU"
+        if args.error_sample > 0:
+            line["error"] = error_vs_fp64(torch, ctx, wl, dev, args.error_sample)
+    ctx.close()
+    if rank == 0 and args.latency_rate > 0 and not serving_workload(args.workload):
+        line["latency"] = serving_latency_leg(local, args.latency_rate, args.latency_seconds, args.seed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, _, _ = oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = base
-    ctx.close()
     if rank == 0:
         emit(line)
     if world > 1:
@@ -480,7 +685,6 @@ def run_serving(args):
     buffers, copies included): steps/s of the served events and p50/p99 event latency (submit
     to result). Events are replayed from a pool of distinct simulated events, each arrival with
     its own RNG seed."""
-    import threading
     import torch
     import torch.distributed as dist
     from paper_2403_03156_gb300 import build, fsmp, workloads
@@ -503,14 +707,11 @@ def run_serving(args):
     # device batch: the rate the serving loop would reach if every event arrived at once
     pb = concat_events(pool)
     dvc = torch.device("cuda", local)
-    tb = {"samples": torch.from_numpy(pb["samples"]).to(dvc), "offsets": torch.from_numpy(pb["offsets"]).to(dvc),
-          "lambda0": torch.from_numpy(pb["lambda0"]).to(dvc), "t_origin_ns": torch.from_numpy(pb["t_origin_ns"]).to(dvc),
-          "wf_ids": torch.from_numpy(pb["wf_ids"].astype(np.int64)).to(dvc)}
+    tb = _device_tensors(torch, pb, dvc)
     nm = int(np.diff(pb["offsets"]).max())
     tuned = None if args.no_autotune else ctx.autotune(tb, sample=32768, trial_steps=n_steps, seed=int(pb["seed"]),
                                                         n_max_hint=nm)
     Wp = len(pb["offsets"]) - 1
-    tb["out"] = torch.zeros(Wp * fsmp.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dvc)
     batch_ms = []
     for rep in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -521,81 +722,35 @@ def run_serving(args):
         batch_ms.append(e0.elapsed_time(e1))
     batch_rate = Wp * n_steps / (batch_ms[-1] * 1e-3)
     del tb
-    # warm-up: the first requests pay for lazy initialisation
-    for i in range(args.warmup):
-        ctx.run(pool[i % len(pool)], request_id=(1 << 40) + i)
-    rng = np.random.default_rng(1234 + rank)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * args.serve_seconds * 1.2) + 16))
-    arrivals = arrivals[arrivals < args.serve_seconds]
-    n_ev = len(arrivals)
-    sizes = np.zeros(n_ev, np.int64)
-    lat = np.full(n_ev, np.nan)
-    t_done_last = [0.0]
-    done = [0]
-    stop = threading.Event()
-
-    def poller():
-        while not stop.is_set() or done[0] < n_ev:
-            for r in ctx.poll(4096, 50):
-                i = int(r["request_id"])
-                lat[i] = r["latency_s"]
-                done[0] += 1
-                t_done_last[0] = time.perf_counter()
-            if stop.is_set() and done[0] >= n_ev:
-                break
-
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    launches0 = ctx.info()["n_launches"]
     clocks = Clocks(local)
     clocks.start()
-    th = threading.Thread(target=poller, daemon=True)
-    th.start()
-    t0 = time.perf_counter()
-    busy = 0
-    for i in range(n_ev):
-        ev = dict(pool[i % len(pool)])
-        ev["seed"] = int(args.seed) * 1000003 + i  # each arrival is a new event for the sampler
-        sizes[i] = len(ev["offsets"]) - 1
-        wait = t0 + arrivals[i] - time.perf_counter()
-        if wait > 0:
-            time.sleep(wait)
-        while ctx.submit(ev, request_id=i) == fsmp.ERR_BUSY:
-            busy += 1
-            time.sleep(0.001)
-    t_sub = time.perf_counter() - t0
-    stop.set()
-    th.join()
-    t_all = t_done_last[0] - t0
+    r = serve_stream(ctx, pool, rate, args.serve_seconds, args.seed, warmup=args.warmup)
     clk = clocks.stop()
-    launches = ctx.info()["n_launches"] - launches0
     ctx.close()
-    steps = float(sizes.sum()) * n_steps
-    value = steps / t_all
+    value, t_all = r["value"], r["t_all"]
     if world > 1:
-        tv = torch.tensor([steps, t_all], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tv[:1], op=dist.ReduceOp.SUM)
+        tv = torch.tensor([r["steps"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tv, op=dist.ReduceOp.SUM)
         tmax = torch.tensor([t_all], dtype=torch.float64, device="cuda")
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         value = float(tv[0].item()) / float(tmax.item())
-    completed_rate = n_ev / t_all
-    bytes_in = sum(int(pool[i % len(pool)]["samples"].nbytes) for i in range(n_ev)) / n_ev
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_ev,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / n_ev, "higher_is_better": True,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": r["events"],
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / r["events"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "offered_rate_hz": rate, "submitted_in_s": t_sub,
-                       "stream_s": args.serve_seconds, "events": n_ev, "waveforms": int(sizes.sum()),
-                       "mcmc_steps_per_chain": n_steps, "completed_rate_hz": completed_rate,
-                       "sustained": bool(completed_rate >= 0.95 * rate), "busy_retries": busy,
+            "config": {"workload": args.workload, "offered_rate_hz": rate, "submitted_in_s": r["submitted_in_s"],
+                       "stream_s": args.serve_seconds, "events": r["events"], "waveforms": r["waveforms"],
+                       "mcmc_steps_per_chain": n_steps, "completed_rate_hz": r["completed_rate_hz"],
+                       "sustained": r["sustained"], "busy_retries": r["busy_retries"],
                        "timing": "host wall clock from the first submit to the last result (end to end)",
-                       "kernel": "pe_kernel<float> (serving loop, one launch per pack)", "autotune": tuned,
+                       "kernel": "pe_kernel<float> (serving loop)", "autotune": tuned,
                        "pool_as_one_batch_steps_per_s": batch_rate, "pool_waveforms": Wp},
-            "latency": {"p50_s": float(np.nanpercentile(lat, 50)), "p99_s": float(np.nanpercentile(lat, 99)),
-                        "mean_s": float(np.nanmean(lat)), "max_s": float(np.nanmax(lat))},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(bytes_in),
-                    "d2h_bytes_per_step": int(sizes.mean() * fsmp.SUMMARY_DTYPE.itemsize)},
-            "gpu_launches": int(launches), "clocks": clk}
+            "latency": {"p50_s": r["p50_s"], "p99_s": r["p99_s"], "mean_s": r["mean_s"], "max_s": r["max_s"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": r["h2d_bytes_per_event"],
+                    "d2h_bytes_per_step": r["d2h_bytes_per_event"]},
+            "gpu_launches": r["launches"], "clocks": clk}
     if rank == 0:
         emit(line)
     if world > 1:
