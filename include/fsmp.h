@@ -142,6 +142,13 @@ typedef struct {
   double lambda_hat;             /* lambda_FSMP = argmax_lambda -lambda + log sum_N h_N
                                     (lambda / lambda0)^N over the chain's N samples h
                                     (Eq. (reduce-mu0)); 0 if every sample has N = 0 */
+  /* Mean and variance over the samples of the Wasserstein scalars of the PE sequence, the
+   * convergence representatives of Sec. 3.2: a dummy PE at t = 0, e = 0 joins the sequence
+   * (so that an empty z is a distribution too) and the scalar is the 1-Wasserstein distance
+   * from the sequence to the dummy alone, sum_k |t_k| / (N + 1) for the PE times (ns from the
+   * window's first sample) and sum_k e_k / (N + 1) for the MCP components (0 for the dynode
+   * model). */
+  double mean_wt, var_wt, mean_we, var_we;
   int32_t acc[3], prop[3];
   int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples, n_refresh, reserved;
 } fsmp_summary;
@@ -295,7 +302,28 @@ int fsmp_run_device(fsmp_ctx* ctx, const fsmp_device_batch* batch, void* stream)
 #define FSMP_RHAT_N 0
 #define FSMP_RHAT_T0 1
 #define FSMP_RHAT_Q 2
+#define FSMP_RHAT_WT 3          /* the Wasserstein scalar of the PE times {t_i} (Sec. 3.2)     */
+#define FSMP_RHAT_WE 4          /* the Wasserstein scalar of the MCP components {e_i}          */
 int fsmp_gelman_rubin(const fsmp_summary* chains, int m, int field, double* rhat);
+
+/* The convergence check as Sec. 3.2 plots it: the degrees-of-freedom corrected potential scale
+ * reduction of a scalar over m >= 2 chains of the same waveform, with its upper confidence
+ * limit (Gelman and Rubin 1992, Sec. 3, with the correction (d + 3) / (d + 1) of Brooks and
+ * Gelman 1998). From the chains' summaries (n samples each, n >= 2): chain means x_j and
+ * within-chain variances s2_j = v_j n / (n - 1); across chains, with m - 1 denominators,
+ * var(x), var(s2), cov(s2, x^2), cov(s2, x) and xx = mean of x_j:
+ *   W = mean s2_j, B = n var(x), V = (n - 1) / n W + (1 + 1/m) B / n,
+ *   var(V) = [(n - 1)^2 var(s2) / m + (1 + 1/m)^2 2 B^2 / (m - 1)
+ *             + 2 (n - 1)(1 + 1/m)(n / m)(cov(s2, x^2) - 2 xx cov(s2, x))] / n^2,
+ *   d = 2 V^2 / var(V),  c = (d + 3) / (d + 1)  (1 if var(V) = 0),
+ *   rhat  = sqrt(c [(n - 1) / n + (1 + 1/m) (B / W) / n]),
+ *   upper = the same with B / W times the F(m - 1, 2 W^2 m / var(s2)) quantile at
+ *           (1 + confidence) / 2 (chi2(m - 1) / (m - 1) when var(s2) = 0).
+ * The paper plots the 90 % upper limit: confidence = 0.9. W = 0 gives 1 (all means equal) or
+ * +inf. Host only. Returns FSMP_OK or FSMP_ERR_INVALID (m < 2, n < 2, unequal n, confidence
+ * outside (0, 1), unknown field). */
+int fsmp_gelman_diag(const fsmp_summary* chains, int m, int field, double confidence, double* rhat,
+                     double* upper);
 
 /* Launch shape of the PE-space kernel chosen by fsmp_autotune. */
 typedef struct {

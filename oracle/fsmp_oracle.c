@@ -584,8 +584,10 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
   if (c->mode == ORC_MODE_DEFINITION && !p->prior_only)
     logp_cur = logp_def(M, c->w, n, list, list_e, N, NULL, NULL, NULL);
 
-  double sN = 0, sN2 = 0, st0 = 0, st02 = 0, sQ = 0, sQ2 = 0;
+  double sN = 0, sN2 = 0, st0 = 0, st02 = 0, sQ = 0, sQ2 = 0, sWt = 0, sWt2 = 0, sWe = 0, sWe2 = 0;
   double* hist = (double*)calloc((size_t)p->n_cap + 1, sizeof(double));
+  double* wbuf = (double*)malloc(sizeof(double) * ((size_t)p->n_cap + 1));
+  double* wbuf_e = (double*)malloc(sizeof(double) * ((size_t)p->n_cap + 1));
   int q_valid = 0;
   double q_cur = 0.0;
   const double logJ = log(p->jump_J);
@@ -761,6 +763,10 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     }
     tr.la = la; tr.lu = lu; tr.dnu = dnu;
     tr.N = N; tr.k0 = k0; tr.jump = jump;
+    /* the Wasserstein scalars of the new state (convergence check of Sec. 3.2) */
+    for (int kk = 0; kk < N; ++kk) { wbuf[kk] = list[kk] * g; wbuf_e[kk] = list_e[kk]; }
+    tr.wt = orc_pe_wasserstein(wbuf, N);
+    tr.we = orc_pe_wasserstein(wbuf_e, N);
     if (trace) trace[step] = tr;
 
     /* ---- summaries after burn-in (reading R8 for the charge) ---- */
@@ -800,6 +806,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       sN += N; sN2 += (double)N * N;
       if (N >= 0 && N <= p->n_cap) hist[N] += 1.0;
       st0 += t0ns; st02 += t0ns * t0ns;
+      sWt += tr.wt; sWt2 += tr.wt * tr.wt;
+      sWe += tr.we; sWe2 += tr.we * tr.we;
       sQ += q_cur; sQ2 += q_cur * q_cur;
       if (c->occ)
         for (int kk = 0; kk < N; ++kk) {
@@ -819,6 +827,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     out->mean_N = sN * inv; out->var_N = sN2 * inv - out->mean_N * out->mean_N;
     out->mean_t0 = st0 * inv; out->var_t0 = st02 * inv - out->mean_t0 * out->mean_t0;
     out->mean_Q = sQ * inv; out->var_Q = sQ2 * inv - out->mean_Q * out->mean_Q;
+    out->mean_wt = sWt * inv; out->var_wt = sWt2 * inv - out->mean_wt * out->mean_wt;
+    out->mean_we = sWe * inv; out->var_we = sWe2 * inv - out->mean_we * out->mean_we;
     out->N_final = N;
     out->k0_final = k0;
     out->lambda_hat = ns > 0 ? orc_lambda_mle(hist, p->n_cap, c->lambda0) : NAN;
@@ -853,6 +863,8 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
     }
     free(hist);
   }
+  free(wbuf);
+  free(wbuf_e);
 done:
   free(tb.phi); free(tb.logphi); free(tb.Phi_T); free(list); free(list_e); free(zprop_e);
   free(av); free(uvec); free(svec); free(zprop);
@@ -1069,6 +1081,51 @@ static double lambda_dloglik(const double* h, int n_max, double lambda0, double 
       snw += k * e;
     }
   return -1.0 + snw / (lam * sw);
+}
+
+/* ------------------------------------------------------------------------------------
+ * The Wasserstein distance the convergence check of Sec. 3.2 uses on PE sequences.
+ * ---------------------------------------------------------------------------------- */
+static int cmp_double(const void* x, const void* y) {
+  const double a = *(const double*)x, b = *(const double*)y;
+  return (a > b) - (a < b);
+}
+
+double orc_wasserstein1(const double* a, int na, const double* b, int nb) {
+  /* W1 on the line is the area between the two CDFs: walk the merged sorted points, and on
+   * each interval between consecutive points add |F_a - F_b| times its length */
+  double* sa = (double*)malloc(sizeof(double) * (size_t)na);
+  double* sb = (double*)malloc(sizeof(double) * (size_t)nb);
+  if (!sa || !sb) { free(sa); free(sb); return NAN; }
+  memcpy(sa, a, sizeof(double) * (size_t)na);
+  memcpy(sb, b, sizeof(double) * (size_t)nb);
+  qsort(sa, (size_t)na, sizeof(double), cmp_double);
+  qsort(sb, (size_t)nb, sizeof(double), cmp_double);
+  int i = 0, j = 0;
+  double x = fmin(sa[0], sb[0]), area = 0.0;
+  while (i < na || j < nb) {
+    /* the next point of either sample; both CDFs are constant on [x, next) */
+    const double next = (j >= nb || (i < na && sa[i] <= sb[j])) ? sa[i] : sb[j];
+    area += fabs((double)i / na - (double)j / nb) * (next - x);
+    x = next;
+    while (i < na && sa[i] == x) ++i;
+    while (j < nb && sb[j] == x) ++j;
+  }
+  free(sa);
+  free(sb);
+  return area;
+}
+
+double orc_pe_wasserstein(const double* v, int N) {
+  /* the sequence with its dummy PE at 0 against the dummy alone */
+  double* a = (double*)malloc(sizeof(double) * ((size_t)N + 1));
+  if (!a) return NAN;
+  a[0] = 0.0;
+  for (int k = 0; k < N; ++k) a[k + 1] = v[k];
+  const double zero = 0.0;
+  const double d = orc_wasserstein1(a, N + 1, &zero, 1);
+  free(a);
+  return d;
 }
 
 double orc_lambda_mle(const double* h, int n_max, double lambda0) {

@@ -67,6 +67,9 @@ typedef struct {
 typedef struct {
   double la0, lu0, la, lu, dnu;
   int32_t N, k0, jump, flags;
+  /* the Wasserstein scalars of the state after the step (orc_pe_wasserstein): of the PE times
+   * {t_i} (ns from the window's first sample) and of the MCP components {e_i} */
+  double wt, we;
 } orc_trace;
 
 enum { ORC_F_T0_PROPOSED = 1, ORC_F_T0_ACCEPTED = 2, ORC_F_ACCEPTED = 4, ORC_F_NOOP = 8,
@@ -80,7 +83,22 @@ typedef struct {
   int32_t acc[3], prop[3];
   int32_t acc_t0, prop_t0, N_final, k0_final, status, n_samples;
   double lambda_hat;  /* lambda_FSMP of the chain's N samples (Eq. (reduce-mu0)); 0 if none */
+  /* mean and population variance over the samples of the Wasserstein scalars of {t_i} and
+   * {e_i} (orc_pe_wasserstein; the convergence check of Sec. 3.2) */
+  double mean_wt, var_wt, mean_we, var_we;
 } orc_summary;
+
+/* 1-Wasserstein distance between the empirical distributions (equal weights) of a[0..na) and
+ * b[0..nb) on the real line: the integral of |F_a(x) - F_b(x)| over x, with F the empirical
+ * CDFs (na, nb >= 1). */
+double orc_wasserstein1(const double* a, int na, const double* b, int nb);
+
+/* The scalar the convergence check of Sec. 3.2 takes from a trans-dimensional PE sequence:
+ * a dummy PE (t = 0, e = 0) joins every sequence, so that an empty z is a distribution too,
+ * and the scalar is the 1-Wasserstein distance from the sequence with its dummy to the dummy
+ * alone. v[0..N) are the PEs' times in ns from the window's first sample (or their MCP
+ * components). */
+double orc_pe_wasserstein(const double* v, int N);
 
 /* lambda_FSMP = argmax_lambda l(lambda), l = -lambda + log sum_N h[N] (lambda / lambda0)^N
  * (Eq. (reduce-mu0) with the samples counted by N in h[0 .. n_max]), by a dense grid over

@@ -32,13 +32,14 @@ MAX_MIX = 8
 
 TRACE_DTYPE = np.dtype([("la0", "<f8"), ("lu0", "<f8"), ("la", "<f8"), ("lu", "<f8"),
                         ("dnu", "<f8"), ("N", "<i4"), ("k0", "<i4"), ("jump", "<i4"),
-                        ("flags", "<i4")])
+                        ("flags", "<i4"), ("wt", "<f8"), ("we", "<f8")])
 SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"),
                           ("var_t0", "<f8"), ("mean_Q", "<f8"), ("var_Q", "<f8"),
                           ("logL", "<f8"), ("logdet", "<f8"), ("acc", "<i4", (3,)),
                           ("prop", "<i4", (3,)), ("acc_t0", "<i4"), ("prop_t0", "<i4"),
                           ("N_final", "<i4"), ("k0_final", "<i4"), ("status", "<i4"),
-                          ("n_samples", "<i4"), ("lambda_hat", "<f8")])
+                          ("n_samples", "<i4"), ("lambda_hat", "<f8"), ("mean_wt", "<f8"),
+                          ("var_wt", "<f8"), ("mean_we", "<f8"), ("var_we", "<f8")])
 
 
 class OrcParams(ctypes.Structure):
@@ -126,6 +127,10 @@ def lib():
         L.orc_lucyddm.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_wasserstein1.restype = ctypes.c_double
+        L.orc_wasserstein1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+        L.orc_pe_wasserstein.restype = ctypes.c_double
+        L.orc_pe_wasserstein.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_lambda_mle.restype = ctypes.c_double
         L.orc_lambda_mle.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_run_chain_state.restype = ctypes.c_int
@@ -244,6 +249,19 @@ def lambda_mle(hist, lambda0):
     """lambda_FSMP of an N histogram (counts h[0..n_max]) by Eq. (reduce-mu0)."""
     h = np.ascontiguousarray(hist, np.float64)
     return lib().orc_lambda_mle(h.ctypes.data, len(h) - 1, float(lambda0))
+
+
+def wasserstein1(a, b):
+    """1-Wasserstein distance between the empirical distributions of a and b (1-D)."""
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    return lib().orc_wasserstein1(a.ctypes.data, len(a), b.ctypes.data, len(b))
+
+
+def pe_wasserstein(v):
+    """The convergence scalar of a PE sequence (Sec. 3.2): W1 from {0} and v to {0}."""
+    v = np.ascontiguousarray(v, np.float64)
+    return lib().orc_pe_wasserstein(v.ctypes.data if len(v) else None, len(v))
 
 
 def delta_nu(params, w, j, kind, k=0, jp=0, mode=MODE_INCREMENTAL, e=None, ep=0):

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfsmp.so")
 SOURCES = ["fsmp_tables.cu", "fsmp_chain.cu", "fsmp_pe.cu", "fsmp_pe_mix.cu", "fsmp_lucy.cu", "fsmp_runtime.cu",
-           "fsmp_probe.cu",
+           "fsmp_probe.cu", "fsmp_rhat.cu",
            "fsmp_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "fsmp_internal.h"), os.path.join(CSRC, "fsmp_pe_kernel.cuh"),
            os.path.join(INCLUDE, "fsmp.h")]

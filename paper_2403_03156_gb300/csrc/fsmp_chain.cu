@@ -154,6 +154,10 @@ struct ChainScalars {
   // between state changes and added with its holding time
   long long sN, sN2, sK, sK2;
   double q_cur, sQ, sQ2;
+  // the Wasserstein scalar of the PE times (Sec. 3.2), held like the charge summary: St is the
+  // sum of |t_k| in grid units over the PEs of the state
+  long long St;
+  double wt_cur, sWt, sWt2;
   int q_from, q_pending, pending_step;
   unsigned long long alg_words;
   double drift_max;
@@ -536,10 +540,17 @@ __device__ void refresh_state(const DevModel& M, Layout<T>& L, T* P, unsigned ch
 }
 
 // Add the charge summary held since the last state change (lane 0 of warp 0).
+// The Wasserstein scalar of the PE times is held with it: with a dummy PE at t = 0 added, the
+// 1-Wasserstein distance from the sequence to the dummy alone, sum_k |t_k| / (N + 1).
 template <typename T>
 __device__ __forceinline__ void close_charge_hold(ChainScalars<T>& S, int upto) {
   const int hold = upto - max(S.q_from, S.burn_in);
-  if (hold > 0) { S.sQ += S.q_cur * hold; S.sQ2 += S.q_cur * S.q_cur * hold; }
+  if (hold > 0) {
+    S.sQ += S.q_cur * hold;
+    S.sQ2 += S.q_cur * S.q_cur * hold;
+    S.sWt += S.wt_cur * hold;
+    S.sWt2 += S.wt_cur * S.wt_cur * hold;
+  }
 }
 
 // Bookkeeping of one decided step from its snapshot (one thread): counters, status, the
@@ -628,6 +639,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       S.N = 0; S.status = 0; S.n_acc_refresh = 0;
       S.sN = S.sN2 = S.sK = S.sK2 = 0;
       S.q_cur = 0.0; S.sQ = S.sQ2 = 0.0; S.q_from = 0; S.q_pending = 0; S.bk_pending = 0;
+      S.St = 0; S.wt_cur = 0.0; S.sWt = S.sWt2 = 0.0;
       for (int k = 0; k < 3; ++k) { S.acc[k] = 0; S.prop[k] = 0; }
       S.acc_t0 = 0; S.prop_t0 = 0; S.n_refresh = 0;
       S.alg_words = 0; S.drift_max = 0.0;
@@ -639,6 +651,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
         fsmp_summary o;
         o.mean_N = o.var_N = o.mean_t0 = o.var_t0 = o.mean_Q = o.var_Q = o.logL = o.logdet = NAN;
         o.drift_max = 0.0; o.alg_bytes = 0.0; o.lambda_hat = NAN;
+        o.mean_wt = o.var_wt = o.mean_we = o.var_we = NAN;
         for (int k = 0; k < 3; ++k) { o.acc[k] = 0; o.prop[k] = 0; }
         o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
         o.status = FSMP_ST_INVALID;
@@ -716,6 +729,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
           if (lane == 0) {
             close_charge_hold(S, S.pending_step);
             S.q_cur = S.N * M.mu_q + M.sq2 * (double)part;
+            S.wt_cur = M.g * (double)S.St / (double)(S.N + 1);
             S.q_from = S.pending_step;
             S.q_pending = 0;
           }
@@ -1066,9 +1080,11 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
         const T qv = warp_sum<T>(qs.value());
         if (lane == 0) L.red[warp * 8 + 5] = qv;
         if (tid == 0) {  // warp 0 lane 0 holds the step's proposal in registers
+          const int jrem = jump != 0 ? L.list[kk] : 0;  // the PE a death or update removes
           if (jump == 0) { L.list[N - 1] = jp; }
           else if (jump == 1) { L.list[kk] = L.list[N]; }
           else L.list[kk] = jp;
+          S.St += (jump != 1 ? abs(jp) : 0) - (jump != 0 ? abs(jrem) : 0);
           S.N = N;
           S.logdet += (double)S.dT_pending;
           S.logL += (double)S.dnu_pending;
@@ -1091,6 +1107,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
         if (lane == 0) {
           close_charge_hold(S, S.pending_step);
           S.q_cur = S.N * M.mu_q + M.sq2 * (double)part;
+          S.wt_cur = M.g * (double)S.St / (double)(S.N + 1);
           S.q_from = S.pending_step;
           S.q_pending = 0;
         }
@@ -1118,6 +1135,8 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       o.mean_N = mN; o.var_N = (double)S.sN2 * inv - mN * mN;
       o.mean_t0 = S.t_origin + M.g * mK; o.var_t0 = M.g * M.g * ((double)S.sK2 * inv - mK * mK);
       o.mean_Q = S.sQ * inv; o.var_Q = S.sQ2 * inv - o.mean_Q * o.mean_Q;
+      o.mean_wt = S.sWt * inv; o.var_wt = S.sWt2 * inv - o.mean_wt * o.mean_wt;
+      o.mean_we = 0.0; o.var_we = 0.0;  // one charge model: every e is 0
       o.logL = S.logL; o.logdet = S.logdet;
       o.drift_max = S.drift_max; o.alg_bytes = (double)S.alg_words * (double)sizeof(T);
       o.lambda_hat = S.lambda_hat;

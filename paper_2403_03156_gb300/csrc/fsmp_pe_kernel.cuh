@@ -380,7 +380,10 @@ __device__ __forceinline__ float u01_float(uint64_t x) {
 // Per-chain statistics (shared memory, written by the group's first lane).
 struct PeStats {
   long long sN, sN2, sK, sK2;
+  long long St, Se;  // sum of |t_k| (grid units) and of e_k over the PEs of the state
   double sQ, sQ2, q_cur, logdet, logL, drift_max, wsq;
+  // the Wasserstein scalars of the state (held like q_cur) and their sums
+  double wt_cur, we_cur, sWt, sWt2, sWe, sWe2;
   unsigned long long alg_words;
   int acc[3], prop[3], acc_t0, prop_t0, n_refresh, status, q_from, n_acc_refresh, refresh_fail, pad;
 };
@@ -451,14 +454,28 @@ __host__ __device__ inline size_t pe_ws_doubles(int n_cap) {
   return pe_ws_a2((size_t)n_cap * n_cap) + (2 + 2 * kSweepBlock) * pe_ws_a2(n_cap) + kSweepBlock * kSweepBlock;
 }
 
-// Charge hold: the state's charge summary q_cur holds from step q_from on; close it at step s.
+// Hold of the state's summaries: the charge summary q_cur and the Wasserstein scalars wt_cur,
+// we_cur hold from step q_from on (they change only with z); close the hold at step s.
 __device__ __forceinline__ void close_hold(PeStats& S, int s, int burn_in) {
   const int from = max(S.q_from, burn_in);
   if (s > from) {
     const double c = (double)(s - from);
     S.sQ += S.q_cur * c;
     S.sQ2 += S.q_cur * S.q_cur * c;
+    S.sWt += S.wt_cur * c;
+    S.sWt2 += S.wt_cur * S.wt_cur * c;
+    S.sWe += S.we_cur * c;
+    S.sWe2 += S.we_cur * S.we_cur * c;
   }
+}
+
+// The Wasserstein scalars of a state with N PEs (the convergence check of Sec. 3.2): with a
+// dummy PE at t = 0, e = 0 added, the 1-Wasserstein distance from the sequence to the dummy
+// alone is the mean of |t| (or of e) over the N + 1 points.
+__device__ __forceinline__ void set_wasserstein(PeStats& S, double g, int N) {
+  const double inv = 1.0 / (double)(N + 1);
+  S.wt_cur = g * (double)S.St * inv;
+  S.we_cur = (double)S.Se * inv;
 }
 
 struct RefreshOut {
@@ -1011,6 +1028,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         fsmp_summary o;
         o.mean_N = o.var_N = o.mean_t0 = o.var_t0 = o.mean_Q = o.var_Q = o.logL = o.logdet = NAN;
         o.drift_max = 0.0; o.alg_bytes = 0.0; o.lambda_hat = NAN;
+        o.mean_wt = o.var_wt = o.mean_we = o.var_we = NAN;
         for (int k = 0; k < 3; ++k) { o.acc[k] = 0; o.prop[k] = 0; }
         o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
         o.status = FSMP_ST_INVALID;
@@ -1049,6 +1067,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
     if (ln.sl == 0) {
       S.sN = S.sN2 = S.sK = S.sK2 = 0;
       S.sQ = S.sQ2 = 0.0; S.q_cur = 0.0; S.q_from = 0;
+      S.St = S.Se = 0; S.wt_cur = S.we_cur = 0.0;
+      S.sWt = S.sWt2 = S.sWe = S.sWe2 = 0.0;
       S.logdet = n * M.log_se2;
       S.logL = -0.5 * (n * kLog2Pi + S.logdet + wsq * M.inv_se2);
       S.wsq = wsq;
@@ -1157,9 +1177,18 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           Cp = Ns > 0 ? W.Cs : Cg;
           cap = Ns > 0 ? Ns : n_cap;
         }
+        long long st = 0;
+        for (int k = ln.sl; k < ni; k += L) st += abs(W.list[k]);
+        st = wsum(st, ln);
         if (ln.sl == 0) {
-          if (ok) S.q_cur = ms + c64(qs);
-          else S.status |= FSMP_ST_BADDET;
+          if (ok) {
+            S.q_cur = ms + c64(qs);
+            S.St = st;
+            S.Se = MIX ? (long long)ni * M.cm_mode : 0;
+            set_wasserstein(S, M.g, ni);
+          } else {
+            S.status |= FSMP_ST_BADDET;
+          }
         }
       }
       if (ln.sl == 0 && cut) S.status |= FSMP_ST_CAPACITY;
@@ -1370,6 +1399,10 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           close_hold(S, step, burn_in);
           S.q_cur = ms + c64(qs);
           S.q_from = step;
+          // the PE removed (death, update) and the one added (birth, update)
+          if (jump != 1) { S.St += abs(mv.jp); S.Se += mv.ep; }
+          if (jump != 0) { S.St -= abs(mv.jm); S.Se -= mv.em; }
+          set_wasserstein(S, M.g, N);
           S.logdet += (double)dT;
           S.logL += (double)dnu;
           S.n_acc_refresh++;
@@ -1453,6 +1486,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       o.mean_N = mN; o.var_N = (double)S.sN2 * inv - mN * mN;
       o.mean_t0 = t_origin + M.g * mK; o.var_t0 = M.g * M.g * ((double)S.sK2 * inv - mK * mK);
       o.mean_Q = S.sQ * inv; o.var_Q = S.sQ2 * inv - o.mean_Q * o.mean_Q;
+      o.mean_wt = S.sWt * inv; o.var_wt = S.sWt2 * inv - o.mean_wt * o.mean_wt;
+      o.mean_we = S.sWe * inv; o.var_we = S.sWe2 * inv - o.mean_we * o.mean_we;
       o.logL = S.logL; o.logdet = S.logdet;
       o.drift_max = S.drift_max; o.alg_bytes = (double)S.alg_words * 8.0;
       for (int k = 0; k < 3; ++k) { o.acc[k] = S.acc[k]; o.prop[k] = S.prop[k]; }

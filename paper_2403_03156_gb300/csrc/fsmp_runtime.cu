@@ -995,36 +995,6 @@ int fsmp_lucyddm(fsmp_ctx* c, const fsmp_lucy_batch* b, void* stream) {
   return note_user_work(c, (cudaStream_t)stream);
 }
 
-int fsmp_gelman_rubin(const fsmp_summary* chains, int m, int field, double* rhat) {
-  g_last_error[0] = 0;
-  if (!chains || !rhat || m < 2 || field < FSMP_RHAT_N || field > FSMP_RHAT_Q)
-    FAIL(FSMP_ERR_INVALID, "fsmp_gelman_rubin: bad arguments");
-  const int n = chains[0].n_samples;
-  if (n < 2) FAIL(FSMP_ERR_INVALID, "fsmp_gelman_rubin: fewer than two samples per chain");
-  double sx = 0.0;
-  for (int j = 0; j < m; ++j) {
-    if (chains[j].n_samples != n) FAIL(FSMP_ERR_INVALID, "fsmp_gelman_rubin: chains of different lengths");
-    sx += field == FSMP_RHAT_N ? chains[j].mean_N : (field == FSMP_RHAT_T0 ? chains[j].mean_t0 : chains[j].mean_Q);
-  }
-  const double xbar = sx / m;
-  double w = 0.0, b = 0.0;
-  for (int j = 0; j < m; ++j) {
-    const fsmp_summary& c = chains[j];
-    const double x = field == FSMP_RHAT_N ? c.mean_N : (field == FSMP_RHAT_T0 ? c.mean_t0 : c.mean_Q);
-    const double v = field == FSMP_RHAT_N ? c.var_N : (field == FSMP_RHAT_T0 ? c.var_t0 : c.var_Q);
-    w += v * n / (n - 1.0);
-    b += (x - xbar) * (x - xbar);
-  }
-  w /= m;
-  const double b_over_n = b / (m - 1.0);
-  if (!(w > 0.0)) {
-    *rhat = b_over_n > 0.0 ? INFINITY : 1.0;
-    return FSMP_OK;
-  }
-  *rhat = sqrt(((n - 1.0) / n * w + b_over_n) / w);
-  return FSMP_OK;
-}
-
 int fsmp_autotune(fsmp_ctx* c, const fsmp_device_batch* b, int sample, int trial_steps, fsmp_tune* out) {
   g_last_error[0] = 0;
   if (!c || !b || b->n_waveforms < 1 || !b->samples || !b->offsets || !b->lambda0 || sample < 1 || trial_steps < 1)

@@ -22,7 +22,8 @@ KERNEL_AUTO, KERNEL_SMEM, KERNEL_GLOBAL, KERNEL_PLAIN, KERNEL_PE = 0, 1, 2, 3, 4
 SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"),
                           ("var_t0", "<f8"), ("mean_Q", "<f8"), ("var_Q", "<f8"),
                           ("logL", "<f8"), ("logdet", "<f8"), ("drift_max", "<f8"),
-                          ("alg_bytes", "<f8"), ("lambda_hat", "<f8"), ("acc", "<i4", (3,)), ("prop", "<i4", (3,)),
+                          ("alg_bytes", "<f8"), ("lambda_hat", "<f8"), ("mean_wt", "<f8"), ("var_wt", "<f8"),
+                          ("mean_we", "<f8"), ("var_we", "<f8"), ("acc", "<i4", (3,)), ("prop", "<i4", (3,)),
                           ("acc_t0", "<i4"), ("prop_t0", "<i4"), ("N_final", "<i4"),
                           ("k0_final", "<i4"), ("status", "<i4"), ("n_samples", "<i4"),
                           ("n_refresh", "<i4"), ("reserved", "<i4")])
@@ -97,7 +98,7 @@ class Info(ctypes.Structure):
 EXPORTS = ["fsmp_create", "fsmp_submit", "fsmp_poll", "fsmp_destroy", "fsmp_run_device",
            "fsmp_get_tables", "fsmp_get_info", "fsmp_philox_blocks", "fsmp_strerror",
            "fsmp_last_error", "fsmp_measure_peaks", "fsmp_run_device_noalloc", "fsmp_autotune",
-           "fsmp_gelman_rubin", "fsmp_lucyddm", "fsmp_lambda_mle"]
+           "fsmp_gelman_rubin", "fsmp_gelman_diag", "fsmp_lucyddm", "fsmp_lambda_mle"]
 
 _lib = None
 
@@ -125,6 +126,8 @@ def load(build_if_missing: bool = False):
     L.fsmp_run_device_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(DeviceBatch), _vp]
     L.fsmp_autotune.argtypes = [_vp, ctypes.POINTER(DeviceBatch), _c_int, _c_int, ctypes.POINTER(Tune)]
     L.fsmp_gelman_rubin.argtypes = [_vp, _c_int, _c_int, ctypes.POINTER(_c_double)]
+    L.fsmp_gelman_diag.argtypes = [_vp, _c_int, _c_int, _c_double, ctypes.POINTER(_c_double),
+                                   ctypes.POINTER(_c_double)]
     L.fsmp_lucyddm.argtypes = [_vp, ctypes.POINTER(LucyBatch), _vp]
     L.fsmp_lambda_mle.argtypes = [_vp, _vp, _c_int, _c_int, _vp, _c_int, _vp]
     L.fsmp_get_tables.argtypes = [_vp, _vp, _c_int, ctypes.POINTER(_c_int), _c_int, _c_int, _vp, _vp]
@@ -444,7 +447,7 @@ def run_device_noalloc(params: dict, dev: dict, n_steps: int, burn_in: int = 0, 
     _check(load().fsmp_run_device_noalloc(ctypes.byref(prm), ctypes.byref(b), st), "fsmp_run_device_noalloc")
 
 
-RHAT_N, RHAT_T0, RHAT_Q = 0, 1, 2
+RHAT_N, RHAT_T0, RHAT_Q, RHAT_WT, RHAT_WE = 0, 1, 2, 3, 4
 
 
 def gelman_rubin(summaries: np.ndarray, field: int = RHAT_N) -> float:
@@ -453,6 +456,16 @@ def gelman_rubin(summaries: np.ndarray, field: int = RHAT_N) -> float:
     r = _c_double()
     _check(load().fsmp_gelman_rubin(s.ctypes.data, len(s), int(field), ctypes.byref(r)), "fsmp_gelman_rubin")
     return r.value
+
+
+def gelman_diag(summaries: np.ndarray, field: int = RHAT_N, confidence: float = 0.9):
+    """fsmp_gelman_diag over the chains of one waveform: (R, its upper confidence limit), the
+    degrees-of-freedom corrected potential scale reduction (Sec. 3.2 plots the 90 % limit)."""
+    s = np.ascontiguousarray(summaries, SUMMARY_DTYPE)
+    r, u = _c_double(), _c_double()
+    _check(load().fsmp_gelman_diag(s.ctypes.data, len(s), int(field), float(confidence), ctypes.byref(r),
+                                   ctypes.byref(u)), "fsmp_gelman_diag")
+    return r.value, u.value
 
 
 def summaries_from_bytes(buf) -> np.ndarray:

@@ -39,7 +39,7 @@ def test_strerror_without_gpu():
 
 def test_struct_sizes_match_header_layout():
     from paper_2403_03156_gb300 import fsmp
-    assert fsmp.SUMMARY_DTYPE.itemsize == 11 * 8 + 14 * 4
+    assert fsmp.SUMMARY_DTYPE.itemsize == 15 * 8 + 14 * 4
     assert fsmp.TRACE_DTYPE.itemsize == 5 * 8 + 4 * 4
 
 

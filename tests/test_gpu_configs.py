@@ -80,7 +80,8 @@ def _assert_summaries(s_gpu, s_orc, lam=True):
     # the variances come from the same exact integer sums as E[x^2] - E[x]^2, which cancels by
     # a factor E[x^2] / var (about 2000 for t0 on a 1024-sample window): the two sides' last-bit
     # roundings there show at 1e-12
-    for f in ("var_N", "var_t0", "mean_Q", "var_Q", "logL", "logdet") + (("lambda_hat",) if lam else ()):
+    for f in ("var_N", "var_t0", "mean_Q", "var_Q", "logL", "logdet", "mean_wt", "var_wt", "mean_we",
+              "var_we") + (("lambda_hat",) if lam else ()):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9, err_msg=f)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f], err_msg=f)

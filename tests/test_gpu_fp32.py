@@ -94,7 +94,7 @@ def test_fp32_summaries_match_oracle_statistically(lib, orc, kernel):
     with fsmp.Context(_params(wl, refresh_every=64, kernel=kernel[0], pe_lanes=kernel[1])) as ctx:
         s_gpu, _ = ctx.run(b)
     s_orc, _ = orc.run_batch(wl["params"], b, orc.MODE_INCREMENTAL, n_threads=16)
-    for f in ("mean_N", "mean_Q", "mean_t0", "lambda_hat"):
+    for f in ("mean_N", "mean_Q", "mean_t0", "lambda_hat", "mean_wt"):
         d = s_gpu[f] - s_orc[f]
         se = d.std(ddof=1) / math.sqrt(len(d))
         assert abs(d.mean()) <= 3 * se + 1e-9, (f, d.mean(), se)

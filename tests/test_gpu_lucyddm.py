@@ -117,7 +117,7 @@ def test_chain_from_lucyddm_state_fp64_lockstep(lib, orc, lanes):
     gpu_util.compare_traces(t_gpu, t_orc)
     for f in ("mean_N", "mean_t0"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12)
-    for f in ("mean_Q", "logL", "logdet"):
+    for f in ("mean_Q", "logL", "logdet", "mean_wt", "var_wt"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
     np.testing.assert_array_equal(s_gpu["status"], s_orc["status"])
     # the chains did start from the given PEs

@@ -42,7 +42,7 @@ def test_mcp_lockstep_fp64(lib, orc, lanes):
     gpu_util.compare_traces(t_gpu, t_orc)
     for f in ("mean_N", "var_N", "mean_t0", "var_t0"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12)
-    for f in ("mean_Q", "var_Q", "logL", "logdet", "lambda_hat"):
+    for f in ("mean_Q", "var_Q", "logL", "logdet", "lambda_hat", "mean_wt", "var_wt", "mean_we", "var_we"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f])

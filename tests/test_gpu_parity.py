@@ -68,7 +68,7 @@ def test_lockstep_fp64_config1(lib, orc, kernel, lanes):
     gpu_util.compare_traces(t_gpu, t_orc)
     for f in ("mean_N", "var_N", "mean_t0", "var_t0"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12)
-    for f in ("mean_Q", "var_Q", "logL", "logdet", "lambda_hat"):
+    for f in ("mean_Q", "var_Q", "logL", "logdet", "lambda_hat", "mean_wt", "var_wt", "mean_we", "var_we"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f])
@@ -134,3 +134,42 @@ def test_fp32_pileup_variant_statistics(lib, orc):
         assert abs(d.mean()) <= 3 * se + 1e-9, (f, d.mean(), se)
     assert np.all((s_gpu["status"] & (fsmp.ST_DRIFT | fsmp.ST_BADDET | fsmp.ST_NONFINITE | fsmp.ST_INVALID)) == 0)
     assert s_gpu["n_refresh"].sum() > 0
+
+
+@pytest.mark.parametrize("workload", ["plain_fp64_256x128", "mcp_uneven_20k"])
+def test_gelman_diag_of_gpu_chains_matches_oracle(lib, orc, workload):
+    """The convergence check as Sec. 3.2 plots it: four chains of each of 8 waveforms (distinct
+    RNG streams, t0 started across the prior range, FP64), and for N, t0 and the Wasserstein
+    scalars of {t_i} (and, with the MCP mixture, {e_i}) the degrees-of-freedom corrected R with
+    its 90 % upper limit from the GPU summaries (fsmp_gelman_diag) equal to the oracle's
+    gelman_diag on the oracle's raw per-step samples of the same chains (lockstep)."""
+    from oracle import convergence
+    burn, steps, m = 300, 1500, 4
+    wl = workloads.make_workload(workload, n_waveforms=8, n_steps=steps, burn_in=burn, seed=19)
+    params, b = wl["params"], wl["batch"]
+    idx = np.repeat(np.arange(8), m)
+    rb = workloads.subset(b, idx)
+    rb["wf_ids"] = np.arange(len(idx), dtype=np.uint64) + np.uint64(20_000)
+    rb["t0_init"] = np.tile(np.linspace(params["t0_lo"], params["t0_hi"], m), 8)
+    n_max = max(64, int(np.diff(rb["offsets"]).max()))
+    with fsmp.Context(params, n_max=n_max, precision=fsmp.FP64, kernel=fsmp.KERNEL_PE) as ctx:
+        s_gpu, _ = ctx.run(rb)
+    s_orc, t_orc = orc.run_batch(params, rb, orc.MODE_DEFINITION if params.get("n_mix") else orc.MODE_INCREMENTAL,
+                                 n_threads=16, trace=True)
+    g = params["grid_ns"]
+    raw = {fsmp.RHAT_N: t_orc["N"].astype(float), fsmp.RHAT_T0: rb["t_origin_ns"][:, None] + g * t_orc["k0"],
+           fsmp.RHAT_WT: t_orc["wt"]}
+    if params.get("n_mix"):
+        raw[fsmp.RHAT_WE] = t_orc["we"]
+    n_checked = 0
+    for w in range(8):
+        sl = slice(w * m, (w + 1) * m)
+        for field, x in raw.items():
+            xs = x[sl, burn:]
+            if np.all(xs.var(1) == 0):
+                continue
+            r, u = fsmp.gelman_diag(s_gpu[sl], field, 0.9)
+            r0, u0 = convergence.gelman_diag(xs, 0.9)
+            assert np.isfinite(r) and abs(r - r0) <= 1e-7 * r0 and abs(u - u0) <= 1e-7 * u0, (w, field, r, r0, u, u0)
+            n_checked += 1
+    assert n_checked >= 24

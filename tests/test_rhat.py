@@ -54,3 +54,41 @@ def test_rhat_limits():
     assert fsmp.gelman_rubin(_summaries_from_chains(const)) == 1.0
     with pytest.raises(fsmp.FsmpError):
         fsmp.gelman_rubin(_summaries_from_chains(const)[:1])
+
+
+def test_gelman_diag_matches_the_oracle_on_raw_chains():
+    """fsmp_gelman_diag (the degrees-of-freedom corrected R with its upper confidence limit, from
+    summaries) against the oracle's gelman_diag on the raw sample chains (numpy, scipy's F
+    quantile), for every field it reads, at the paper's 90 % and at 95 %: chains of one
+    distribution, chains apart, chains of unequal spread, few and many chains."""
+    _lib_or_skip()
+    from oracle import convergence
+    rng = np.random.default_rng(21)
+    fields = {fsmp.RHAT_N: ("mean_N", "var_N"), fsmp.RHAT_T0: ("mean_t0", "var_t0"),
+              fsmp.RHAT_Q: ("mean_Q", "var_Q"), fsmp.RHAT_WT: ("mean_wt", "var_wt"),
+              fsmp.RHAT_WE: ("mean_we", "var_we")}
+    n_cases = 0
+    for m in (2, 3, 4, 8, 16):
+        for n in (10, 200, 3000):
+            for spread in (0.0, 0.1, 1.0, 5.0):
+                x = rng.normal(0, 1, (m, n)) * rng.uniform(0.5, 1.5, (m, 1)) + spread * rng.normal(0, 1, (m, 1))
+                x = 3.0 * x + 40.0
+                for field, (fm, fv) in fields.items():
+                    s = np.zeros(m, fsmp.SUMMARY_DTYPE)
+                    s[fm], s[fv], s["n_samples"] = x.mean(1), x.var(1), n
+                    for conf in (0.9, 0.95):
+                        r, u = fsmp.gelman_diag(s, field, conf)
+                        r0, u0 = convergence.gelman_diag(x, conf)
+                        assert abs(r - r0) <= 1e-9 * r0 and abs(u - u0) <= 1e-9 * u0, (m, n, spread, field, r, r0, u, u0)
+                n_cases += 1
+    # equal within-chain variances: the chi-square limit of the upper limit
+    base = rng.normal(0, 1, 500)
+    x = np.stack([base + c for c in (0.0, 0.1, -0.2)])
+    s = np.zeros(3, fsmp.SUMMARY_DTYPE)
+    s["mean_wt"], s["var_wt"], s["n_samples"] = x.mean(1), x.var(1), 500
+    r, u = fsmp.gelman_diag(s, fsmp.RHAT_WT)
+    r0, u0 = convergence.gelman_diag(x)
+    assert abs(r - r0) <= 1e-9 * r0 and abs(u - u0) <= 1e-9 * u0
+    with pytest.raises(fsmp.FsmpError):
+        fsmp.gelman_diag(s, fsmp.RHAT_WT, 1.0)
+    assert n_cases == 60
