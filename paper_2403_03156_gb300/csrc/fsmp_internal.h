@@ -18,6 +18,7 @@ constexpr int kMaxWarps = 16;  // CTAs of at most 512 threads
 struct DevModel {
   double g, inv_g, dt;        // PE grid step, 1 / g (grid steps per ns), sample period
   int R;                      // grid points per sample
+  float inv_Rf;               // 1 / R in FP32 (a first estimate of the sample of a grid index)
   int Lt, L_V;                // SER table length (L_V * R) and support in samples
   int D;                      // phi tables cover grid offsets d in [-D, D]
   int LU;                     // longest union support of a two-PE jump (samples)

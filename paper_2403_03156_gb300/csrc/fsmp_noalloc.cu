@@ -154,7 +154,7 @@ extern "C" int fsmp_run_device_noalloc(const fsmp_params* p, const fsmp_device_b
       if (e != cudaSuccess) { ds.have_tables = false; cudaSetDevice(prev_dev); return fail(FSMP_ERR_CUDA, cudaGetErrorString(e)); }
       if (Lt < R) { ds.have_tables = false; cudaSetDevice(prev_dev); return fail(FSMP_ERR_INVALID, "SER table shorter than one sample"); }
       M = DevModel{};
-      M.R = (int)R; M.g = p->grid_ns; M.inv_g = 1.0 / p->grid_ns; M.dt = p->dt_sample_ns; M.D = (int)D;
+      M.R = (int)R; M.inv_Rf = 1.0f / (float)R; M.g = p->grid_ns; M.inv_g = 1.0 / p->grid_ns; M.dt = p->dt_sample_ns; M.D = (int)D;
       M.Lt = Lt; M.L_V = Lt / (int)R;
       M.LU = M.L_V + (int)ceil(8.7 / p->dt_sample_ns) + 2;
       M.V64 = (const double*)(B0 + tl.V64); M.V32 = (const float*)(B0 + tl.V32);

@@ -8,10 +8,10 @@ size_t pe_smem_bytes(const DevModel& M, int n_alloc, int warps, int lanes, int N
   const int chains = warps * (32 / lanes);
   const bool l16 = lanes == 16;
   if (M.precision == FSMP_FP64)
-    return pe_block_bytes<double>(M.Lt, M.n_cap) +
+    return pe_block_bytes<double>(M) +
            (size_t)chains * (l16 ? pe_chain_bytes<double, 16>(M.n_cap, n_alloc, M.win_extra, Ns)
                                  : pe_chain_bytes<double, 32>(M.n_cap, n_alloc, M.win_extra, Ns));
-  return pe_block_bytes<float>(M.Lt, M.n_cap) +
+  return pe_block_bytes<float>(M) +
          (size_t)chains * (l16 ? pe_chain_bytes<float, 16>(M.n_cap, n_alloc, M.win_extra, Ns)
                                : pe_chain_bytes<float, 32>(M.n_cap, n_alloc, M.win_extra, Ns));
 }

@@ -223,7 +223,7 @@ __device__ __forceinline__ int pe_draw_comp(const DevModel& M, double u) {
 
 // group sums of state values: over all lanes, or over lanes [0, m) (zero beyond m)
 template <int L, typename C> __device__ __forceinline__ C csum(C v, const Lanes<L> ln) {
-#pragma unroll
+#pragma unroll 1
   for (int o = L / 2; o > 0; o >>= 1) v = cadd(v, cshfl_xor<L>(v, o, ln.gm));
   return v;
 }
@@ -273,12 +273,12 @@ __device__ __forceinline__ C dot_row(const C* __restrict__ Cp, int q, const int*
 }
 
 template <int L, typename T> __device__ __forceinline__ T wsum(T v, const Lanes<L> ln) {
-#pragma unroll
+#pragma unroll 1
   for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(ln.gm, v, o, L);
   return v;
 }
 template <int L, typename T> __device__ __forceinline__ T wmax(T v, const Lanes<L> ln) {
-#pragma unroll
+#pragma unroll 1
   for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(ln.gm, v, o, L));
   return v;
 }
@@ -317,11 +317,16 @@ struct Sup {
 };
 __device__ __forceinline__ Sup pe_sup(const DevModel& M, int n, int j) {
   Sup s;
-  s.w0 = (int)floorf((float)(j + M.R - 1) / (float)M.R);  // exact for |j| < 2^22
-  s.ph = s.w0 * M.R - j;
-  const int mph = (M.Lt - s.ph + M.R - 1) / M.R;
-  s.ilo = max(0, -s.w0);
-  s.ihi = min(mph, n - s.w0);
+  // w0 = ceil(j / R) = floor((j + R - 1) / R): an FP32 estimate (off by at most one for
+  // |j| < 2^22) corrected by one integer step, instead of a division
+  const int num = j + M.R - 1;
+  int q = __float2int_rd((float)num * M.inv_Rf);
+  if (q * M.R > num) --q;
+  else if ((q + 1) * M.R <= num) ++q;
+  s.w0 = q;
+  s.ph = q * M.R - j;
+  s.ilo = max(0, -q);
+  s.ihi = min(M.L_V, n - q);  // every phase ph < R covers L_V samples (Lt = L_V R)
   if (s.ihi <= s.ilo) s.ilo = s.ihi = 0;  // no sample of the window: an all-zero column
   return s;
 }
@@ -412,8 +417,9 @@ template <typename T, int L> __host__ __device__ inline size_t pe_chain_bytes(in
          4 * a16(cs * (size_t)n_cap) + a16(sizeof(T) * n_alloc) + a16(sizeof(T) * win_extra) +
          a16(cs * (size_t)tri(Ns));
 }
-template <typename T> __host__ __device__ inline size_t pe_block_bytes(int Lt, int n_cap) {
-  return a16(sizeof(T) * Lt) + a16(sizeof(T) * (n_cap + 2));
+// Block tables: the SER, log(i) and 1 / i (i <= n_cap + 1).
+template <typename T> __host__ __device__ inline size_t pe_block_bytes(const DevModel& M) {
+  return a16(sizeof(T) * M.Lt) + a16(sizeof(T) * (M.n_cap + 2)) + a16(sizeof(double) * (M.n_cap + 2));
 }
 template <typename T, int L> __device__ PeChain<T> pe_carve(unsigned char* p, int n_cap, int n_alloc, int win_extra, int Ns) {
   using C = typename PeTab<T>::C;
@@ -472,10 +478,18 @@ __device__ __forceinline__ void close_hold(PeStats& S, int s, int burn_in) {
 // The Wasserstein scalars of a state with N PEs (the convergence check of Sec. 3.2): with a
 // dummy PE at t = 0, e = 0 added, the 1-Wasserstein distance from the sequence to the dummy
 // alone is the mean of |t| (or of e) over the N + 1 points.
-__device__ __forceinline__ void set_wasserstein(PeStats& S, double g, int N) {
-  const double inv = 1.0 / (double)(N + 1);
+// inv1[i] = 1 / i (a block table, so that no FP64 division runs in the step loop).
+__device__ __forceinline__ void set_wasserstein(PeStats& S, double g, int N, const double* inv1) {
+  const double inv = inv1[N + 1];
   S.wt_cur = g * (double)S.St * inv;
   S.we_cur = (double)S.Se * inv;
+}
+
+// lambda_FSMP at the chain end, out of line: the estimator's code stays out of the step loop's
+// instruction stream
+template <int L>
+__device__ __noinline__ double pe_lambda_mle(const int* h, int n_max, double lambda0, int sl, unsigned gm) {
+  return group_lambda_mle<L>(h, n_max, lambda0, sl, gm);
 }
 
 struct RefreshOut {
@@ -977,14 +991,17 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
   constexpr int kGroups = 32 / L;  // chains per warp
   const int cw = (threadIdx.x >> 5) * kGroups + ln.g, nchains = (blockDim.x >> 5) * kGroups;
   const int n_alloc = B.n_max, n_cap = M.n_cap, Ns = G.Ns;
-  // block tables: the SER and log(i), i = 1 .. n_cap + 1
+  // block tables: the SER, log(i) and 1 / i, i = 1 .. n_cap + 1
   T* Vs = reinterpret_cast<T*>(smem_raw);
   T* lgN = reinterpret_cast<T*>(smem_raw + a16(sizeof(T) * M.Lt));
+  double* inv1 = reinterpret_cast<double*>(smem_raw + a16(sizeof(T) * M.Lt) + a16(sizeof(T) * (n_cap + 2)));
   for (int m = threadIdx.x; m < M.Lt; m += blockDim.x) Vs[m] = PeTab<T>::V(M)[m];
-  for (int i = threadIdx.x; i < n_cap + 2; i += blockDim.x)
+  for (int i = threadIdx.x; i < n_cap + 2; i += blockDim.x) {
     lgN[i] = i > 0 ? (fp32 ? (T)logf((float)i) : (T)log((double)i)) : (T)0;
+    inv1[i] = i > 0 ? 1.0 / (double)i : 0.0;
+  }
   __syncthreads();
-  PeChain<T> W = pe_carve<T, L>(smem_raw + pe_block_bytes<T>(M.Lt, n_cap) +
+  PeChain<T> W = pe_carve<T, L>(smem_raw + pe_block_bytes<T>(M) +
                                     (size_t)cw * pe_chain_bytes<T, L>(n_cap, n_alloc, M.win_extra, Ns),
                                 n_cap, n_alloc, M.win_extra, Ns);
   PeStats& S = *W.st;
@@ -1185,7 +1202,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
             S.q_cur = ms + c64(qs);
             S.St = st;
             S.Se = MIX ? (long long)ni * M.cm_mode : 0;
-            set_wasserstein(S, M.g, ni);
+            set_wasserstein(S, M.g, ni, inv1);
           } else {
             S.status |= FSMP_ST_BADDET;
           }
@@ -1402,7 +1419,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           // the PE removed (death, update) and the one added (birth, update)
           if (jump != 1) { S.St += abs(mv.jp); S.Se += mv.ep; }
           if (jump != 0) { S.St -= abs(mv.jm); S.Se -= mv.em; }
-          set_wasserstein(S, M.g, N);
+          set_wasserstein(S, M.g, N, inv1);
           S.logdet += (double)dT;
           S.logL += (double)dnu;
           S.n_acc_refresh++;
@@ -1474,7 +1491,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         }
       }
     }
-    const double lam_hat = group_lambda_mle<L>(hist, n_cap, lambda0, ln.sl, ln.gm);
+    const double lam_hat = pe_lambda_mle<L>(hist, n_cap, lambda0, ln.sl, ln.gm);
     if (ln.sl == 0) {
       close_hold(S, n_steps, burn_in);
       fsmp_summary o;

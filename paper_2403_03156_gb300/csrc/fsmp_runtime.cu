@@ -705,6 +705,7 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
   const fsmp_params& p = c->p;
   DevModel& M = c->M;
   M.R = (int)lround(p.dt_sample_ns / p.grid_ns);
+  M.inv_Rf = 1.0f / (float)M.R;
   M.g = p.grid_ns;
   M.inv_g = 1.0 / p.grid_ns;
   M.dt = p.dt_sample_ns;
