@@ -233,6 +233,36 @@ template <int L, typename C> __device__ __forceinline__ C csum_first(C v, int m,
   return cshfl<L>(v, 0, ln.gm);
 }
 
+// twice a state value (exact)
+__device__ __forceinline__ double ctwice(double a) { return 2.0 * a; }
+__device__ __forceinline__ dd ctwice(dd a) { return dd{2.0 * a.hi, 2.0 * a.lo}; }
+__device__ __forceinline__ ff ctwice(ff a) { return ff{2.0f * a.hi, 2.0f * a.lo}; }
+
+// two group sums of state values in one butterfly
+template <int L, typename C> __device__ __forceinline__ void csum2(C& a, C& b, const Lanes<L> ln) {
+#pragma unroll 1
+  for (int o = L / 2; o > 0; o >>= 1) {
+    const C a2 = cshfl_xor<L>(a, o, ln.gm), b2 = cshfl_xor<L>(b, o, ln.gm);
+    a = cadd(a, a2);
+    b = cadd(b, b2);
+  }
+}
+
+// four group sums in one butterfly (two state values, two scoring-precision values), so that
+// their shuffles and additions overlap
+template <int L, typename C, typename T>
+__device__ __forceinline__ void gsum4(C& a, C& b, T& x, T& y, const Lanes<L> ln) {
+#pragma unroll 1
+  for (int o = L / 2; o > 0; o >>= 1) {
+    const C a2 = cshfl_xor<L>(a, o, ln.gm), b2 = cshfl_xor<L>(b, o, ln.gm);
+    const T x2 = __shfl_xor_sync(ln.gm, x, o, L), y2 = __shfl_xor_sync(ln.gm, y, o, L);
+    a = cadd(a, a2);
+    b = cadd(b, b2);
+    x += x2;
+    y += y2;
+  }
+}
+
 // C^-1 is symmetric and stored as its lower triangle, row by row: entry (i, j), j <= i, at
 // tri(i) + j. The storage has no row stride, so a chain's C^-1 moves from the shared tile to
 // its global slot by a plain copy.
@@ -807,11 +837,35 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   // always apply both terms, so that they have no branches on the move type.
   const int krow = has_m ? kk : 0;
   const int npu = has_p ? np : 0;
+  if constexpr (BIG) {
 #pragma unroll 1
-  for (int i = ln.sl; i < N; i += L) {
-    const C ci = Cp[pk(krow, i)];
-    W.cv[i] = has_m ? ci : czero<C>();
-    W.uv[i] = dot_row<C, BIG>(Cp, i, W.ovi, W.ovb, npu, skip);
+    for (int i = ln.sl; i < N; i += L) {
+      const C ci = Cp[pk(krow, i)];
+      W.cv[i] = has_m ? ci : czero<C>();
+      W.uv[i] = dot_row<C, BIG>(Cp, i, W.ovi, W.ovb, npu, skip);
+    }
+  } else {
+    // s lanes per row (s N <= L), each summing every s-th term of the row's product with b~,
+    // then a butterfly over the s lanes: the dependent chain of a row is npu / s terms long
+    int s = 1;
+    while (s < 8 && 2 * s * N <= L) s <<= 1;
+    const int rq = ln.sl / s, qq = ln.sl - rq * s, rpp = L / s;
+#pragma unroll 1
+    for (int i0 = 0; i0 < N; i0 += rpp) {
+      const int i = i0 + rq;
+      C acc = czero<C>();
+      if (i < N) {
+#pragma unroll 1
+        for (int a = qq; a < npu; a += s)
+          if (W.ovi[a] != skip) acc = cfma(Cp[pk(i, W.ovi[a])], W.ovb[a], acc);
+      }
+#pragma unroll 1
+      for (int o = 1; o < s; o <<= 1) acc = cadd(acc, cshfl_xor<L>(acc, o, ln.gm));
+      if (i < N && qq == 0) {
+        W.cv[i] = has_m ? Cp[pk(krow, i)] : czero<C>();
+        W.uv[i] = acc;
+      }
+    }
   }
   if (ln.sl == 0 && jump == 0) { W.cv[N] = czero<C>(); W.uv[N] = czero<C>(); }  // slot N of a birth (N < n_cap)
   __syncwarp(ln.gm);
@@ -821,22 +875,21 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
     fv = cmul(cadd(mv.vk, mum), ig);
   }
   if (has_p) {
-    // b^T v in full state precision (the scoring used an FP32 sum)
-    C bvf = czero<C>();
+    // b^T v in full state precision (the scoring used an FP32 sum) and, for an update, the
+    // entry of b for PE k, in one butterfly
+    C bvf = czero<C>(), bk = czero<C>();
 #pragma unroll 1
-    for (int a = ln.sl; a < np; a += L) bvf = cfma(W.ovb[a], W.v[W.ovi[a]], bvf);
-    bvf = csum(bvf, ln);
-    C bk = czero<C>(), wk = czero<C>();
+    for (int a = ln.sl; a < np; a += L) {
+      bvf = cfma(W.ovb[a], W.v[W.ovi[a]], bvf);
+      if (jump == 2 && W.ovi[a] == kk) bk = W.ovb[a];
+    }
+    const C wk = jump == 2 ? W.uv[kk] : czero<C>();  // read by every lane before the butterfly
+    csum2(bvf, bk, ln);
     if (jump == 2) {
       // u' = w - c w_k / gamma on the system without PE k
-      wk = W.uv[kk];
       const C wkg = cneg(cmul(wk, ig));
 #pragma unroll 1
       for (int i = ln.sl; i < N; i += L) W.uv[i] = (i == kk) ? czero<C>() : cfma(W.cv[i], wkg, W.uv[i]);
-#pragma unroll 1
-      for (int a = ln.sl; a < np; a += L)
-        if (W.ovi[a] == kk) bk = W.ovb[a];
-      bk = csum(bk, ln);
       __syncwarp(ln.gm);
     }
     C bu = czero<C>();
@@ -1314,41 +1367,33 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           __syncwarp(ln.gm);
           mv.np = np;
           mv.aa = xcorr<C>(M, tc, sp, 0);
-          // rows of C^-1 b on the overlap set: lane a holds (C^-1 b)_{ovi[a]} (a < L), so that
-          // b^T C^-1 b and b^T v reduce over the group and (C^-1 b)_k is one of them for an update
+          // b^T C^-1 b over the lower triangle of the overlap block (lanes over its entries, the
+          // off-diagonal ones counted twice), b^T v, (C^-1 b)_k of an update and a_+^T y, then one
+          // reduction of the four over the group
           T ayp = (T)0;
 #pragma unroll 1
           for (int i = sp.ilo + ln.sl; i < sp.ihi; i += L) ayp += Vs[sp.ph + i * R] * W.y[sp.w0 + i];
           C qp = czero<C>(), ck = czero<C>();
           T bvp = (T)0;
-          int kpos = -1;
+          const int nt = tri(np);
 #pragma unroll 1
-          for (int a0 = 0; a0 < np; a0 += L) {
-            const int a = a0 + ln.sl;
-            if (a < np) {
-              const C rq = dot_row<C, BIG>(Cp, W.ovi[a], W.ovi, W.ovb, np, -1);
-              const C ba = W.ovb[a];
-              qp = cfma(ba, rq, qp);
-              bvp += (T)cnum(ba) * (T)cnum(W.v[W.ovi[a]]);
-              if (jump == 2 && W.ovi[a] == kk) { ck = rq; kpos = a; }
-            }
+          for (int e = ln.sl; e < nt; e += L) {
+            int a, b2;
+            untri(e, a, b2);
+            const C t = cmul(Cp[pk(W.ovi[a], W.ovi[b2])], cmul(W.ovb[a], W.ovb[b2]));
+            qp = cadd(qp, a == b2 ? t : ctwice(t));
           }
-          mv.quad = np <= L ? csum_first(qp, np, ln) : csum(qp, ln);
-          const T bvT = wsum(bvp, ln);  // b^T v at the scoring precision (the accept recomputes it)
-          const T ayT = wsum(ayp, ln);
+#pragma unroll 1
+          for (int a = ln.sl; a < np; a += L) {
+            const C ba = W.ovb[a];
+            bvp += (T)cnum(ba) * (T)cnum(W.v[W.ovi[a]]);
+            if (jump == 2) ck = cfma(Cp[pk(kk, W.ovi[a])], ba, ck);
+          }
+          gsum4<L>(qp, ck, bvp, ayp, ln);
+          mv.quad = qp;
+          const T bvT = bvp;  // b^T v at the scoring precision (the accept recomputes it)
+          const T ayT = ayp;
           mv.ay = cfromf(ayT);
-          if (jump == 2) {
-            // (C^-1 b)_k: from the lane that holds PE k's row, else (no overlap with the old
-            // position) a separate dot product
-            const unsigned hk = gballot(kpos >= 0, ln);
-            if (hk) {
-              ck = cshfl<L>(ck, __ffs(hk) - 1, ln.gm);
-            } else {
-              C c2 = czero<C>();
-              for (int a = ln.sl; a < np; a += L) c2 = cfma(Cp[pk(kk, W.ovi[a])], W.ovb[a], c2);
-              ck = csum(c2, ln);
-            }
-          }
           mpp = (T)cnum(csub(mv.aa, mv.quad)) * ise2T;
           gp = (ayT - bvT) * ise2T;
           mmp = (T)cnum(ck);  // times 1 / sigma_-^2 below (update only)
