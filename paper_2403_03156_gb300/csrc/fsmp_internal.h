@@ -35,6 +35,8 @@ struct DevModel {
   double cm_mu[FSMP_MAX_MIX], cm_q[FSMP_MAX_MIX], cm_iq[FSMP_MAX_MIX], cm_r[FSMP_MAX_MIX], cm_lr[FSMP_MAX_MIX];
   double cm_cum[FSMP_MAX_MIX];
   float cm_mu_hi[FSMP_MAX_MIX], cm_mu_lo[FSMP_MAX_MIX], cm_r_hi[FSMP_MAX_MIX], cm_r_lo[FSMP_MAX_MIX];
+  // FP32 copies of cm_mu, cm_q, cm_iq, cm_r for the FP32 scoring (no FP64 conversion in the step)
+  float cmf_mu[FSMP_MAX_MIX], cmf_q[FSMP_MAX_MIX], cmf_iq[FSMP_MAX_MIX], cmf_r[FSMP_MAX_MIX];
   double t0_lo, t0_hi;
   int sample_t0;
   double J, log_J;

@@ -212,6 +212,23 @@ template <typename C> __device__ __forceinline__ C c_r(const DevModel& M, int e)
 template <> __device__ __forceinline__ dd c_r<dd>(const DevModel& M, int e) { return dd{M.cm_r[e], 0.0}; }
 template <> __device__ __forceinline__ ff c_r<ff>(const DevModel& M, int e) { return ff{M.cm_r_hi[e], M.cm_r_lo[e]}; }
 
+// A charge component's constant in the scoring precision T: the FP32 copies in FP32 mode, so
+// that the step loop converts nothing from FP64 (an FP64 instruction costs this part as much as
+// 64 FP32 ones).
+template <typename T> struct CmT;
+template <> struct CmT<float> {
+  __device__ static float mu(const DevModel& M, int e) { return M.cmf_mu[e]; }
+  __device__ static float q(const DevModel& M, int e) { return M.cmf_q[e]; }
+  __device__ static float iq(const DevModel& M, int e) { return M.cmf_iq[e]; }
+  __device__ static float r(const DevModel& M, int e) { return M.cmf_r[e]; }
+};
+template <> struct CmT<double> {
+  __device__ static double mu(const DevModel& M, int e) { return M.cm_mu[e]; }
+  __device__ static double q(const DevModel& M, int e) { return M.cm_q[e]; }
+  __device__ static double iq(const DevModel& M, int e) { return M.cm_iq[e]; }
+  __device__ static double r(const DevModel& M, int e) { return M.cm_r[e]; }
+};
+
 // Component of a born or updated PE, e+ ~ G (Sec. 2.4): the smallest e whose cumulative
 // probability exceeds the uniform u, else the last component with G > 0. The comparison is
 // in FP64 in both modes, so the draw is the same as the FP64 reference's.
@@ -826,7 +843,7 @@ __device__ __noinline__ AcceptOut<typename PeTab<T>::C> pe_accept(const DevModel
   using C = typename PeTab<T>::C;
   const int em = MIX ? mv.em : 0, ep = MIX ? mv.ep : 0;
   const C mum = c_mu<C>(M, em), mup = c_mu<C>(M, ep), rrp = c_r<C>(M, ep);
-  const T mumT = (T)M.cm_mu[em], mupT = (T)M.cm_mu[ep];
+  const T mumT = CmT<T>::mu(M, em), mupT = CmT<T>::mu(M, ep);
   const int R = M.R, np = mv.np, kk = mv.kk, jump = mv.jump;
   const bool has_m = jump != 0, has_p = jump != 1;
   const int skip = jump == 2 ? kk : -1;
@@ -1400,9 +1417,9 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           words += (unsigned long long)(N + 2 * np + 2 * (sp.ihi - sp.ilo) + np * np + np);
         }
         if (jump != 0) {
-          const T iqm = (T)M.cm_iq[mv.em];
+          const T iqm = CmT<T>::iq(M, mv.em);
           mv.vk = W.v[kk];
-          em = (T)M.cm_r[mv.em] * (T)cnum(Cp[tri(kk) + kk]);
+          em = CmT<T>::r(M, mv.em) * (T)cnum(Cp[tri(kk) + kk]);
           mmm = ((T)1 - em) * iqm;
           gm = (T)cnum(mv.vk) * iqm;
           mmp *= iqm;
@@ -1414,8 +1431,8 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       if (valid) {
         // det(I + Lambda M), Lambda = diag(-q_-, q_+) (q = sigma_e^2 of the PE concerned), with
         // 1 - q_- m_-- = em; lambda = (-mu_-, mu_+) (Eq. (DeltaU), Appendix A.2)
-        const T qm = (T)M.cm_q[mv.em], qp = (T)M.cm_q[mv.ep];
-        const T mum = (T)M.cm_mu[mv.em], mup = (T)M.cm_mu[mv.ep];
+        const T qm = CmT<T>::q(M, mv.em), qp = CmT<T>::q(M, mv.ep);
+        const T mum = CmT<T>::mu(M, mv.em), mup = CmT<T>::mu(M, mv.ep);
         const T Dd = em * ((T)1 + qp * mpp) + qm * qp * mmp * mmp;
         if (!(Dd > (T)0)) {
           la = (T)-INFINITY;

@@ -740,6 +740,10 @@ int fsmp_create(const fsmp_params* params, fsmp_ctx** out) {
       if (on && G > 0.0) M.cm_last = e;
       split_pair(M.cm_mu[e], &M.cm_mu_hi[e], &M.cm_mu_lo[e]);
       split_pair(M.cm_r[e], &M.cm_r_hi[e], &M.cm_r_lo[e]);
+      M.cmf_mu[e] = (float)M.cm_mu[e];
+      M.cmf_q[e] = (float)M.cm_q[e];
+      M.cmf_iq[e] = (float)M.cm_iq[e];
+      M.cmf_r[e] = (float)M.cm_r[e];
     }
   }
   M.t0_lo = p.t0_lo; M.t0_hi = p.t0_hi; M.sample_t0 = p.sample_t0 ? 1 : 0;
