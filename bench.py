@@ -253,15 +253,22 @@ def buckets_of(lengths):
     return out
 
 
+def cost_order(lengths, lambda0):
+    """Waveforms by decreasing expected chain cost, window length x (1 + lambda0): the
+    persistent launch hands chains out in this order, so the heaviest start first and the
+    launch's tail is made of light chains."""
+    return np.argsort(-(np.asarray(lengths, np.float64) * (1.0 + np.asarray(lambda0, np.float64))), kind="stable")
+
+
 def device_batches(torch, wl, dev, n_smem_max, one_launch=False):
     """Split the workload into length buckets, each a device-resident sub-batch (or, for the
-    PE-space kernel, one batch in decreasing window length)."""
+    PE-space kernel, one batch in decreasing expected chain cost)."""
     from paper_2403_03156_gb300 import fsmp, workloads
     b = wl["batch"]
     lengths = np.diff(b["offsets"]).astype(np.int64)
     subs = []
     if one_launch:
-        order = np.argsort(-lengths, kind="stable")
+        order = cost_order(lengths, b["lambda0"])
         groups = [(order, int(lengths.max()))]
     else:
         groups = buckets_of(lengths)

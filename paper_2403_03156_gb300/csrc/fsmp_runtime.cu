@@ -342,10 +342,10 @@ int run_bucketed(fsmp_ctx* c, BatchView B, const int32_t* order_dev, const std::
                  cudaStream_t st, int set) {
   static const int kEdges[] = {64, 96, 128, 160, 192, 224, 256, 320, 384, 512, 768, 1024, 2048, 8192};
   const int W = (int)n_sorted.size();
-  if (c->p.kernel == FSMP_KERNEL_PE) {  // one launch: warps take chains longest first
+  if (c->p.kernel == FSMP_KERNEL_PE) {  // one launch: warps take chains in the given order
     BatchView b = B;
     b.order = order_dev;
-    b.n_max = W > 0 ? n_sorted[0] : 1;
+    b.n_max = W > 0 ? *std::max_element(n_sorted.begin(), n_sorted.end()) : 1;
     return run_view(c, b, st, set);
   }
   int i = 0;
@@ -458,12 +458,21 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
     }
     so += r->samples.size();
   }
-  // processing order: decreasing window length (longest chains first, and length buckets)
+  // processing order: the PE-space kernel takes chains by decreasing expected cost, window
+  // length x (1 + lambda0), so that the heaviest start first and the launch's tail is light;
+  // the Sigma^-1 kernels by decreasing window length (their length buckets)
   std::vector<int> n_sorted(W);
   for (int i = 0; i < W; ++i) order[i] = i;
-  std::stable_sort(order, order + W, [&](int a, int b) {
-    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
-  });
+  if (c->p.kernel == FSMP_KERNEL_PE) {
+    std::stable_sort(order, order + W, [&](int a, int b) {
+      return (double)(offsets[a + 1] - offsets[a]) * (1.0 + lambda0[a]) >
+             (double)(offsets[b + 1] - offsets[b]) * (1.0 + lambda0[b]);
+    });
+  } else {
+    std::stable_sort(order, order + W, [&](int a, int b) {
+      return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+    });
+  }
   for (int i = 0; i < W; ++i) n_sorted[i] = offsets[order[i] + 1] - offsets[order[i]];
   // packs of the Sigma^-1 kernels that use context scratch (global Sigma^-1, or the FP32-mode
   // refresh workspace) share it, so they run on one stream; the PE-space kernel has a scratch
