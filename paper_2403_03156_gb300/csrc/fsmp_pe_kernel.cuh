@@ -1362,6 +1362,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         if (jump != 1) {
           const Sup sp = pe_sup(M, n, jp);
           mv.sp = sp;
+          mv.aa = xcorr<C>(M, tc, sp, 0);  // issued first: its table load overlaps the scan's
           // PEs overlapping a_+, with b_q = a_q^T a_+
           int np = 0;
 #pragma unroll 1
@@ -1383,7 +1384,6 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           }
           __syncwarp(ln.gm);
           mv.np = np;
-          mv.aa = xcorr<C>(M, tc, sp, 0);
           // b^T C^-1 b over the lower triangle of the overlap block (lanes over its entries, the
           // off-diagonal ones counted twice), b^T v, (C^-1 b)_k of an update and a_+^T y, then one
           // reduction of the four over the group
