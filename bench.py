@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered events/s (0: the workload's)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the arrival stream")
     ap.add_argument("--serve-pool", type=int, default=1024, help="serving: distinct events replayed by the stream")
+    ap.add_argument("--serve-streams", type=int, default=0, help="serving: concurrent launch streams (0: library default)")
     ap.add_argument("--stage", default="chain", choices=["chain", "lucyddm"],
                     help="lucyddm: time the LucyDDM deconvolution (Sec. 2.3) of the workload instead of the chains")
     ap.add_argument("--lucy-iters", type=int, default=2000, help="lucyddm stage: Lucy iterations")
@@ -709,7 +710,7 @@ def run_serving(args):
         e["burn_in"] = n_steps // 5
     rate = args.rate or cfg["rate_hz"]
     ctx = fsmp.Context(dict(params, precision=fsmp.FP32_REFRESH, refresh_every=cfg.get("refresh_every", 64),
-                            n_max=cfg["win_max"], device=local, max_queued=1 << 20))
+                            n_max=cfg["win_max"], device=local, max_queued=1 << 20, n_streams=args.serve_streams))
     # launch shape from timed trials on the pool of events (untimed), and the same events as one
     # device batch: the rate the serving loop would reach if every event arrived at once
     pb = concat_events(pool)

@@ -656,6 +656,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
         o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
         o.status = FSMP_ST_INVALID;
         *S.out = o;
+        note_chain_done(B, wi);
       }
       __syncthreads();
       continue;
@@ -1144,6 +1145,7 @@ __global__ void __launch_bounds__(512) chain_kernel(DevModel M, BatchView B, T* 
       o.acc_t0 = S.acc_t0; o.prop_t0 = S.prop_t0; o.N_final = S.N; o.k0_final = k0;
       o.status = S.status; o.n_samples = ns; o.n_refresh = S.n_refresh; o.reserved = 0;
       *S.out = o;
+      note_chain_done(B, wi);
     }
     __syncthreads();
   }

@@ -1120,6 +1120,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
         o.acc_t0 = o.prop_t0 = o.N_final = o.k0_final = o.n_samples = o.n_refresh = o.reserved = 0;
         o.status = FSMP_ST_INVALID;
         *out = o;
+        note_chain_done(B, wi);
       }
       __syncwarp(ln.gm);
       continue;
@@ -1573,6 +1574,7 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
       o.acc_t0 = S.acc_t0; o.prop_t0 = S.prop_t0; o.N_final = N; o.k0_final = k0;
       o.status = S.status; o.n_samples = ns; o.n_refresh = S.n_refresh; o.reserved = 0;
       *out = o;
+      note_chain_done(B, wi);
     }
     __syncwarp(ln.gm);
   }

@@ -75,6 +75,10 @@ struct Pack {
   std::atomic<int> done{0};
   double t_done = 0;
   struct fsmp_ctx* ctx = nullptr;
+  // per request: chains finished (host-mapped counters the kernels bump), and whether the
+  // serving loop has returned it
+  volatile unsigned int* req_done = nullptr;
+  std::vector<char> returned;
 };
 
 }  // namespace
@@ -305,6 +309,7 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st, int set) {
         else b1.trace = B.trace + (size_t)i * B.n_steps;
       }
       b1.order = nullptr;
+      if (B.req_idx) b1.req_idx = B.req_idx + i;
       cudaError_t e = launch_chains(c->M, b1, FSMP_KERNEL_GLOBAL, s, c->gscratch, c->gscratch_bytes, nullptr, 0, 0, st);
       c->n_launches++;
       if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
@@ -373,10 +378,12 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct PackLayout {
   size_t samples, offsets, lambda0, t_origin, T_lo, T_hi, t0_init, wf_ids, seeds, nsteps, burnin,
-      trace_off, order, in_end, out, trace, total;
+      trace_off, order, req_idx, in_end, out, trace, done, total;
 };
 
-PackLayout pack_layout(size_t n_samp, int W, size_t n_trace) {
+// Inputs (staged in pinned memory and copied to the device), then the outputs and the per-request
+// counters, which the kernels write straight into the pinned host block (host-mapped).
+PackLayout pack_layout(size_t n_samp, int W, size_t n_trace, int n_req = 0) {
   PackLayout L;
   size_t o = 0;
   L.samples = o; o = align_up(o + n_samp * 4, 256);
@@ -392,16 +399,19 @@ PackLayout pack_layout(size_t n_samp, int W, size_t n_trace) {
   L.burnin = o; o = align_up(o + (size_t)W * 4, 256);
   L.trace_off = o; o = align_up(o + (size_t)W * 8, 256);
   L.order = o; o = align_up(o + (size_t)W * 4, 256);
+  L.req_idx = o; o = align_up(o + (size_t)W * 4, 256);
   L.in_end = o;
   L.out = o; o = align_up(o + (size_t)W * sizeof(fsmp_summary), 256);
   L.trace = o; o = align_up(o + n_trace * sizeof(fsmp_trace), 256);
+  L.done = o; o = align_up(o + (size_t)n_req * sizeof(unsigned int), 256);
   L.total = o;
   return L;
 }
 
+// Device memory a request holds while it runs: its inputs (outputs go to pinned host memory).
 size_t request_bytes(const Request* r) {
   size_t n_trace = r->record_trace ? (size_t)r->W * r->n_steps : 0;
-  return pack_layout(r->samples.size(), r->W, n_trace).total;
+  return pack_layout(r->samples.size(), r->W, n_trace, 1).in_end;
 }
 
 // Stage and launch one pack (called by the worker without the lock held).
@@ -415,8 +425,9 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
     if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
     n_max = std::max(n_max, r->n_max);
   }
-  PackLayout L = pack_layout(n_samp, W, n_trace);
-  pk->dev_bytes = L.total;
+  const int n_req = (int)pk->reqs.size();
+  PackLayout L = pack_layout(n_samp, W, n_trace, n_req);
+  pk->dev_bytes = L.in_end;
   pk->host_bytes = L.total;
   pk->in_bytes = L.in_end;
   pk->out_off = L.out;
@@ -436,8 +447,13 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   int32_t* burnin = (int32_t*)(h + L.burnin);
   int64_t* toff = (int64_t*)(h + L.trace_off);
   int32_t* order = (int32_t*)(h + L.order);
+  int32_t* req_idx = (int32_t*)(h + L.req_idx);
+  unsigned int* req_done = (unsigned int*)(h + L.done);
+  for (int q = 0; q < n_req; ++q) req_done[q] = 0;
+  pk->req_done = req_done;
+  pk->returned.assign(n_req, 0);
   size_t so = 0, to = 0;
-  int wi = 0;
+  int wi = 0, rq = 0;
   offsets[0] = 0;
   for (Request* r : pk->reqs) {
     memcpy(samples + so, r->samples.data(), r->samples.size() * 4);
@@ -455,8 +471,10 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
       burnin[wi] = r->burn_in;
       toff[wi] = r->record_trace ? (int64_t)to : -1;
       if (r->record_trace) to += (size_t)r->n_steps;
+      req_idx[wi] = rq;
     }
     so += r->samples.size();
+    ++rq;
   }
   // processing order: the PE-space kernel takes chains by decreasing expected cost, window
   // length x (1 + lambda0), so that the heaviest start first and the launch's tail is light;
@@ -482,7 +500,11 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
                              c->p.kernel == FSMP_KERNEL_PLAIN || c->p.precision != FSMP_FP64);
   cudaStream_t st = uses_scratch ? c->gmem_stream : c->streams[pk->stream];
   pk->stream = uses_scratch ? -1 : pk->stream;
-  { cudaError_t e_ = cudaMallocAsync(&pk->dev, L.total, st); if (e_ != cudaSuccess) { set_error("cudaMallocAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  { cudaError_t e_ = cudaMallocAsync(&pk->dev, L.in_end, st); if (e_ != cudaSuccess) { set_error("cudaMallocAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_NOMEM; } }
+  // the outputs and counters stay in the pinned host block, which the kernels write through
+  // its device mapping
+  unsigned char* hd = nullptr;
+  { cudaError_t e_ = cudaHostGetDevicePointer((void**)&hd, pk->host, 0); if (e_ != cudaSuccess) { set_error("cudaHostGetDevicePointer", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   { cudaError_t e_ = cudaMemcpyAsync(pk->dev, pk->host, L.in_end, cudaMemcpyHostToDevice, st); if (e_ != cudaSuccess) { set_error("cudaMemcpyAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   unsigned char* d = (unsigned char*)pk->dev;
   BatchView B{};
@@ -502,45 +524,63 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   B.n_steps_arr = (const int32_t*)(d + L.nsteps);
   B.burn_in_arr = (const int32_t*)(d + L.burnin);
   B.trace_off = n_trace ? (const int64_t*)(d + L.trace_off) : nullptr;
-  B.out = (fsmp_summary*)(d + L.out);
-  B.trace = n_trace ? (fsmp_trace*)(d + L.trace) : nullptr;
+  B.out = (fsmp_summary*)(hd + L.out);
+  B.trace = n_trace ? (fsmp_trace*)(hd + L.trace) : nullptr;
+  B.req_idx = (const int32_t*)(d + L.req_idx);
+  B.req_done = (unsigned int*)(hd + L.done);
   int rc = run_bucketed(c, B, (const int32_t*)(d + L.order), n_sorted, st,
                         pk->stream < 0 ? (int)c->streams.size() : pk->stream);
   if (rc) return rc;
-  if (cudaMemcpyAsync(h + L.out, d + L.out, L.total - L.out, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return FSMP_ERR_CUDA;
   { cudaError_t e_ = cudaFreeAsync(pk->dev, st); if (e_ != cudaSuccess) { set_error("cudaFreeAsync", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   { cudaError_t e_ = cudaLaunchHostFunc(st, pack_done_cb, pk); if (e_ != cudaSuccess) { set_error("cudaLaunchHostFunc", cudaGetErrorString(e_), __LINE__); return FSMP_ERR_CUDA; } }
   return FSMP_OK;
 }
 
+// Copy request q's outputs out of the pack's pinned block into the request (its chains are done).
+void finish_request(Pack* pk, int q) {
+  size_t n_samp = 0, n_trace = 0;
+  int W = 0;
+  for (Request* r : pk->reqs) {
+    n_samp += r->samples.size();
+    W += r->W;
+    if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
+  }
+  PackLayout L = pack_layout(n_samp, W, n_trace, (int)pk->reqs.size());
+  const unsigned char* h = (const unsigned char*)pk->host;
+  const fsmp_summary* out = (const fsmp_summary*)(h + L.out);
+  const fsmp_trace* tr = (const fsmp_trace*)(h + L.trace);
+  size_t to = 0;
+  for (int i = 0; i < q; ++i)
+    if (pk->reqs[i]->record_trace) to += (size_t)pk->reqs[i]->W * pk->reqs[i]->n_steps;
+  Request* r = pk->reqs[q];
+  r->out.assign(out + pk->first[q], out + pk->first[q] + r->W);
+  if (r->record_trace) r->trace.assign(tr + to, tr + to + (size_t)r->W * r->n_steps);
+  r->t_done = now_s();
+  r->status = FSMP_OK;
+}
+
+// Requests of the in-flight pack whose chains have all finished (the kernels' counters in the
+// pinned block), not yet returned.
+std::vector<int> ready_requests(Pack* pk) {
+  std::vector<int> ready;
+  for (int q = 0; q < (int)pk->reqs.size(); ++q) {
+    if (pk->returned[q]) continue;
+    if (pk->req_done[q] >= (unsigned int)pk->reqs[q]->W) ready.push_back(q);
+  }
+  if (!ready.empty()) std::atomic_thread_fence(std::memory_order_acquire);  // then read their outputs
+  return ready;
+}
+
 void finish_pack(fsmp_ctx* c, Pack* pk, int status) {
-  // scatter outputs back to the requests (pinned buffer -> request vectors)
-  if (status == FSMP_OK) {
-    size_t n_samp = 0, n_trace = 0;
-    int W = 0;
-    for (Request* r : pk->reqs) {
-      n_samp += r->samples.size();
-      W += r->W;
-      if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
+  (void)c;
+  for (int q = 0; q < (int)pk->reqs.size(); ++q) {
+    if (pk->returned[q]) continue;
+    if (status == FSMP_OK) {
+      finish_request(pk, q);
+    } else {
+      pk->reqs[q]->status = status;
+      pk->reqs[q]->t_done = now_s();
     }
-    PackLayout L = pack_layout(n_samp, W, n_trace);
-    const unsigned char* h = (const unsigned char*)pk->host;
-    const fsmp_summary* out = (const fsmp_summary*)(h + L.out);
-    const fsmp_trace* tr = (const fsmp_trace*)(h + L.trace);
-    size_t to = 0;
-    for (size_t q = 0; q < pk->reqs.size(); ++q) {
-      Request* r = pk->reqs[q];
-      r->out.assign(out + pk->first[q], out + pk->first[q] + r->W);
-      if (r->record_trace) {
-        r->trace.assign(tr + to, tr + to + (size_t)r->W * r->n_steps);
-        to += (size_t)r->W * r->n_steps;
-      }
-      r->t_done = pk->t_done;
-      r->status = FSMP_OK;
-    }
-  } else {
-    for (Request* r : pk->reqs) { r->status = status; r->t_done = now_s(); }
   }
   if (pk->host) cudaFreeHost(pk->host);
 }
@@ -549,7 +589,21 @@ void worker_main(fsmp_ctx* c) {
   cudaSetDevice(c->p.device);
   std::unique_lock<std::mutex> lk(c->mu);
   while (true) {
-    // completions
+    // requests whose own chains are done return at once, before the rest of their pack
+    for (Pack* pk : c->inflight) {
+      if (pk->returned.empty()) continue;  // not launched yet
+      const std::vector<int> ready = ready_requests(pk);
+      if (ready.empty()) continue;
+      lk.unlock();
+      for (int q : ready) finish_request(pk, q);
+      lk.lock();
+      for (int q : ready) {
+        pk->returned[q] = 1;
+        c->done.push_back(pk->reqs[q]);
+      }
+      c->cv_done.notify_all();
+    }
+    // completed packs: their memory frees
     for (size_t i = 0; i < c->inflight.size();) {
       Pack* pk = c->inflight[i];
       if (pk->done.load()) {
@@ -558,7 +612,8 @@ void worker_main(fsmp_ctx* c) {
         finish_pack(c, pk, FSMP_OK);
         lk.lock();
         c->mem_in_use -= pk->dev_bytes;
-        for (Request* r : pk->reqs) c->done.push_back(r);
+        for (size_t q = 0; q < pk->reqs.size(); ++q)
+          if (!pk->returned[q]) c->done.push_back(pk->reqs[q]);
         delete pk;
         c->cv_done.notify_all();
       } else {
@@ -597,6 +652,7 @@ void worker_main(fsmp_ctx* c) {
           c->mem_in_use -= bytes;
           lk.unlock();
           cudaStreamSynchronize(pk->stream < 0 ? c->gmem_stream : c->streams[pk->stream]);
+          pk->returned.assign(pk->reqs.size(), 0);
           finish_pack(c, pk, rc);
           lk.lock();
           for (Request* r : pk->reqs) c->done.push_back(r);

@@ -173,3 +173,30 @@ def test_drift_flag_under_a_tiny_tolerance(lib):
     assert np.mean((s["status"][refreshed] & fsmp.ST_DRIFT) != 0) > 0.9
     assert np.all((s["status"][~refreshed] & fsmp.ST_DRIFT) == 0)
     assert np.all((res[0.0]["status"] & fsmp.ST_DRIFT) == 0)
+
+
+def test_request_returns_when_its_own_chains_finish(lib):
+    """A light request packed into the same launch as a heavy one returns as soon as its own
+    chain is done (the kernels count finished chains per request in host-mapped memory and the
+    serving loop returns each request when its count is full), not when the launch ends; the
+    heavy one's result is unaffected."""
+    params = workloads.CONFIGS["serving_20k_eps"]["params"]
+    wl = workloads.make_workload("batched_uneven_100k", n_waveforms=400, seed=23)
+    b = wl["batch"]
+    heavy_i, light_i = int(np.argmax(b["lambda0"])), int(np.argmin(b["lambda0"]))
+    heavy = dict(workloads.subset(b, [heavy_i]), n_steps=20000, burn_in=0)
+    light = dict(workloads.subset(b, [light_i]), n_steps=20000, burn_in=0)
+    first = dict(workloads.subset(b, [light_i]), n_steps=3000, burn_in=0)
+    with fsmp.Context(_params(params, n_streams=1)) as ctx:
+        s_alone, _ = ctx.run(heavy, request_id=9)
+        # while `first` holds the only launch stream, the heavy and the light request queue up
+        # and are then packed into one launch
+        assert ctx.submit(first, request_id=0) == fsmp.OK
+        assert ctx.submit(heavy, request_id=1) == fsmp.OK
+        assert ctx.submit(light, request_id=2) == fsmp.OK
+        got = {r["request_id"]: r for r in _drain(ctx, 3)}
+    assert all(r["status"] == fsmp.OK for r in got.values())
+    lat_heavy, lat_light = got[1]["latency_s"], got[2]["latency_s"]
+    assert lat_light < 0.5 * lat_heavy, (lat_light, lat_heavy)
+    for f in FLOAT_FIELDS:
+        np.testing.assert_array_equal(got[1]["summaries"][f], s_alone[f], err_msg=f)
