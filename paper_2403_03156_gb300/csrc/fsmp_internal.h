@@ -92,20 +92,19 @@ struct BatchView {
   int z_stride;
   uint32_t* pe_hist;           // may be null: PE counts per grid point after burn-in
   int pe_hist_width;
-  // serving packs (may be null): the request of each waveform within the pack, and per request
-  // the number of its chains finished, in host-mapped memory that the serving loop polls
-  const int32_t* req_idx;
-  unsigned int* req_done;
+  // serving packs (may be null): per waveform a flag in host-mapped memory that the serving
+  // loop polls, set once the chain's summary (and trace) are written
+  unsigned int* wf_done;
 };
 
 #ifdef __CUDACC__
-// A chain's summary (and trace) are written: make them visible to the host, then count the
-// chain for its request, so that the serving loop can return the request as soon as its own
-// chains are done (the group's or block's writing thread calls it).
+// A chain's summary (and trace) are written: make them visible to the host, then raise the
+// chain's flag (a plain store, no host atomics needed), so that the serving loop can return a
+// request as soon as its own chains are done. The group's or block's writing thread calls it.
 __device__ __forceinline__ void note_chain_done(const BatchView& B, int wi) {
-  if (B.req_done != nullptr) {
+  if (B.wf_done != nullptr) {
     __threadfence_system();
-    atomicAdd_system(B.req_done + B.req_idx[wi], 1u);
+    *(volatile unsigned int*)(B.wf_done + wi) = 1u;
   }
 }
 #endif

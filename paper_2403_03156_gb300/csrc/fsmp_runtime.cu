@@ -75,9 +75,9 @@ struct Pack {
   std::atomic<int> done{0};
   double t_done = 0;
   struct fsmp_ctx* ctx = nullptr;
-  // per request: chains finished (host-mapped counters the kernels bump), and whether the
-  // serving loop has returned it
-  volatile unsigned int* req_done = nullptr;
+  // per waveform: the chain is done (host-mapped flags the kernels raise); per request: whether
+  // the serving loop has returned it
+  volatile unsigned int* wf_done = nullptr;
   std::vector<char> returned;
 };
 
@@ -309,7 +309,7 @@ int run_view(fsmp_ctx* c, BatchView B, cudaStream_t st, int set) {
         else b1.trace = B.trace + (size_t)i * B.n_steps;
       }
       b1.order = nullptr;
-      if (B.req_idx) b1.req_idx = B.req_idx + i;
+      if (B.wf_done) b1.wf_done = B.wf_done + i;
       cudaError_t e = launch_chains(c->M, b1, FSMP_KERNEL_GLOBAL, s, c->gscratch, c->gscratch_bytes, nullptr, 0, 0, st);
       c->n_launches++;
       if (e != cudaSuccess) { set_error("launch_chains", cudaGetErrorString(e), __LINE__); return FSMP_ERR_CUDA; }
@@ -378,12 +378,12 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct PackLayout {
   size_t samples, offsets, lambda0, t_origin, T_lo, T_hi, t0_init, wf_ids, seeds, nsteps, burnin,
-      trace_off, order, req_idx, in_end, out, trace, done, total;
+      trace_off, order, in_end, out, trace, done, total;
 };
 
-// Inputs (staged in pinned memory and copied to the device), then the outputs and the per-request
-// counters, which the kernels write straight into the pinned host block (host-mapped).
-PackLayout pack_layout(size_t n_samp, int W, size_t n_trace, int n_req = 0) {
+// Inputs (staged in pinned memory and copied to the device), then the outputs and the per-waveform
+// done flags, which the kernels write straight into the pinned host block (host-mapped).
+PackLayout pack_layout(size_t n_samp, int W, size_t n_trace) {
   PackLayout L;
   size_t o = 0;
   L.samples = o; o = align_up(o + n_samp * 4, 256);
@@ -399,11 +399,10 @@ PackLayout pack_layout(size_t n_samp, int W, size_t n_trace, int n_req = 0) {
   L.burnin = o; o = align_up(o + (size_t)W * 4, 256);
   L.trace_off = o; o = align_up(o + (size_t)W * 8, 256);
   L.order = o; o = align_up(o + (size_t)W * 4, 256);
-  L.req_idx = o; o = align_up(o + (size_t)W * 4, 256);
   L.in_end = o;
   L.out = o; o = align_up(o + (size_t)W * sizeof(fsmp_summary), 256);
   L.trace = o; o = align_up(o + n_trace * sizeof(fsmp_trace), 256);
-  L.done = o; o = align_up(o + (size_t)n_req * sizeof(unsigned int), 256);
+  L.done = o; o = align_up(o + (size_t)W * sizeof(unsigned int), 256);
   L.total = o;
   return L;
 }
@@ -411,7 +410,7 @@ PackLayout pack_layout(size_t n_samp, int W, size_t n_trace, int n_req = 0) {
 // Device memory a request holds while it runs: its inputs (outputs go to pinned host memory).
 size_t request_bytes(const Request* r) {
   size_t n_trace = r->record_trace ? (size_t)r->W * r->n_steps : 0;
-  return pack_layout(r->samples.size(), r->W, n_trace, 1).in_end;
+  return pack_layout(r->samples.size(), r->W, n_trace).in_end;
 }
 
 // Stage and launch one pack (called by the worker without the lock held).
@@ -426,7 +425,7 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
     n_max = std::max(n_max, r->n_max);
   }
   const int n_req = (int)pk->reqs.size();
-  PackLayout L = pack_layout(n_samp, W, n_trace, n_req);
+  PackLayout L = pack_layout(n_samp, W, n_trace);
   pk->dev_bytes = L.in_end;
   pk->host_bytes = L.total;
   pk->in_bytes = L.in_end;
@@ -447,13 +446,12 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   int32_t* burnin = (int32_t*)(h + L.burnin);
   int64_t* toff = (int64_t*)(h + L.trace_off);
   int32_t* order = (int32_t*)(h + L.order);
-  int32_t* req_idx = (int32_t*)(h + L.req_idx);
-  unsigned int* req_done = (unsigned int*)(h + L.done);
-  for (int q = 0; q < n_req; ++q) req_done[q] = 0;
-  pk->req_done = req_done;
+  unsigned int* wf_done = (unsigned int*)(h + L.done);
+  for (int i = 0; i < W; ++i) wf_done[i] = 0;
+  pk->wf_done = wf_done;
   pk->returned.assign(n_req, 0);
   size_t so = 0, to = 0;
-  int wi = 0, rq = 0;
+  int wi = 0;
   offsets[0] = 0;
   for (Request* r : pk->reqs) {
     memcpy(samples + so, r->samples.data(), r->samples.size() * 4);
@@ -471,10 +469,8 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
       burnin[wi] = r->burn_in;
       toff[wi] = r->record_trace ? (int64_t)to : -1;
       if (r->record_trace) to += (size_t)r->n_steps;
-      req_idx[wi] = rq;
     }
     so += r->samples.size();
-    ++rq;
   }
   // processing order: the PE-space kernel takes chains by decreasing expected cost, window
   // length x (1 + lambda0), so that the heaviest start first and the launch's tail is light;
@@ -526,8 +522,7 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   B.trace_off = n_trace ? (const int64_t*)(d + L.trace_off) : nullptr;
   B.out = (fsmp_summary*)(hd + L.out);
   B.trace = n_trace ? (fsmp_trace*)(hd + L.trace) : nullptr;
-  B.req_idx = (const int32_t*)(d + L.req_idx);
-  B.req_done = (unsigned int*)(hd + L.done);
+  B.wf_done = (unsigned int*)(hd + L.done);
   int rc = run_bucketed(c, B, (const int32_t*)(d + L.order), n_sorted, st,
                         pk->stream < 0 ? (int)c->streams.size() : pk->stream);
   if (rc) return rc;
@@ -545,7 +540,7 @@ void finish_request(Pack* pk, int q) {
     W += r->W;
     if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
   }
-  PackLayout L = pack_layout(n_samp, W, n_trace, (int)pk->reqs.size());
+  PackLayout L = pack_layout(n_samp, W, n_trace);
   const unsigned char* h = (const unsigned char*)pk->host;
   const fsmp_summary* out = (const fsmp_summary*)(h + L.out);
   const fsmp_trace* tr = (const fsmp_trace*)(h + L.trace);
@@ -559,13 +554,16 @@ void finish_request(Pack* pk, int q) {
   r->status = FSMP_OK;
 }
 
-// Requests of the in-flight pack whose chains have all finished (the kernels' counters in the
+// Requests of the in-flight pack whose chains have all finished (the kernels' flags in the
 // pinned block), not yet returned.
 std::vector<int> ready_requests(Pack* pk) {
   std::vector<int> ready;
   for (int q = 0; q < (int)pk->reqs.size(); ++q) {
     if (pk->returned[q]) continue;
-    if (pk->req_done[q] >= (unsigned int)pk->reqs[q]->W) ready.push_back(q);
+    const int w0 = pk->first[q], w1 = w0 + pk->reqs[q]->W;
+    int w = w0;
+    while (w < w1 && pk->wf_done[w]) ++w;
+    if (w == w1) ready.push_back(q);
   }
   if (!ready.empty()) std::atomic_thread_fence(std::memory_order_acquire);  // then read their outputs
   return ready;

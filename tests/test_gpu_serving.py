@@ -177,9 +177,9 @@ def test_drift_flag_under_a_tiny_tolerance(lib):
 
 def test_request_returns_when_its_own_chains_finish(lib):
     """A light request packed into the same launch as a heavy one returns as soon as its own
-    chain is done (the kernels count finished chains per request in host-mapped memory and the
-    serving loop returns each request when its count is full), not when the launch ends; the
-    heavy one's result is unaffected."""
+    chain is done (each chain raises a flag in host-mapped memory after writing its summary there,
+    and the serving loop returns a request once all its chains' flags are up), not when the
+    launch ends; the heavy one's result is unaffected."""
     params = workloads.CONFIGS["serving_20k_eps"]["params"]
     wl = workloads.make_workload("batched_uneven_100k", n_waveforms=400, seed=23)
     b = wl["batch"]
