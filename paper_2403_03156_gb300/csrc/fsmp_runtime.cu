@@ -79,6 +79,11 @@ struct Pack {
   // the serving loop has returned it
   volatile unsigned int* wf_done = nullptr;
   std::vector<char> returned;
+  // the pinned block's output regions and each request's first trace record, fixed at launch
+  // (a returned request may already be freed by fsmp_poll while its pack still runs, so nothing
+  // after the launch reads the other requests of the pack)
+  size_t out_region = 0, trace_region = 0;
+  std::vector<size_t> trace_first;
 };
 
 }  // namespace
@@ -426,6 +431,15 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
   }
   const int n_req = (int)pk->reqs.size();
   PackLayout L = pack_layout(n_samp, W, n_trace);
+  pk->out_region = L.out;
+  pk->trace_region = L.trace;
+  {
+    size_t tf = 0;
+    for (Request* r : pk->reqs) {
+      pk->trace_first.push_back(tf);
+      if (r->record_trace) tf += (size_t)r->W * r->n_steps;
+    }
+  }
   pk->dev_bytes = L.in_end;
   pk->host_bytes = L.total;
   pk->in_bytes = L.in_end;
@@ -533,20 +547,10 @@ int launch_pack(fsmp_ctx* c, Pack* pk) {
 
 // Copy request q's outputs out of the pack's pinned block into the request (its chains are done).
 void finish_request(Pack* pk, int q) {
-  size_t n_samp = 0, n_trace = 0;
-  int W = 0;
-  for (Request* r : pk->reqs) {
-    n_samp += r->samples.size();
-    W += r->W;
-    if (r->record_trace) n_trace += (size_t)r->W * r->n_steps;
-  }
-  PackLayout L = pack_layout(n_samp, W, n_trace);
   const unsigned char* h = (const unsigned char*)pk->host;
-  const fsmp_summary* out = (const fsmp_summary*)(h + L.out);
-  const fsmp_trace* tr = (const fsmp_trace*)(h + L.trace);
-  size_t to = 0;
-  for (int i = 0; i < q; ++i)
-    if (pk->reqs[i]->record_trace) to += (size_t)pk->reqs[i]->W * pk->reqs[i]->n_steps;
+  const fsmp_summary* out = (const fsmp_summary*)(h + pk->out_region);
+  const fsmp_trace* tr = (const fsmp_trace*)(h + pk->trace_region);
+  const size_t to = pk->trace_first[q];
   Request* r = pk->reqs[q];
   r->out.assign(out + pk->first[q], out + pk->first[q] + r->W);
   if (r->record_trace) r->trace.assign(tr + to, tr + to + (size_t)r->W * r->n_steps);
