@@ -308,6 +308,25 @@ static int draw_comp(const orc_params* p, double u) {
 }
 
 /* a[w] = V(w*dt - t_j) on the grid (reading R1): V[w*R - j] inside the table, else 0. */
+/* Samples of the window [0, n) in the support of a PE at grid index j (w R - j in [0, Lt)). */
+static int support_count(const model* M, int n, int j) {
+  int c = 0;
+  for (int w = 0; w < n; ++w) {
+    const int m = w * M->R - j;
+    c += (m >= 0 && m < M->Lt);
+  }
+  return c;
+}
+
+/* Whether PEs at grid indices i and j share a sample of the window. */
+static int supports_overlap(const model* M, int n, int i, int j) {
+  for (int w = 0; w < n; ++w) {
+    const int mi = w * M->R - i, mj = w * M->R - j;
+    if (mi >= 0 && mi < M->Lt && mj >= 0 && mj < M->Lt) return 1;
+  }
+  return 0;
+}
+
 static void pe_vector(const model* M, int n, int j, double* a) {
   for (int w = 0; w < n; ++w) {
     int m = w * M->R - j;
@@ -702,6 +721,18 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
       }
     }
 
+    /* the words the method moves to score this proposal (orc_summary.alg_words) */
+    int np_w = 0, sp_len = 0, sm_len = 0;
+    if (valid && jump != ORC_JUMP_DEATH) {
+      sp_len = support_count(M, n, jp);
+      for (int q = 0; q < N; ++q) np_w += supports_overlap(M, n, list[q], jp);
+      out->alg_words += N + 2.0 * np_w + 2.0 * sp_len + (double)np_w * np_w + np_w;
+    }
+    if (valid && jump != ORC_JUMP_BIRTH) {
+      sm_len = support_count(M, n, list[k]);
+      out->alg_words += 2.0;
+    }
+
     double logp_new = 0.0;
     if (valid) {
       int ok = 1;
@@ -753,6 +784,12 @@ static int run_chain(const chain_in* c, orc_summary* out, orc_trace* trace, int3
         tr.flags |= ORC_F_NOOP;
       } else {
         out->acc[jump]++;
+        {
+          const double Nout = N + (jump == ORC_JUMP_BIRTH ? 1 : (jump == ORC_JUMP_DEATH ? -1 : 0));
+          out->alg_words += (double)N * np_w + Nout * (Nout + 1.0) + 2.0 * Nout;
+          if (jump != ORC_JUMP_BIRTH) out->alg_words += 2.0 * sm_len + N;
+          if (jump != ORC_JUMP_DEATH) out->alg_words += 2.0 * sp_len;
+        }
         if (c->mode == ORC_MODE_INCREMENTAL && !p->prior_only) inc_accept(&st, p);
         if (c->mode == ORC_MODE_DEFINITION) logp_cur = logp_new;
         if (jump == ORC_JUMP_BIRTH) { list[N] = jp; list_e[N] = ep; N++; }

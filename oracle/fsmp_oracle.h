@@ -86,6 +86,13 @@ typedef struct {
   /* mean and population variance over the samples of the Wasserstein scalars of {t_i} and
    * {e_i} (orc_pe_wasserstein; the convergence check of Sec. 3.2) */
   double mean_wt, var_wt, mean_we, var_we;
+  /* Words of chain state the method moves, counted from the chain's own path for the roofline's
+   * algorithmic bytes (a measurement count, not part of the chain's arithmetic): per scored
+   * birth or update N + 2p + 2|S+| + p^2 + p (p = PEs whose samples in the window overlap the new
+   * PE's, |S+| its samples in the window), per scored death or update 2 more, per accepted move
+   * N p + N'(N' + 1) + 2N' (N' = N after it), plus 2|S-| + N when a PE leaves and 2|S+| when one
+   * arrives (|S-| the leaving PE's samples in the window). */
+  double alg_words;
 } orc_summary;
 
 /* 1-Wasserstein distance between the empirical distributions (equal weights) of a[0..na) and

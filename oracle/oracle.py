@@ -39,7 +39,7 @@ SUMMARY_DTYPE = np.dtype([("mean_N", "<f8"), ("var_N", "<f8"), ("mean_t0", "<f8"
                           ("prop", "<i4", (3,)), ("acc_t0", "<i4"), ("prop_t0", "<i4"),
                           ("N_final", "<i4"), ("k0_final", "<i4"), ("status", "<i4"),
                           ("n_samples", "<i4"), ("lambda_hat", "<f8"), ("mean_wt", "<f8"),
-                          ("var_wt", "<f8"), ("mean_we", "<f8"), ("var_we", "<f8")])
+                          ("var_wt", "<f8"), ("mean_we", "<f8"), ("var_we", "<f8"), ("alg_words", "<f8")])
 
 
 class OrcParams(ctypes.Structure):

@@ -74,7 +74,7 @@ def _lucy_state(orc, params, b, cap):
     return dict(T_lo=T_lo, T_hi=T_hi, t0_init=t0, z_init=z, n_init=nz, z_stride=cap)
 
 
-def _assert_summaries(s_gpu, s_orc, lam=True):
+def _assert_summaries(s_gpu, s_orc, lam=True, words=False):
     for f in ("mean_N", "mean_t0"):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-12, atol=1e-12, err_msg=f)
     # the variances come from the same exact integer sums as E[x^2] - E[x]^2, which cancels by
@@ -85,6 +85,8 @@ def _assert_summaries(s_gpu, s_orc, lam=True):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9, err_msg=f)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f], err_msg=f)
+    if words:  # the PE-space kernel's algorithmic bytes against the oracle's count of its words
+        np.testing.assert_array_equal(s_gpu["alg_bytes"], 8.0 * s_orc["alg_words"])
 
 
 # ------------------------------------------------------------------ 0.2 ns grid (R = 5)
@@ -103,7 +105,7 @@ def test_lockstep_fp64_lowocc_grid_0p2ns(lib, orc, kernel, lanes):
         s_gpu, t_gpu = ctx.run(b, record_trace=True)
     s_orc, t_orc = orc.run_batch(params, b, orc.MODE_INCREMENTAL, n_threads=16, trace=True)
     gpu_util.compare_traces(t_gpu, t_orc)
-    _assert_summaries(s_gpu, s_orc)
+    _assert_summaries(s_gpu, s_orc, words=kernel == fsmp.KERNEL_PE)
     assert s_gpu["acc"].sum() > 1000 and t_gpu["N"].max() >= 4
 
 
@@ -138,7 +140,7 @@ def test_lockstep_fp64_highpileup(lib, orc):
     s_gpu, t_gpu = _results(t, W)
     s_orc, t_orc = orc.run_batch(params, b, orc.MODE_DEFINITION, n_threads=16, trace=True)
     gpu_util.compare_traces(t_gpu, t_orc)
-    _assert_summaries(s_gpu, s_orc)
+    _assert_summaries(s_gpu, s_orc, words=True)
     assert t_gpu["N"].max() >= 60 and s_gpu["acc"].sum() >= 100
 
 

@@ -72,6 +72,10 @@ def test_lockstep_fp64_config1(lib, orc, kernel, lanes):
         np.testing.assert_allclose(s_gpu[f], s_orc[f], rtol=1e-9, atol=1e-9)
     for f in ("acc", "prop", "acc_t0", "prop_t0", "N_final", "k0_final", "status"):
         np.testing.assert_array_equal(s_gpu[f], s_orc[f])
+    if kernel == fsmp.KERNEL_PE:
+        # the roofline's algorithmic bytes: the kernel's own count equals the oracle's count of
+        # the same words along the same path (8-byte words)
+        np.testing.assert_array_equal(s_gpu["alg_bytes"], 8.0 * s_orc["alg_words"])
 
 
 def test_gelman_rubin_of_gpu_chains_matches_oracle(lib, orc):
