@@ -614,6 +614,18 @@ def run_ours(args):
     if prec == fsmp.FP64:
         fp64 = peaks["fp64_tflops"]
         roofline["note"] = "FP64 mode is FP64-FMA bound on this part (measured %.2f TFLOP/s FP64)" % fp64
+    if tr is not None and tr.get("warp_inst_per_step"):
+        # the binding roofline of a latency-bound chain: instruction issue. Warp instructions per
+        # MCMC step from the committed ncu capture of the same kernel source (smsp__inst_executed
+        # / steps), times the launch's steps per second, against 4 issue slots per SM per clock at
+        # the SM clock sampled during the timed region
+        steps_launch = float(summ[kdom]["prop"].sum())
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        ach = tr["warp_inst_per_step"] * steps_launch / (mean_dur[kdom] * 1e-3)
+        pk_issue = info["sm_count"] * 4 * mhz * 1e6
+        roofline["issue"] = {"achieved": ach, "peak": pk_issue, "unit": "warp instructions/s", "frac": ach / pk_issue,
+                             "warp_inst_per_step": tr["warp_inst_per_step"],
+                             "source": "instructions per step: " + tr.get("command", "ncu capture")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
