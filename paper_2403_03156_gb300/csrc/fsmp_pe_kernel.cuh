@@ -1051,6 +1051,23 @@ __device__ __noinline__ void pe_draw(const DevModel& M, PeRand<T>* rnd, uint64_t
   __syncwarp(ln.gm);
 }
 
+// Out-of-line pieces of the step that run only when the caller asked for them (a trace record,
+// the PE-time histogram), so that their code stays out of the step loop's instruction stream.
+__device__ __noinline__ void pe_trace_record(fsmp_trace* t, double la0, double lu0, double la, double lu, double dnu,
+                                             int N, int k0, int jump, int flags) {
+  fsmp_trace tr;
+  tr.la0 = la0; tr.lu0 = lu0; tr.la = la; tr.lu = lu; tr.dnu = dnu;
+  tr.N = N; tr.k0 = k0; tr.jump = jump; tr.flags = flags;
+  *t = tr;
+}
+template <int L>
+__device__ __noinline__ void pe_hist_add(uint32_t* peh, const int* list, int N, int T_lo, int width, const Lanes<L> ln) {
+  for (int k = ln.sl; k < N; k += L) {
+    const int c = list[k] - T_lo;
+    if (c >= 0 && c < width) atomicAdd(peh + c, 1u);
+  }
+}
+
 template <typename T, bool BIG, int L, bool MIX>
 __global__ void __launch_bounds__(kPeMaxThreads, 4)
     pe_kernel(const __grid_constant__ DevModel M, const __grid_constant__ BatchView B, const __grid_constant__ PeSlots G) {
@@ -1522,20 +1539,10 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           S.sN += Nn; S.sN2 += Nn * Nn; S.sK += kq; S.sK2 += kq * kq;
           atomicAdd(hist + N, 1);  // no value returned: the lane does not wait on it
         }
-        if (trace) {
-          fsmp_trace tr;
-          tr.la0 = (double)la0; tr.lu0 = (double)lu0; tr.la = (double)la; tr.lu = (double)lu;
-          tr.dnu = (double)dnu; tr.N = N; tr.k0 = k0; tr.jump = jump;
-          tr.flags = t0f | (acc ? 4 : 0) | ((acc && noop) ? 8 : 0);
-          trace[step] = tr;
-        }
+        if (trace) pe_trace_record(trace + step, (double)la0, (double)lu0, (double)la, (double)lu, (double)dnu, N, k0, jump,
+                                   t0f | (acc ? 4 : 0) | ((acc && noop) ? 8 : 0));
       }
-      if (peh && step >= burn_in) {  // PE-time histogram: one count per PE and step
-        for (int k = ln.sl; k < N; k += L) {
-          const int c = W.list[k] - T_lo;
-          if (c >= 0 && c < B.pe_hist_width) atomicAdd(peh + c, 1u);
-        }
-      }
+      if (peh && step >= burn_in) pe_hist_add<L>(peh, W.list, N, T_lo, B.pe_hist_width, ln);
       __syncwarp(ln.gm);
     }
 
