@@ -544,6 +544,11 @@ struct RefreshOut {
   double logdet, logL, drift;
 };
 
+// Hint that the line holding p (global memory) will be read soon: fetched into L1, no register.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L1 [ga];\n\t}" ::"l"(p));
+}
+
 // FP64 rebuild of C^-1, v, y, log|Sigma| and the log-likelihood from the PE list (FP32 mode).
 // ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
 // value (no address of the caller's locals escapes, so they stay in registers).
@@ -598,8 +603,22 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
 #pragma unroll 1
   for (int k = ln.sl; k < N; k += L) {
     const Sup s = pe_sup(M, n, W.list[k]);
+    // the loops' loads go four at a time ahead of their (unchanged) sums
     double a0 = 0.0, a1 = 0.0;
     int i = s.ilo;
+#pragma unroll 1
+    for (; i + 3 < s.ihi; i += 4) {
+      double vv[4], ww[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        vv[u] = V[s.ph + (i + u) * M.R];
+        ww[u] = (double)w[s.w0 + i + u];
+      }
+      a0 = fma(vv[0], ww[0], a0);
+      a1 = fma(vv[1], ww[1], a1);
+      a0 = fma(vv[2], ww[2], a0);
+      a1 = fma(vv[3], ww[3], a1);
+    }
 #pragma unroll 1
     for (; i + 1 < s.ihi; i += 2) {
       a0 = fma(V[s.ph + i * M.R], (double)w[s.w0 + i], a0);
@@ -607,20 +626,40 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
     }
     if (i < s.ihi) a0 = fma(V[s.ph + i * M.R], (double)w[s.w0 + i], a0);
     const double aw = a0 + a1;
+    auto c_kj = [&](int j) { return *(j <= k ? A + (size_t)k * ws_ld + j : A + (size_t)j * ws_ld + k); };
+    int j = 0;
     if (mix) {
       const int ek = W.le[k];
       const double mk = M.cm_mu[ek];
       double hs = -M.cm_r[ek] * mk;  // (A^T A m)_k = sum_j C_kj m_j - r_k m_k
 #pragma unroll 1
-      for (int j = 0; j < N; ++j)
-        hs = fma(*(j <= k ? A + (size_t)k * ws_ld + j : A + (size_t)j * ws_ld + k), M.cm_mu[W.le[j]], hs);
+      for (; j + 3 < N; j += 4) {
+        double cc[4], mm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cc[u] = c_kj(j + u);
+          mm[u] = M.cm_mu[W.le[j + u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) hs = fma(cc[u], mm[u], hs);
+      }
+#pragma unroll 1
+      for (; j < N; ++j) hs = fma(c_kj(j), M.cm_mu[W.le[j]], hs);
       h[k] = aw - hs;
       awt = fma(mk, aw, awt);
       rst = fma(mk, hs, rst);
     } else {
       double rs = -r;
 #pragma unroll 1
-      for (int j = 0; j < N; ++j) rs += *(j <= k ? A + (size_t)k * ws_ld + j : A + (size_t)j * ws_ld + k);
+      for (; j + 3 < N; j += 4) {
+        double cc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cc[u] = c_kj(j + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rs += cc[u];
+      }
+#pragma unroll 1
+      for (; j < N; ++j) rs += c_kj(j);
       h[k] = aw - mu * rs;
       awt += aw;
       rst += rs;
@@ -629,16 +668,35 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   awt = wsum(awt, ln);
   rst = wsum(rst, ln);
   const double yy = mix ? wsq - 2.0 * awt + rst : wsq - 2.0 * mu * awt + mu * mu * rst;
-  // the FP32 residual, each sample summed in FP64 over the PEs that cover it
+  // the FP32 residual, each sample summed in FP64 over the PEs that cover it, in list order: PE
+  // by PE with lanes over its support samples, into an FP64 copy of the window held in the
+  // sweep's panel buffers (free until the sweep); sample by sample where the window does not fit
+  if (n <= 2 * kSweepBlock * (int)lv) {
+    double* yd = P;  // P and Pn are contiguous
 #pragma unroll 1
-  for (int x = ln.sl; x < n; x += L) {
-    double yv = (double)w[x];
+    for (int x = ln.sl; x < n; x += L) yd[x] = (double)w[x];
+    __syncwarp(ln.gm);
 #pragma unroll 1
     for (int k = 0; k < N; ++k) {
-      const int idx = x * M.R - W.list[k];
-      if (idx >= 0 && idx < M.Lt) yv = fma(mix ? -M.cm_mu[W.le[k]] : -mu, V[idx], yv);
+      const Sup s = pe_sup(M, n, W.list[k]);
+      const double mk = mix ? -M.cm_mu[W.le[k]] : -mu;
+#pragma unroll 1
+      for (int i = s.ilo + ln.sl; i < s.ihi; i += L) yd[s.w0 + i] = fma(mk, V[s.ph + i * M.R], yd[s.w0 + i]);
+      __syncwarp(ln.gm);
     }
-    W.y[x] = (T)yv;
+#pragma unroll 1
+    for (int x = ln.sl; x < n; x += L) W.y[x] = (T)yd[x];
+  } else {
+#pragma unroll 1
+    for (int x = ln.sl; x < n; x += L) {
+      double yv = (double)w[x];
+#pragma unroll 1
+      for (int k = 0; k < N; ++k) {
+        const int idx = x * M.R - W.list[k];
+        if (idx >= 0 && idx < M.Lt) yv = fma(mix ? -M.cm_mu[W.le[k]] : -mu, V[idx], yv);
+      }
+      W.y[x] = (T)yv;
+    }
   }
   __syncwarp(ln.gm);
   // Inversion by the symmetric sweep operator (Gauss-Jordan with diagonal pivots, kept
@@ -649,103 +707,124 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   // over the matrix per block K = [k0, k1): the block's rows A_K. (the panel) are swept first --
   // they change only through their own entries -- then every other entry (i, j), i, j outside K,
   // takes the rank-SB update A_ij -= sum_q P_iq G_qj, with P_i. = A_Ki before the sweep and
-  // G_.j = A_Kj after it. The panel is swept in a staged copy: Pn_j. = A_Kj for j outside K, Kb
-  // = A_KK in full.
+  // G_.j = A_Kj after it. Within the panel, the diagonal block A_KK depends on nothing else, so
+  // it is swept first and its pivots and factors recorded; each other column A_Kj then takes
+  // them in turn (the same operations in the same order as sweeping the panel pivot by pivot).
   double pm = 1.0;
   int pe = 0;
+  double* F = Kb;  // the block's pivot factors: F[q SB + r] = A_rp / pivot (r != q), F[q SB + q] = 1 / pivot
 #pragma unroll 1
   for (int k0 = 0; k0 < N; k0 += SB) {
     const int nb = min(SB, N - k0), k1 = k0 + nb;
-#pragma unroll 1
-    for (int i = ln.sl; i < N; i += L) {
-      if (i >= k0 && i < k1) {
-        const int r = i - k0;
+    // the diagonal block A_KK swept on its own, lane r holding its row r in full; each pivot's
+    // row goes to the other lanes by shuffles
+    const int rl = ln.sl;
+    double kr[SB];
+#pragma unroll
+    for (int c = 0; c < SB; ++c)
+      kr[c] = (rl < nb && c < nb)
+                  ? *(c <= rl ? A + (size_t)(k0 + rl) * ws_ld + k0 + c : A + (size_t)(k0 + c) * ws_ld + k0 + rl)
+                  : 0.0;
+#pragma unroll
+    for (int q = 0; q < SB; ++q) {
+      if (q < nb) {
+        const double piv = __shfl_sync(ln.gm, kr[q], q, L);
+        if (!(piv > 0.0) || !isfinite(piv)) return out;
+        const double ip = 1.0 / piv;
+        int ex;
+        pm *= frexp(piv, &ex);
+        pe += ex;
+        pm = frexp(pm, &ex);
+        pe += ex;
+        const double fr = kr[q] * ip;  // A_rp / pivot for this lane's row r
+        double aq[SB];
+#pragma unroll
+        for (int c = 0; c < SB; ++c) aq[c] = __shfl_sync(ln.gm, kr[c], q, L);
 #pragma unroll
         for (int c = 0; c < SB; ++c)
-          Kb[r * SB + c] = c < nb ? *(c <= r ? A + (size_t)i * ws_ld + k0 + c : A + (size_t)(k0 + c) * ws_ld + i) : 0.0;
-      } else {
-#pragma unroll
-        for (int q = 0; q < SB; ++q) {
-          const double a = q < nb ? *(i > k0 ? A + (size_t)i * ws_ld + k0 + q : A + (size_t)(k0 + q) * ws_ld + i) : 0.0;
-          P[(size_t)i * SB + q] = a;
-          Pn[(size_t)i * SB + q] = a;
-        }
+          kr[c] = (rl == q) ? (c == q ? -ip : aq[c] * ip) : (c == q ? fr : fma(-fr, aq[c], kr[c]));
+        if (rl < nb) F[q * SB + rl] = (rl == q) ? ip : fr;
       }
+    }
+    if (rl < nb) {
+#pragma unroll
+      for (int c = 0; c < SB; ++c)
+        if (c <= rl) A[(size_t)(k0 + rl) * ws_ld + k0 + c] = kr[c];
     }
     __syncwarp(ln.gm);
-#pragma unroll 1
-    for (int q = 0; q < nb; ++q) {
-      const int p = k0 + q;
-      const double piv = Kb[q * SB + q];
-      if (!(piv > 0.0) || !isfinite(piv)) return out;
-      const double ip = 1.0 / piv;
-      int ex;
-      pm *= frexp(piv, &ex);
-      pe += ex;
-      pm = frexp(pm, &ex);
-      pe += ex;
-      double f[SB];  // A_rp / pivot for the block's rows r
-#pragma unroll
-      for (int r = 0; r < SB; ++r) f[r] = r < nb ? Kb[r * SB + q] * ip : 0.0;
-      __syncwarp(ln.gm);
-#pragma unroll 1
-      for (int j = ln.sl; j < N; j += L) {
-        const bool inK = j >= k0 && j < k1;
-        double* b = inK ? Kb + (j - k0) : Pn + (size_t)j * SB;
-        const int st = inK ? SB : 1;
-        const double apj = b[q * st];
-#pragma unroll
-        for (int r = 0; r < SB; ++r) {
-          if (r < nb) {
-            double* x = b + r * st;
-            *x = (r == q) ? ((j == p) ? -ip : apj * ip) : ((j == p) ? f[r] : fma(-f[r], apj, *x));
-          }
-        }
-      }
-      __syncwarp(ln.gm);
-    }
-    // the swept panel back into the matrix, and the entries outside the block's rows and
-    // columns, RG rows at a time so that their loads overlap
+    // the panel A_Kj of every column j outside the block: P_j. keeps it as it was, then the
+    // block's pivots are applied to it in registers and it goes to Pn_j. and back into A
 #pragma unroll 1
     for (int j = ln.sl; j < N; j += L) {
       if (j >= k0 && j < k1) continue;
-      double g[SB];
-#pragma unroll
-      for (int q = 0; q < SB; ++q) g[q] = Pn[(size_t)j * SB + q];
+      double b[SB];
 #pragma unroll
       for (int q = 0; q < SB; ++q)
-        if (q < nb) *(j < k0 ? A + (size_t)(k0 + q) * ws_ld + j : A + (size_t)j * ws_ld + k0 + q) = g[q];
-      int i = j, hi = j < k0 ? k0 : N;
-#pragma unroll 1
-      for (int part = 0; part < 2; ++part) {
-#pragma unroll 1
-        for (; i < hi; i += RG) {
-          double x[RG];
+        b[q] = q < nb ? *(j > k0 ? A + (size_t)j * ws_ld + k0 + q : A + (size_t)(k0 + q) * ws_ld + j) : 0.0;
 #pragma unroll
-          for (int t = 0; t < RG; ++t) x[t] = A[(size_t)min(i + t, hi - 1) * ws_ld + j];
+      for (int q = 0; q < SB; ++q) P[(size_t)j * SB + q] = b[q];
 #pragma unroll
-          for (int t = 0; t < RG; ++t) {
-            const double2* Pi = reinterpret_cast<const double2*>(P + (size_t)min(i + t, hi - 1) * SB);
+      for (int q = 0; q < SB; ++q) {
+        if (q < nb) {
+          const double apj = b[q];
 #pragma unroll
-            for (int q = 0; q < SB / 2; ++q) {
-              const double2 pq = Pi[q];
-              x[t] = fma(-pq.x, g[2 * q], x[t]);
-              x[t] = fma(-pq.y, g[2 * q + 1], x[t]);
-            }
-          }
-#pragma unroll
-          for (int t = 0; t < RG; ++t)
-            if (i + t < hi) A[(size_t)(i + t) * ws_ld + j] = x[t];
+          for (int r = 0; r < SB; ++r)
+            if (r < nb) b[r] = (r == q) ? apj * F[q * SB + q] : fma(-F[q * SB + r], apj, b[r]);
         }
-        if (j >= k0) break;
-        i = k1;
-        hi = N;
+      }
+#pragma unroll
+      for (int q = 0; q < SB; ++q) {
+        Pn[(size_t)j * SB + q] = b[q];
+        if (q < nb) *(j < k0 ? A + (size_t)(k0 + q) * ws_ld + j : A + (size_t)j * ws_ld + k0 + q) = b[q];
       }
     }
+    __syncwarp(ln.gm);
+    // every entry (i, j), i >= j, outside the block's rows and columns: lanes over a group of L
+    // columns, the rows in step across the lanes (a row's loads coalesce and its P row is one
+    // broadcast), RG rows at a time so that their loads overlap
 #pragma unroll 1
-    for (int e = ln.sl; e < nb * nb; e += L) {
-      const int r = e / nb, c = e - r * nb;
-      if (c <= r) A[(size_t)(k0 + r) * ws_ld + k0 + c] = Kb[r * SB + c];
+    for (int j0 = 0; j0 < N; j0 += L) {
+      const int j = j0 + ln.sl;
+      const bool jv = j < N && (j < k0 || j >= k1);
+      double g[SB];
+#pragma unroll
+      for (int q = 0; q < SB; ++q) g[q] = jv ? Pn[(size_t)j * SB + q] : 0.0;
+      // the column group's rows: [j0, k0) above the block, then [max(j0, k1), N) below it; the
+      // next RG rows' entries are loaded while the current ones are updated
+      const int nA = max(0, k0 - j0), s2 = max(j0, k1), nr = nA + max(0, N - s2);
+      auto row = [&](int t) { return t < nA ? j0 + t : s2 + (t - nA); };
+      double xn[RG];
+#pragma unroll
+      for (int t = 0; t < RG; ++t) {
+        const int r = row(t);
+        xn[t] = (jv && t < nr && r >= j) ? A[(size_t)r * ws_ld + j] : 0.0;
+      }
+#pragma unroll 1
+      for (int t0 = 0; t0 < nr; t0 += RG) {
+        if (BIG && ln.sl < RG && t0 + 2 * RG + ln.sl < nr) prefetch_l1(P + (size_t)row(t0 + 2 * RG + ln.sl) * SB);
+        double x[RG];
+        int rr[RG];
+#pragma unroll
+        for (int t = 0; t < RG; ++t) {
+          x[t] = xn[t];
+          rr[t] = row(min(t0 + t, nr - 1));
+          const int tt = t0 + RG + t, r = row(tt);
+          xn[t] = (jv && tt < nr && r >= j) ? A[(size_t)r * ws_ld + j] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < RG; ++t) {
+          const double2* Pi = reinterpret_cast<const double2*>(P + (size_t)rr[t] * SB);
+#pragma unroll
+          for (int q = 0; q < SB / 2; ++q) {
+            const double2 pq = Pi[q];
+            x[t] = fma(-pq.x, g[2 * q], x[t]);
+            x[t] = fma(-pq.y, g[2 * q + 1], x[t]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < RG; ++t)
+          if (jv && t0 + t < nr && rr[t] >= j) A[(size_t)rr[t] * ws_ld + j] = x[t];
+      }
     }
     __syncwarp(ln.gm);
   }
@@ -775,14 +854,31 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   hv = wsum(hv, ln);
   // drift of the incremental state, then the refreshed state (packed lower triangle)
   double dmax = 0.0, amax = 0.0;
+  constexpr int RD = BIG ? 4 : 1;  // entries per lane at a time, their loads ahead of their stores
+  const int nt = tri(N);
 #pragma unroll 1
-  for (int e = ln.sl; e < tri(N); e += L) {
-    int i, j;
-    untri(e, i, j);
-    const double nv = -A[(size_t)i * ws_ld + j];
-    dmax = fmax(dmax, fabs(nv - c64(Cp[e])));
-    amax = fmax(amax, fabs(nv));
-    Cp[e] = cfrom64<C>(nv);
+  for (int e0 = ln.sl; e0 < nt; e0 += RD * L) {
+    double nv[RD], ov[RD];
+#pragma unroll
+    for (int u = 0; u < RD; ++u) {
+      const int e = e0 + u * L;
+      nv[u] = ov[u] = 0.0;
+      if (e < nt) {
+        int i, j;
+        untri(e, i, j);
+        nv[u] = -A[(size_t)i * ws_ld + j];
+        ov[u] = c64(Cp[e]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RD; ++u) {
+      const int e = e0 + u * L;
+      if (e < nt) {
+        dmax = fmax(dmax, fabs(nv[u] - ov[u]));
+        amax = fmax(amax, fabs(nv[u]));
+        Cp[e] = cfrom64<C>(nv[u]);
+      }
+    }
   }
   double vd = 0.0, va = 0.0;
 #pragma unroll 1
