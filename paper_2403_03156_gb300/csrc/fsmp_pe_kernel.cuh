@@ -293,25 +293,34 @@ __device__ __forceinline__ void untri(int e, int& i, int& j) {
   j = e - tri(i);
 }
 
-// sum_a C^-1[q][idx[a]] b[a] over a < m (skipping idx[a] == skip); BIG: four independent
-// partial sums so that the gathers of consecutive terms overlap
+// sum_a C^-1[q][idx[a]] b[a] over a < m (skipping idx[a] == skip); BIG (C^-1 in global memory):
+// four independent partial sums so that the gathers of consecutive terms overlap
 template <typename C, bool BIG>
 __device__ __forceinline__ C dot_row(const C* __restrict__ Cp, int q, const int* __restrict__ idx,
                                      const C* __restrict__ b, int m, int skip) {
   C s0 = czero<C>();
   int a = 0;
   if constexpr (BIG) {
-    C s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
+    constexpr int G = 4;
+    C sp[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) sp[u] = czero<C>();
 #pragma unroll 1
-    for (; a + 3 < m; a += 4) {
-      const int i0 = idx[a], i1 = idx[a + 1], i2 = idx[a + 2], i3 = idx[a + 3];
-      const C r0 = Cp[pk(q, i0)], r1 = Cp[pk(q, i1)], r2 = Cp[pk(q, i2)], r3 = Cp[pk(q, i3)];
-      if (i0 != skip) s0 = cfma(r0, b[a], s0);
-      if (i1 != skip) s1 = cfma(r1, b[a + 1], s1);
-      if (i2 != skip) s2 = cfma(r2, b[a + 2], s2);
-      if (i3 != skip) s3 = cfma(r3, b[a + 3], s3);
+    for (; a + G - 1 < m; a += G) {
+      int ix[G];
+      C r[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        ix[u] = idx[a + u];
+        r[u] = Cp[pk(q, ix[u])];
+      }
+#pragma unroll
+      for (int u = 0; u < G; ++u)
+        if (ix[u] != skip) sp[u] = cfma(r[u], b[a + u], sp[u]);
     }
-    s0 = cadd(cadd(s0, s1), cadd(s2, s3));
+#pragma unroll
+    for (int u = 1; u < G; ++u) sp[0] = cadd(sp[0], sp[u]);
+    s0 = sp[0];
   }
 #pragma unroll 1
   for (; a < m; ++a)
@@ -1507,8 +1516,29 @@ __global__ void __launch_bounds__(kPeMaxThreads, 4)
           C qp = czero<C>(), ck = czero<C>();
           T bvp = (T)0;
           const int nt = tri(np);
+          int e = ln.sl;
+          if constexpr (BIG) {  // C^-1 in the global slot: four entries' loads ahead of their sums
 #pragma unroll 1
-          for (int e = ln.sl; e < nt; e += L) {
+            for (; e + 3 * L < nt; e += 4 * L) {
+              C cq[4], bb[4];
+              bool dg[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                int a, b2;
+                untri(e + u * L, a, b2);
+                cq[u] = Cp[pk(W.ovi[a], W.ovi[b2])];
+                bb[u] = cmul(W.ovb[a], W.ovb[b2]);
+                dg[u] = a == b2;
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const C t = cmul(cq[u], bb[u]);
+                qp = cadd(qp, dg[u] ? t : ctwice(t));
+              }
+            }
+          }
+#pragma unroll 1
+          for (; e < nt; e += L) {
             int a, b2;
             untri(e, a, b2);
             const C t = cmul(Cp[pk(W.ovi[a], W.ovi[b2])], cmul(W.ovb[a], W.ovb[b2]));
