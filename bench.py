@@ -299,16 +299,19 @@ def device_batches(torch, wl, dev, n_smem_max, one_launch=False):
     return subs
 
 
-def load_traffic(kernel_src, name):
-    """DRAM traffic per launch of a chain kernel from the committed ncu summary
-    profiles/<name>_dram_traffic.json, if it was taken on the current kernel source; else None."""
+def load_traffic(kernel_src, name, workload):
+    """DRAM traffic and instructions per launch of a chain kernel on a workload, from the committed
+    ncu summary profiles/<name>_dram_traffic.json, if it was taken on the current kernel source
+    and on that workload; else None."""
     path = os.path.join(ROOT, "profiles", name + "_dram_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    return d if d.get("kernel_sha") == sha else None
+    if d.get("kernel_sha") != sha:
+        return None
+    return d.get("workloads", {}).get(workload)
 
 
 def plain_fp64_baseline(torch, wl, dev, n_sample, sample_seed=3):
@@ -597,7 +600,7 @@ def run_ours(args):
     alg_bytes = float(summ[kdom]["alg_bytes"].sum())
     achieved = alg_bytes / (mean_dur[kdom] * 1e-3) / 1e9
     kernel_src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_pe_kernel.cuh" if pe else "fsmp_chain.cu")
-    tr = load_traffic(kernel_src, "pe_kernel" if pe else "chain_kernel")
+    tr = load_traffic(kernel_src, "pe_kernel" if pe else "chain_kernel", args.workload)
     allsum = np.concatenate(summ)
     acc = allsum["acc"].sum(0)
     prop = allsum["prop"].sum(0)
