@@ -508,8 +508,9 @@ struct PeSlots {
 };
 
 // FP64 refresh workspace of one chain: C (n_cap x n_cap), h and v (n_cap each), a sweep block's
-// rows before and after its sweep (n_cap x kSweepBlock each) and its diagonal block; every part
-// starts on a 16-byte boundary.
+// rows before and after its sweep (n_cap x kSweepBlock each; together they also hold an FP64
+// copy of the window while the residual is rebuilt) and the block's pivot factors
+// (kSweepBlock x kSweepBlock); every part starts on a 16-byte boundary.
 constexpr int kSweepBlock = 8;
 __host__ __device__ inline size_t pe_ws_a2(size_t n) { return (n + 1) & ~(size_t)1; }
 __host__ __device__ inline size_t pe_ws_doubles(int n_cap) {
@@ -553,11 +554,6 @@ struct RefreshOut {
   double logdet, logL, drift;
 };
 
-// Hint that the line holding p (global memory) will be read soon: fetched into L1, no register.
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L1 [ga];\n\t}" ::"l"(p));
-}
-
 // FP64 rebuild of C^-1, v, y, log|Sigma| and the log-likelihood from the PE list (FP32 mode).
 // ok = 0 (state untouched) if C is not numerically positive definite. Arguments are passed by
 // value (no address of the caller's locals escapes, so they stay in registers).
@@ -575,7 +571,8 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   double* rowk = h + lv;                          // v
   double* P = rowk + lv;                          // a sweep block's rows before its sweep (N x SB)
   double* Pn = P + (size_t)kSweepBlock * lv;      // the same rows during and after it
-  double* Kb = Pn + (size_t)kSweepBlock * lv;     // the block's diagonal block (SB x SB, full)
+  // the block's pivot factors: F[q SB + r] = A_rp / pivot (r != q), F[q SB + q] = 1 / pivot
+  double* F = Pn + (size_t)kSweepBlock * lv;
   const double* V = M.V64;
   constexpr bool mix = MIX;
   const double mu = M.cm_mu[0], r = M.cm_r[0];  // the dynode model's (one component)
@@ -721,7 +718,6 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
   // them in turn (the same operations in the same order as sweeping the panel pivot by pivot).
   double pm = 1.0;
   int pe = 0;
-  double* F = Kb;  // the block's pivot factors: F[q SB + r] = A_rp / pivot (r != q), F[q SB + q] = 1 / pivot
 #pragma unroll 1
   for (int k0 = 0; k0 < N; k0 += SB) {
     const int nb = min(SB, N - k0), k1 = k0 + nb;
@@ -810,7 +806,6 @@ __device__ __noinline__ RefreshOut pe_refresh(const DevModel& M, const PeChain<T
       }
 #pragma unroll 1
       for (int t0 = 0; t0 < nr; t0 += RG) {
-        if (BIG && ln.sl < RG && t0 + 2 * RG + ln.sl < nr) prefetch_l1(P + (size_t)row(t0 + 2 * RG + ln.sl) * SB);
         double x[RG];
         int rr[RG];
 #pragma unroll
