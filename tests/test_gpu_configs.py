@@ -169,6 +169,60 @@ def test_fp32_highpileup_statistics(lib, orc):
     assert s_gpu["n_refresh"].min() >= 1 and s_gpu["mean_N"].mean() > 50
 
 
+def test_fp32_pileup_refresh_tracks_oracle(lib, orc):
+    """FP32 mode in the pile-up variant with an FP64 rebuild after every accepted move (K = 1):
+    12 of the high pile-up workload's waveforms from their LucyDDM states, 100 steps. Each
+    rebuild recomputes C^-1, v, y, log|Sigma| and log L in FP64 from the PE list (the blocked
+    sweep with its register-swept diagonal blocks, the residual summed PE by PE), so the chains
+    follow the FP64 oracle step by step with log acceptance ratios equal to FP32 rounding, and a
+    chain that stays in lockstep to the end reports the log-likelihood and log|Sigma| of its
+    final state (Eq. (mgauss), by Cholesky of Sigma in the oracle) to 1e-8: they come from the
+    final rebuild."""
+    torch = pytest.importorskip("torch")
+    n_steps, W = 100, 12
+    wl, params, b = _pileup(orc, W, n_steps, seed=65)
+    assert b["n_init"].min() >= 30
+    t = _device(torch, b, n_steps, trace=True, z=(b["z_init"], b["n_init"]))
+    with fsmp.Context(params, n_max=1024, precision=fsmp.FP32_REFRESH, refresh_every=1,
+                      kernel=fsmp.KERNEL_PE) as ctx:
+        ctx.run_device(t, n_steps=n_steps, burn_in=0, seed=int(b["seed"]), n_max_hint=1024)
+        torch.cuda.synchronize()
+    s_gpu, t_gpu = _results(t, W)
+    s_orc, t_orc = orc.run_batch(params, b, orc.MODE_INCREMENTAL, n_threads=16, trace=True)
+    same = (t_gpu["flags"] == t_orc["flags"]) & (t_gpu["N"] == t_orc["N"]) & (t_gpu["k0"] == t_orc["k0"])
+    pref = np.where((~same).any(1), (~same).argmax(1), n_steps)
+    bad = fsmp.ST_DRIFT | fsmp.ST_BADDET | fsmp.ST_NONFINITE | fsmp.ST_INVALID
+    assert np.all((s_gpu["status"] & bad) == 0)
+    assert s_gpu["n_refresh"].min() >= 10 and t_gpu["N"].min() >= 30
+    full = pref == n_steps
+    assert full.sum() >= W // 2, pref
+    errs = []
+    for i in range(W):
+        a = np.maximum(np.nan_to_num(t_gpu["la"][i, :pref[i]], nan=0.0), gpu_util.LA_FLOOR)
+        o = np.maximum(np.nan_to_num(t_orc["la"][i, :pref[i]], nan=0.0), gpu_util.LA_FLOOR)
+        near = np.abs(o) < 20
+        errs.append(np.abs(a - o)[near])
+    err = np.concatenate(errs)
+    print("|dla| p50 %.2e p99 %.2e max %.2e; lockstep to the end: %d of %d" % (
+        *np.percentile(err, [50, 99, 100]), full.sum(), W))
+    assert np.percentile(err, 99) < 2e-2 and err.max() < 1.0
+    # the reference for the rebuilt log L and log|Sigma|: Eq. (mgauss) by Cholesky of Sigma(z) on
+    # the final state. The rebuild inverts C = diag(r) + A^T A in FP64: r = sigma_eps^2 / sigma_q^2
+    # = 0.01 bounds its smallest eigenvalue and N |a|^2 (about 600 here) its largest, so kappa(C)
+    # reaches ~6e4 and rounding in h^T C^-1 h (~1e3) enters log L amplified by 1 / (2 sigma_eps^2)
+    # = 200: 1e-8 of log L (measured worst 1.1e-9) is within that arithmetic, 1e-9 is not always
+    for i in np.nonzero(full)[0]:
+        one = {k: b[k][i:i + 1] for k in ("lambda0", "t_origin_ns", "T_lo", "T_hi", "t0_init", "n_init")}
+        o0, o1 = int(b["offsets"][i]), int(b["offsets"][i + 1])
+        one.update(samples=b["samples"][o0:o1], offsets=np.array([0, o1 - o0], np.int32), z_init=b["z_init"][i:i + 1],
+                   seed=b["seed"], n_steps=n_steps, burn_in=0, index_base=int(b.get("index_base", 0)) + int(i))
+        st = orc.run_chain_state(params, one)
+        assert st["N"] == s_gpu["N_final"][i] and st["k0"] == s_gpu["k0_final"][i]
+        logp, logdet, _ = orc.logp_definition(params, b["samples"][o0:o1], st["z"])
+        np.testing.assert_allclose(s_gpu["logL"][i], logp, rtol=1e-8, atol=1e-8, err_msg=str(i))
+        np.testing.assert_allclose(s_gpu["logdet"][i], logdet, rtol=1e-8, atol=1e-8, err_msg=str(i))
+
+
 # ------------------------------------------------------------------ the plain FP64 form
 def test_lockstep_plain_form(lib, orc):
     """The plain one-launch-per-chain FP64 form (full Sigma^-1 in global memory): 32 waveforms
