@@ -5,6 +5,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -22,3 +24,37 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "batched_uneven_100k"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+
+def test_capture_data_is_taken_only_for_its_kernel_source_and_workload(tmp_path, monkeypatch):
+    """roofline.traffic and roofline.issue come from a committed ncu capture of the same kernel
+    source and the same workload; another workload, or a changed source, gets nothing."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cuh"
+    src.write_bytes(b"// a kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    entry = {"warp_inst_per_step": 100.0, "traffic_bytes_per_launch": 10, "units_per_launch": 5, "units": "steps"}
+    (tmp_path / "profiles" / "k_dram_traffic.json").write_text(
+        json.dumps({"kernel_sha": sha, "workloads": {"w1": entry}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic(str(src), "k", "w1") == entry
+    assert bench.load_traffic(str(src), "k", "w2") is None
+    src.write_bytes(b"// a changed kernel source\n")
+    assert bench.load_traffic(str(src), "k", "w1") is None
+    assert bench.load_traffic(str(src), "absent", "w1") is None
+
+
+def test_committed_capture_covers_the_default_workload():
+    """The committed capture of the PE kernel (when it is of the current source) has the default
+    workload's warp instructions per step and DRAM bytes per launch."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_2403_03156_gb300", "csrc", "fsmp_pe_kernel.cuh")
+    d = bench.load_traffic(src, "pe_kernel", "batched_uneven_100k")
+    if d is None:
+        pytest.skip("the committed capture predates the current kernel source")
+    assert d["warp_inst_per_step"] > 0 and d["traffic_bytes_per_launch"] > 0 and d["units_per_launch"] > 0
